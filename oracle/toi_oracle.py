@@ -1,0 +1,620 @@
+"""FP64 CPU oracle of the FIP-TOI hot path (TOI 2-D imaging + FITrig tLISI).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product (the CUDA library and its
+Python binding) imports, links or executes this module; only the tests,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference legs of
+``bench.py`` use it.  It shares no code with the CUDA path.
+
+It is a plain, slow, step-by-step restatement of the method in float64:
+
+  S1  Section 3 / 3.1 / 3.5  wavelength scaling, sample selection and weights,
+                             SVD basis V of the centred baseline cloud, R = B V^T
+  S2  Section 3.2            (r1, r2) -> continuous grid coordinates
+  S3  Section 4.1 stage 3    convolutional gridding ("place visibilities on a
+                             grid"; kernel = exponential of semicircle, reading c1)
+  S4  Section 4.1 stage 4    inverse 2-D FFT (numpy.fft as the library step)
+  S5  Section 3.2 Eq. 11     grid correction, crop, Re, 1/(omega sum w)
+  S6  Section 3.3 / App. A   reduced SIN re-projection (and the WCS route)
+  S7  Section 2 / 4.5        tLISI per tile from the three youngest images
+                             (stand-in formula, reading c9: parity unpinned
+                             against the paper, which does not print it)
+  S8  Section 2, 6.2, 6.3    periodic / non-periodic scores, z-threshold,
+                             connected tiles -> bounding boxes, in a fixed FP64
+                             evaluation order so that another implementation
+                             of the same order reproduces it bit for bit.
+  adjoint                   degridding = exact adjoint of gridding
+
+Exact-definition routines used as pins: ``dirty_image_dft`` (the 2-D dirty
+image of Section 3.2 evaluated by brute force).
+
+Parity status per function (pins live in tests/):
+  wavelength/sample selection, svd_basis, grid_es, image pipeline: pinned
+    (planted planes, brute-force DFT, point-source closed forms, adjoint).
+  reproject_*: pinned (two derivations agree; identity at xi = eta = 0).
+  tlisi: parity unpinned against the paper (its formula is not printed);
+    pinned only by invariants of the stand-in definition.
+  candidates_*: pinned by planted cubes and an independent FFT cross-check.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+
+C_LIGHT = 299_792_458.0
+ARCSEC = math.pi / 648000.0
+
+
+# ==========================================================================
+# S1 — data handling (Section 3.5) and the SVD basis (Section 3.1)
+# ==========================================================================
+
+def parallel_hands(n_pol: int) -> Tuple[int, int]:
+    """Indices of the parallel-hand polarisations (reading c13): linear feeds
+    XX,XY,YX,YY -> (0, 3); two pols -> (0, 1); Stokes I only -> (0, 0)."""
+    if n_pol == 4:
+        return 0, 3
+    if n_pol == 2:
+        return 0, 1
+    if n_pol == 1:
+        return 0, 0
+    raise ValueError("n_pol must be 1, 2 or 4")
+
+
+def sample_weights_and_values(vis, flag, weight):
+    """Section 3.5: flagged samples get zero weight; WEIGHT_SPECTRUM (or unit
+    weights) is applied before gridding; the parallel hands are averaged with
+    their weights.  Returns per (baseline, channel):
+        w_q = w_a + w_b                  (the sample weight)
+        c_q = w_a V_a + w_b V_b = w_q Vis_q   (the weighted visibility)
+    For a single polarisation, w_q = w_0 and c_q = w_0 V_0."""
+    vis = np.asarray(vis)
+    n_pol = vis.shape[2]
+    pa, pb = parallel_hands(n_pol)
+    f = np.asarray(flag).astype(bool)
+    if weight is None:
+        wp = np.where(f, 0.0, 1.0)
+    else:
+        wp = np.where(f, 0.0, np.asarray(weight, dtype=np.float64))
+    v = vis.astype(np.complex128)
+    if pa == pb:
+        w_q = wp[:, :, pa]
+        c_q = wp[:, :, pa] * v[:, :, pa]
+    else:
+        w_q = wp[:, :, pa] + wp[:, :, pb]
+        c_q = wp[:, :, pa] * v[:, :, pa] + wp[:, :, pb] * v[:, :, pb]
+    return w_q, c_q
+
+
+def wavelength_baselines(uvw_m, freq_hz):
+    """Section 3: each UVW (metres) is converted to wavelengths for its channel,
+    b_q = uvw * nu / c.  Shape [n_bl, n_ch, 3]."""
+    uvw = np.asarray(uvw_m, dtype=np.float64)
+    k = np.asarray(freq_hz, dtype=np.float64) / C_LIGHT
+    return uvw[:, None, :] * k[None, :, None]
+
+
+def svd_basis(B_sel: np.ndarray) -> np.ndarray:
+    """Section 3.1: SVD of the centred baseline matrix B~ = B - mean(B).
+    Rows of V are the basis vectors.  Sign / in-plane conventions (reading c5,
+    the paper leaves them open): v3 = right singular vector of the smallest
+    singular value with V33 > 0; v1 = e_u projected onto the plane and
+    normalised (e_v if e_u is within 0.999 of the normal); v2 = v3 x v1, so
+    (v1, v2, v3) is right-handed."""
+    Bt = B_sel - B_sel.mean(axis=0, keepdims=True)
+    _, _, Vt = np.linalg.svd(Bt, full_matrices=False)
+    v3 = Vt[2].copy()
+    if v3[2] < 0:
+        v3 = -v3
+    e = np.array([1.0, 0.0, 0.0])
+    if abs(e @ v3) > 0.999:
+        e = np.array([0.0, 1.0, 0.0])
+    v1 = e - (e @ v3) * v3
+    v1 /= np.linalg.norm(v1)
+    v2 = np.cross(v3, v1)
+    return np.stack([v1, v2, v3])
+
+
+def omega_of(V: np.ndarray) -> float:
+    """Eq. 11: area Jacobian omega = |V11 V22 - V21 V12|."""
+    return abs(V[0, 0] * V[1, 1] - V[1, 0] * V[0, 1])
+
+
+def tilt_of(V: np.ndarray) -> Tuple[float, float]:
+    """Section 3.3: xi = V31 / V33, eta = V32 / V33."""
+    return V[2, 0] / V[2, 2], V[2, 1] / V[2, 2]
+
+
+def prepare(uvw_m, freq_hz, vis, flag, weight=None) -> Dict:
+    """S1 for one snapshot: selected samples (w_q > 0, reading c4), the basis
+    V, R = B V^T (Section 3.1), omega, xi, eta and sum of weights."""
+    w_q, c_q = sample_weights_and_values(vis, flag, weight)
+    B = wavelength_baselines(uvw_m, freq_hz)
+    sel = w_q > 0
+    if not sel.any():
+        raise ValueError("no unflagged sample with positive weight")
+    Bs = B[sel]
+    V = svd_basis(Bs)
+    R = Bs @ V.T
+    xi, eta = tilt_of(V)
+    return dict(V=V, omega=omega_of(V), xi=xi, eta=eta, sumw=float(w_q[sel].sum()),
+                r=R, c=c_q[sel], w=w_q[sel], sel=sel, n_vis=int(sel.sum()))
+
+
+# ==========================================================================
+# S2/S3 — gridding with the exponential-of-semicircle kernel (reading c1)
+# ==========================================================================
+
+def es_beta(W: int) -> float:
+    """ES shape parameter for upsampling 2: beta = 2.30 W (Barnett, Magland &
+    af Klinteberg 2019)."""
+    return 2.30 * W
+
+
+def es_kernel(x, W: int, beta: float):
+    """psi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)) for |x| <= W/2, else 0."""
+    z = 2.0 * np.asarray(x, dtype=np.float64) / W
+    inside = np.abs(z) <= 1.0
+    zz = np.where(inside, z, 0.0)
+    return np.where(inside, np.exp(beta * (np.sqrt(1.0 - zz * zz) - 1.0)), 0.0)
+
+
+def grid_coords(r1, r2, N: int, cell_arcsec: float, sigma: int = 2):
+    """Section 3.2 with the pixel convention of Section 3.3 (reading c6):
+    t1 = -beta (j1 - N/2), t2 = beta (j2 - N/2) (0-based j, beta in radians).
+    The phase 2 pi (r1 t1 + r2 t2) is reproduced by a centred DFT over a
+    G = sigma N grid when a sample sits at
+        g1 = G/2 - r1 beta G,   g2 = G/2 + r2 beta G."""
+    G = sigma * N
+    beta = cell_arcsec * ARCSEC
+    g1 = G / 2 - np.asarray(r1) * beta * G
+    g2 = G / 2 + np.asarray(r2) * beta * G
+    return g1, g2
+
+
+def tap_start(g, W: int):
+    """First tap index of a sample at continuous coordinate g: ceil(g - W/2)."""
+    return np.ceil(g - W / 2.0).astype(np.int64)
+
+
+def grid_es(g1, g2, c, G: int, W: int, beta: float) -> np.ndarray:
+    """Convolutional gridding: Grid[k2, k1] = sum_q c_q psi(k1 - g1_q) psi(k2 - g2_q)
+    over the W x W taps k = ceil(g - W/2) + 0..W-1 of every sample.  Full
+    complex G x G grid, row index k2, column index k1."""
+    g1 = np.asarray(g1, dtype=np.float64)
+    g2 = np.asarray(g2, dtype=np.float64)
+    c = np.asarray(c, dtype=np.complex128)
+    k1 = tap_start(g1, W)
+    k2 = tap_start(g2, W)
+    if len(c) and (k1.min() < 0 or k2.min() < 0 or k1.max() + W > G or k2.max() + W > G):
+        raise ValueError("a kernel footprint leaves the grid: reduce the cell size")
+    re = np.zeros(G * G)
+    im = np.zeros(G * G)
+    wx = [es_kernel(k1 + a - g1, W, beta) for a in range(W)]
+    wy = [es_kernel(k2 + b - g2, W, beta) for b in range(W)]
+    for b in range(W):
+        for a in range(W):
+            idx = (k2 + b) * G + (k1 + a)
+            val = c * (wx[a] * wy[b])
+            re += np.bincount(idx, weights=val.real, minlength=G * G)
+            im += np.bincount(idx, weights=val.imag, minlength=G * G)
+    return (re + 1j * im).reshape(G, G)
+
+
+def degrid_es(grid: np.ndarray, g1, g2, W: int, beta: float) -> np.ndarray:
+    """Adjoint of grid_es: d_q = sum_k Grid[k2, k1] psi(k1 - g1_q) psi(k2 - g2_q)."""
+    g1 = np.asarray(g1, dtype=np.float64)
+    g2 = np.asarray(g2, dtype=np.float64)
+    k1 = tap_start(g1, W)
+    k2 = tap_start(g2, W)
+    out = np.zeros(len(g1), dtype=np.complex128)
+    for b in range(W):
+        wy = es_kernel(k2 + b - g2, W, beta)
+        for a in range(W):
+            wx = es_kernel(k1 + a - g1, W, beta)
+            out += grid[k2 + b, k1 + a] * (wx * wy)
+    return out
+
+
+# ==========================================================================
+# S4/S5 — inverse FFT, grid correction, normalisation
+# ==========================================================================
+
+def ifft_centred(grid: np.ndarray, N: int) -> np.ndarray:
+    """Section 4.1 stage 4: unnormalised inverse 2-D DFT with centred indices,
+    I[j2', j1'] = sum_k' Grid[k'] exp(+2 pi i (k1' j1' + k2' j2') / G),
+    k' = k - G/2, returning the central N x N block (j' = j - N/2)."""
+    G = grid.shape[0]
+    y = np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(grid), norm="forward"))
+    lo = G // 2 - N // 2
+    return y[lo:lo + N, lo:lo + N]
+
+
+def es_fourier(f, W: int, beta: float, nodes: int = 400) -> np.ndarray:
+    """psi_hat(f) = integral_{-W/2}^{W/2} psi(x) cos(2 pi x f) dx by
+    Gauss-Legendre quadrature (reading c1: correction by the kernel's
+    numerically integrated Fourier transform)."""
+    x, wts = np.polynomial.legendre.leggauss(nodes)
+    x = x * (W / 2.0)
+    wts = wts * (W / 2.0)
+    psi = es_kernel(x, W, beta)
+    f = np.asarray(f, dtype=np.float64)
+    return (psi[None, :] * np.cos(2 * np.pi * np.outer(f, x)) * wts[None, :]).sum(1)
+
+
+def correction_vector(N: int, G: int, W: int, beta: float) -> np.ndarray:
+    j = np.arange(N) - N // 2
+    return es_fourier(j / G, W, beta)
+
+
+def tilted_image(grid: np.ndarray, N: int, W: int, beta: float, omega: float,
+                 sumw: float) -> np.ndarray:
+    """S4+S5: Re of the centred inverse FFT, divided by psi_hat(j1') psi_hat(j2')
+    and by omega * sum w (Eq. 11 and reading c2, c3)."""
+    G = grid.shape[0]
+    img = ifft_centred(grid, N).real
+    ph = correction_vector(N, G, W, beta)
+    return img / (ph[:, None] * ph[None, :]) / (omega * sumw)
+
+
+def dirty_image_dft(r1, r2, c, N: int, cell_arcsec: float, omega: float,
+                    sumw: float, rows=None, cols=None) -> np.ndarray:
+    """Exact 2-D dirty image of Section 3.2 by brute force:
+    I(t1, t2) = 1/(omega sum w) Re sum_q c_q exp(i 2 pi (r1 t1 + r2 t2)),
+    t1 = -beta (j1 - N/2), t2 = beta (j2 - N/2).  Optional pixel subsets."""
+    beta = cell_arcsec * ARCSEC
+    rows = np.arange(N) if rows is None else np.asarray(rows)
+    cols = np.arange(N) if cols is None else np.asarray(cols)
+    t1 = -beta * (cols - N // 2)
+    t2 = beta * (rows - N // 2)
+    r1 = np.asarray(r1)
+    r2 = np.asarray(r2)
+    c = np.asarray(c)
+    e1 = np.exp(2j * np.pi * np.outer(t1, r1))        # [cols, q]
+    e2 = np.exp(2j * np.pi * np.outer(t2, r2))        # [rows, q]
+    img = (e2 * c[None, :]) @ e1.T                    # [rows, cols]
+    return img.real / (omega * sumw)
+
+
+# ==========================================================================
+# S6 — re-projection (Section 3.3; Appendix A)
+# ==========================================================================
+
+def reproject_map_reduced(p1, p2, N: int, cell_deg: float, xi: float, eta: float):
+    """Section 3.3 reduced pixel-to-pixel map of a tilted-plane pixel (p1, p2)
+    (1-based) to the standard plane.  Sign of y' from Appendix A (reading c7):
+    y' = y + r0 z eta (with z = 0 the map is then the identity)."""
+    c0 = N / 2 + 1
+    x = -cell_deg * (np.asarray(p1, dtype=np.float64) - c0)
+    y = cell_deg * (np.asarray(p2, dtype=np.float64) - c0)
+    h = np.sqrt(x * x + y * y)
+    r0 = 180.0 / np.pi
+    q = (h / r0) ** 2
+    z = q / (1.0 + np.sqrt(1.0 - q))
+    xp = x + r0 * z * xi
+    yp = y + r0 * z * eta
+    return -xp / cell_deg + c0, yp / cell_deg + c0
+
+
+def reproject_map_wcs(p1, p2, N: int, cell_deg: float, xi: float, eta: float,
+                      eps: float = 1e-10):
+    """Appendix A: the conventional WCS route through native spherical
+    coordinates (phi, theta) with the SIN tilt terms; angles in radians."""
+    c0 = N / 2 + 1
+    x = -(np.pi / 180) * cell_deg * (np.asarray(p1, dtype=np.float64) - c0)
+    y = (np.pi / 180) * cell_deg * (np.asarray(p2, dtype=np.float64) - c0)
+    x, y = np.broadcast_arrays(x, y)
+    phi = np.where((x == 0) & (y <= 0), 0.0,
+          np.where((x == 0) & (y > 0), np.pi,
+          np.where((y == 0) & (x > 0), np.pi / 2,
+          np.where((y == 0) & (x < 0), -np.pi / 2, np.arctan2(x, -y)))))
+    r2 = x * x + y * y
+    r = np.sqrt(r2)
+    theta_small = np.where(r == 0, np.pi / 2,
+                  np.where((r >= 1) & (r - 1 < eps), 0.0, np.arccos(np.minimum(r, 1.0))))
+    s = np.sqrt(np.maximum(1.0 - r2, 0.0))
+    theta_large = np.where(s == 0, 0.0,
+                  np.where((s >= 1) & (s - 1 < eps), np.pi / 2, np.arcsin(np.minimum(s, 1.0))))
+    theta = np.where(r2 < 0.5, theta_small, theta_large)
+    xs = np.cos(theta) * np.sin(phi) + xi * (1 - np.sin(theta))
+    ys = -(np.cos(theta) * np.cos(phi) - eta * (1 - np.sin(theta)))
+    xd = xs * 180 / np.pi
+    yd = ys * 180 / np.pi
+    return -xd / cell_deg + c0, yd / cell_deg + c0
+
+
+def reproject_source_pixels(N: int, cell_deg: float, xi: float, eta: float,
+                            iters: int = 8):
+    """Reading c8 (gather): for every output pixel p' find the tilted pixel p
+    with map(p) = p' by fixed-point iteration p <- p' - (map(p) - p).  Returns
+    0-based float source indices (j1, j2) as arrays [N, N] (row = j2)."""
+    j2o, j1o = np.meshgrid(np.arange(N, dtype=np.float64), np.arange(N, dtype=np.float64),
+                           indexing="ij")
+    p1o, p2o = j1o + 1, j2o + 1
+    p1, p2 = p1o.copy(), p2o.copy()
+    for _ in range(iters):
+        m1, m2 = reproject_map_reduced(p1, p2, N, cell_deg, xi, eta)
+        p1 = p1o - (m1 - p1)
+        p2 = p2o - (m2 - p2)
+    return p1 - 1, p2 - 1
+
+
+def bilinear(img: np.ndarray, j1, j2) -> np.ndarray:
+    """Bilinear interpolation at 0-based (j1 = column, j2 = row); a source
+    position outside [0, N-1] in either axis gives 0 (the missing corners);
+    neighbours beyond the last row/column count as 0."""
+    N = img.shape[0]
+    out = np.zeros(np.shape(j1))
+    ok = (j1 >= 0) & (j1 <= N - 1) & (j2 >= 0) & (j2 <= N - 1)
+    a0 = np.floor(j1).astype(np.int64)
+    b0 = np.floor(j2).astype(np.int64)
+    fa = j1 - a0
+    fb = j2 - b0
+    pad = np.zeros((N + 1, N + 1))
+    pad[:N, :N] = img
+    a0c = np.clip(a0, 0, N - 1)
+    b0c = np.clip(b0, 0, N - 1)
+    v = ((1 - fb) * ((1 - fa) * pad[b0c, a0c] + fa * pad[b0c, a0c + 1]) +
+         fb * ((1 - fa) * pad[b0c + 1, a0c] + fa * pad[b0c + 1, a0c + 1]))
+    out[ok] = v[ok]
+    return out
+
+
+def reproject(img_tilted: np.ndarray, cell_arcsec: float, xi: float, eta: float,
+              iters: int = 8) -> np.ndarray:
+    """S6: standard-plane image from the tilted-plane image (reading c8)."""
+    N = img_tilted.shape[0]
+    j1, j2 = reproject_source_pixels(N, cell_arcsec / 3600.0, xi, eta, iters)
+    return bilinear(img_tilted, j1, j2)
+
+
+# ==========================================================================
+# One snapshot: S1..S6
+# ==========================================================================
+
+def image_snapshot(uvw_m, freq_hz, vis, flag, weight, N: int, cell_arcsec: float,
+                   W: int = 8, sigma: int = 2, keep_grid: bool = False) -> Dict:
+    p = prepare(uvw_m, freq_hz, vis, flag, weight)
+    G = sigma * N
+    beta = es_beta(W)
+    g1, g2 = grid_coords(p["r"][:, 0], p["r"][:, 1], N, cell_arcsec, sigma)
+    grid = grid_es(g1, g2, p["c"], G, W, beta)
+    tilted = tilted_image(grid, N, W, beta, p["omega"], p["sumw"])
+    image = reproject(tilted, cell_arcsec, p["xi"], p["eta"])
+    out = dict(V=p["V"], omega=p["omega"], xi=p["xi"], eta=p["eta"], sumw=p["sumw"],
+               n_vis=p["n_vis"], tilted=tilted, image=image, g1=g1, g2=g2, c=p["c"],
+               r=p["r"])
+    if keep_grid:
+        out["grid"] = grid
+    return out
+
+
+def hermitian_half(grid: np.ndarray) -> np.ndarray:
+    """S[k] = (Grid[k] + conj(Grid[-k])) / 2 (k' = k - G/2, -k' taken modulo
+    G), returned for rows k2' = 0..G/2 (row k2' = G/2 is the periodic copy of
+    k2' = -G/2).  The inverse DFT of S equals Re of the inverse DFT of Grid;
+    this is a test helper for half-plane grid layouts."""
+    G = grid.shape[0]
+    idx = (G - np.arange(G)) % G
+    S = 0.5 * (grid + np.conj(grid[idx][:, idx]))
+    rows = (G // 2 + np.arange(G // 2 + 1)) % G
+    return S[rows, :]
+
+
+# ==========================================================================
+# S7 — tLISI (stand-in definition, reading c9; parity unpinned vs the paper)
+# ==========================================================================
+
+def tlisi(I0: np.ndarray, I1: np.ndarray, I2: np.ndarray, T: int) -> np.ndarray:
+    """tLISI of every T x T tile from the three youngest images (Section 2,
+    Section 4.5): D_a = I1 - I0, D_b = I2 - I1.  With tile moments in float64
+    (population moments over the n = T^2 pixels),
+      S = ((2 mu_a mu_b + C1)(2 s_ab + C2)) / ((mu_a^2 + mu_b^2 + C1)(s_a^2 + s_b^2 + C2)),
+    C1 = (0.01 L)^2, C2 = (0.03 L)^2, tLISI = (1 + S) / 2 in [0, 1].
+    L is the dynamic range of the three images, max |I| over all pixels of
+    I0, I1, I2 (so a quiet tile stays near 1 whatever happens elsewhere, as
+    Section 2 describes); L = 0 gives 1 everywhere."""
+    a = np.asarray(I1, np.float64) - np.asarray(I0, np.float64)
+    b = np.asarray(I2, np.float64) - np.asarray(I1, np.float64)
+    N = a.shape[0]
+    nt = N // T
+    L = max(np.abs(I0).max(), np.abs(I1).max(), np.abs(I2).max())
+    if L == 0:
+        return np.ones((nt, nt))
+    at = a.reshape(nt, T, nt, T).transpose(0, 2, 1, 3).reshape(nt, nt, T * T)
+    bt = b.reshape(nt, T, nt, T).transpose(0, 2, 1, 3).reshape(nt, nt, T * T)
+    n = T * T
+    mu_a = at.sum(-1) / n
+    mu_b = bt.sum(-1) / n
+    va = (at * at).sum(-1) / n - mu_a * mu_a
+    vb = (bt * bt).sum(-1) / n - mu_b * mu_b
+    cab = (at * bt).sum(-1) / n - mu_a * mu_b
+    C1 = (0.01 * L) ** 2
+    C2 = (0.03 * L) ** 2
+    S = ((2 * mu_a * mu_b + C1) * (2 * cab + C2)) / ((mu_a ** 2 + mu_b ** 2 + C1) * (va + vb + C2))
+    return (1.0 + S) / 2.0
+
+
+# ==========================================================================
+# S8 — candidates (Sections 2, 6.2, 6.3) in a fixed FP64 evaluation order
+# ==========================================================================
+# Evaluation-order rules (readings c10-c12, written so a second implementation
+# can reproduce every bit): IEEE binary64, round to nearest, every product and
+# sum rounded separately (no fused multiply-add), sums sequential in the stated
+# index order unless a pairwise tree is stated.
+
+TAYLOR_TERMS = 13
+PI_2 = 1.5707963267948966      # binary64 nearest to pi/2
+
+
+def _inv_factorials():
+    fact = [1.0]
+    for n in range(1, 2 * TAYLOR_TERMS + 2):
+        fact.append(fact[-1] * float(n))
+    cos_c = [(1.0 if k % 2 == 0 else -1.0) / fact[2 * k] for k in range(TAYLOR_TERMS)]
+    sin_c = [(1.0 if k % 2 == 0 else -1.0) / fact[2 * k + 1] for k in range(TAYLOR_TERMS)]
+    return cos_c, sin_c
+
+
+def twiddle(m: int, S: int) -> Tuple[float, float]:
+    """cos, sin of 2 pi m / S: quadrant q = floor(4m / S), remainder
+    a = 4m - qS, r = (PI_2 * a) / S in [0, pi/2), Taylor series in r^2
+    (Horner from the highest of 13 terms), then the quadrant's swap/sign."""
+    m %= S
+    q = (4 * m) // S
+    a = 4 * m - q * S
+    r = (PI_2 * float(a)) / float(S)
+    r2 = r * r
+    cos_c, sin_c = _inv_factorials()
+    c = cos_c[-1]
+    s = sin_c[-1]
+    for k in range(TAYLOR_TERMS - 2, -1, -1):
+        c = c * r2 + cos_c[k]
+        s = s * r2 + sin_c[k]
+    s = s * r
+    if q == 0:
+        return c, s
+    if q == 1:
+        return -s, c
+    if q == 2:
+        return -c, -s
+    return s, -c
+
+
+def twiddle_table(S: int):
+    cs = [twiddle(m, S) for m in range(S)]
+    return np.array([x[0] for x in cs]), np.array([x[1] for x in cs])
+
+
+def pairwise_sum(a, lo: int = 0, hi: Optional[int] = None) -> float:
+    """Pairwise tree: sum(a[lo:hi]) = sum(a[lo:mid]) + sum(a[mid:hi]),
+    mid = lo + (hi - lo) // 2; a single element is itself; empty is 0."""
+    if hi is None:
+        hi = len(a)
+    n = hi - lo
+    if n <= 0:
+        return 0.0
+    if n == 1:
+        return float(a[lo])
+    mid = lo + n // 2
+    return pairwise_sum(a, lo, mid) + pairwise_sum(a, mid, hi)
+
+
+HARMONICS = (1, 2, 4, 8)
+
+
+def periodic_scores(cube: np.ndarray) -> np.ndarray:
+    """Section 2 / 6.2: per tile, the tLISI series x_t (t = 0..S-1, mean
+    removed) is Fourier transformed along time, P_f = A_f^2 + B_f^2 with
+    A_f = sum_t x_t cos(2 pi f t / S), B_f = sum_t x_t sin(2 pi f t / S)
+    (f = 1..F, F = floor(S/2)); harmonic sums H_h(f) = sum_{i=1..h, i f <= F}
+    P_{i f} for h in (1, 2, 4, 8); score = max_{f,h} H_h(f) / sqrt(h)."""
+    S = cube.shape[0]
+    x = cube.reshape(S, -1).astype(np.float64)
+    nt = x.shape[1]
+    acc = np.zeros(nt)
+    for t in range(S):
+        acc = acc + x[t]
+    mu = acc / float(S)
+    xc = [x[t] - mu for t in range(S)]
+    F = S // 2
+    if F == 0:
+        return np.zeros(nt)
+    cos_t, sin_t = twiddle_table(S)
+    P = np.zeros((F + 1, nt))
+    for f in range(1, F + 1):
+        A = np.zeros(nt)
+        B = np.zeros(nt)
+        for t in range(S):
+            m = (f * t) % S
+            A = A + xc[t] * cos_t[m]
+            B = B + xc[t] * sin_t[m]
+        P[f] = A * A + B * B
+    best = np.zeros(nt)
+    roots = {h: math.sqrt(float(h)) for h in HARMONICS}
+    for f in range(1, F + 1):
+        for h in HARMONICS:
+            H = np.zeros(nt)
+            for i in range(1, h + 1):
+                if i * f > F:
+                    break
+                H = H + P[i * f]
+            best = np.maximum(best, H / roots[h])
+    return best
+
+
+def nonperiodic_scores(cube: np.ndarray) -> np.ndarray:
+    """Section 6.3: score = sum_t (1 - tLISI_t), sequential in t."""
+    S = cube.shape[0]
+    x = cube.reshape(S, -1).astype(np.float64)
+    acc = np.zeros(x.shape[1])
+    for t in range(S):
+        acc = acc + (1.0 - x[t])
+    return acc
+
+
+def threshold(scores: np.ndarray, k: float) -> Tuple[float, float, float]:
+    """Significance (reading c11): mean and population standard deviation over
+    all tiles by the pairwise tree, thr = mean + k * std."""
+    s = np.asarray(scores, dtype=np.float64).ravel()
+    n = len(s)
+    mu = pairwise_sum(s) / float(n)
+    d = s - mu
+    var = pairwise_sum(d * d) / float(n)
+    sd = math.sqrt(var)
+    return mu + k * sd, mu, sd
+
+
+def connected_boxes(mask: np.ndarray, T: int):
+    """Reading c12: 8-connected candidate tiles; a component's label is its
+    first tile in raster order; box = [x0, y0, x1, y1) in 0-based pixels
+    (tile bounds times T); boxes sorted by (y0, x0, label)."""
+    nty, ntx = mask.shape
+    lab = -np.ones((nty, ntx), dtype=np.int64)
+    boxes = []
+    for y in range(nty):
+        for x in range(ntx):
+            if not mask[y, x] or lab[y, x] >= 0:
+                continue
+            root = y * ntx + x
+            stack = [(y, x)]
+            lab[y, x] = root
+            xs, ys = [x], [y]
+            while stack:
+                cy, cx = stack.pop()
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        ny, nx = cy + dy, cx + dx
+                        if 0 <= ny < nty and 0 <= nx < ntx and mask[ny, nx] and lab[ny, nx] < 0:
+                            lab[ny, nx] = root
+                            stack.append((ny, nx))
+                            xs.append(nx)
+                            ys.append(ny)
+            boxes.append((min(ys) * T, min(xs) * T, root,
+                          [min(xs) * T, min(ys) * T, (max(xs) + 1) * T, (max(ys) + 1) * T]))
+    boxes.sort(key=lambda b: (b[0], b[1], b[2]))
+    return [b[3] for b in boxes], lab
+
+
+MODE_PERIODIC = 0
+MODE_NONPERIODIC = 1
+
+
+def candidates(cube: np.ndarray, T: int, mode: int) -> Dict:
+    """S8 on a tLISI cube [S, nty, ntx]: scores, threshold (5 sigma periodic,
+    4 sigma non-periodic; Sections 2 and 6.3), candidate mask, boxes."""
+    S, nty, ntx = cube.shape
+    if mode == MODE_PERIODIC:
+        sc = periodic_scores(cube)
+        k = 5.0
+    elif mode == MODE_NONPERIODIC:
+        sc = nonperiodic_scores(cube)
+        k = 4.0
+    else:
+        raise ValueError(mode)
+    thr, mu, sd = threshold(sc, k)
+    mask = (sc > thr).reshape(nty, ntx)
+    boxes, lab = connected_boxes(mask, T)
+    return dict(scores=sc.reshape(nty, ntx), threshold=thr, mean=mu, std=sd,
+                mask=mask, boxes=boxes)
