@@ -1,0 +1,232 @@
+/*
+ * toi.h - C ABI of libtoi, a GB300 (sm_103a) implementation of the FIP-TOI
+ * hot path: per-snapshot Transient-Oriented Imager (TOI, 2-D mode) imaging of
+ * interferometer visibilities into dirty images, FITrig's per-tile tLISI
+ * statistic over the snapshot stream, and the candidate search on the tLISI
+ * cube.  (Li et al., "FIP-TOI: Fast Imaging Pipeline for Pulsar Localisation
+ * with a Transient-Oriented Radio Astronomical Imager".)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All data pointers are caller-owned.  "dev" pointers are CUDA device
+ *    memory of the current device, "host" pointers are host memory.  The
+ *    library never frees or retains a caller pointer beyond the call, except
+ *    that the images passed to tlisi_update are copied into the plan.
+ *  - A plan owns all of its device scratch; it allocates only in toi_plan()
+ *    and frees only in toi_plan_destroy() (no allocation in the per-snapshot
+ *    loop, Section 4.2).  tlisi_candidates() allocates its own scratch per
+ *    call (it runs once per observation).
+ *  - Every per-snapshot call is asynchronous on the plan's stream (the stream
+ *    given to toi_plan / toi_set_stream); none synchronises the host.
+ *  - Errors are status codes, never aborts.  Argument errors are detected on
+ *    the host before anything is launched.  Data-dependent errors found on
+ *    the device (a kernel footprint leaving the grid, no selected sample,
+ *    non-monotone frequencies) are latched in a device status word that
+ *    toi_sync_status() reads; the affected outputs are then zero.
+ *  - Array layouts are C order (last index fastest).  Images are [N][N] with
+ *    row index j2 and column index j1, 0-based; pixel (j1, j2) is the paper's
+ *    1-based (p1, p2) = (j1 + 1, j2 + 1) with the phase centre at N/2
+ *    (Section 3.3: x = -beta (p1 - (N/2 + 1)), y = beta (p2 - (N/2 + 1))).
+ */
+#ifndef TOI_H
+#define TOI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TOI_OK = 0,
+  TOI_ERR_ARG = 1,          /* invalid argument (sizes, null pointers, config) */
+  TOI_ERR_CUDA = 2,         /* a CUDA runtime call failed                       */
+  TOI_ERR_OOM = 3,          /* device allocation failed in toi_plan             */
+  TOI_ERR_EMPTY = 4,        /* no sample with positive weight (sum w == 0)      */
+  TOI_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                    */
+  TOI_ERR_UNSUPPORTED = 6,  /* valid but not implemented (e.g. N not 2^k)       */
+  TOI_ERR_RANGE = 7         /* a kernel footprint leaves the grid: cell too big,
+                               or channel frequencies not monotone              */
+} toi_status;
+
+/* Visibility storage (Section 3.5 DATA column; FP16 variant of the precision
+ * study): C64 = interleaved float32 (re, im); C16_CHANSCALE = interleaved
+ * float16 (re, im) times a per-channel float32 scale. */
+typedef enum { TOI_VIS_C64 = 0, TOI_VIS_C16_CHANSCALE = 1 } toi_vis_dtype;
+
+/* Candidate scoring (Section 2: temporal FFT + harmonic summing, 5 sigma;
+ * Section 6.3: sum of (1 - tLISI), 4 sigma). */
+typedef enum { TOI_CAND_PERIODIC = 0, TOI_CAND_NONPERIODIC = 1 } toi_cand_mode;
+
+typedef struct {
+  int32_t image_size;       /* N: power of two, 64 <= N <= 4096 (Section 2:
+                               user-supplied image size)                        */
+  double  cell_arcsec;      /* beta, pixel size in arcseconds (> 0)             */
+  int32_t max_baselines;    /* largest n_bl a call may pass                     */
+  int32_t max_channels;     /* largest n_ch a call may pass                     */
+  int32_t n_pol;            /* 1, 2 or 4 (parallel hands: 0; 0,1; 0,3)         */
+  int32_t vis_dtype;        /* toi_vis_dtype                                    */
+  int32_t kernel_support;   /* W, gridding-kernel width in cells: 8 (default)   */
+  int32_t oversample;       /* sigma, grid = sigma N: 2 (default)               */
+  int32_t tlisi_tile;       /* T, tLISI tile side: 32 (default); divides N      */
+  int32_t grid_slots;       /* grid buffers held by the plan (>= 1; default 1)  */
+  int32_t reserved[6];      /* must be zero                                     */
+} toi_config;
+
+typedef struct toi_plan_s* toi_plan_t;
+
+/* Fill *cfg with the defaults above for the given geometry and maxima. */
+toi_status toi_config_default(toi_config* cfg, int32_t image_size,
+                              double cell_arcsec, int32_t max_baselines,
+                              int32_t max_channels, int32_t n_pol);
+
+/* Validate *cfg and allocate every device buffer the plan will use: grid
+ * slots, the image ring (three images, Section 4.3 ring buffering), tilted
+ * image, per-baseline and per-channel tables, the grid-correction table and
+ * FFT twiddles (Section 5.2: allocation and FFT set-up happen once).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  On success
+ * *out receives the plan.  Errors: TOI_ERR_ARG, TOI_ERR_UNSUPPORTED,
+ * TOI_ERR_OOM, TOI_ERR_CUDA. */
+toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out);
+
+/* Synchronise the plan's stream and free everything it owns. */
+toi_status toi_plan_destroy(toi_plan_t plan);
+
+/* Make subsequent calls of this plan run on cuda_stream. */
+toi_status toi_set_stream(toi_plan_t plan, void* cuda_stream);
+
+/* S1-S3 of one snapshot into grid slot `slot` (Sections 3, 3.1, 3.2, 3.5 and
+ * Section 4.1 stage 3):
+ *   - per sample q = (baseline, channel): w_q = w_a + w_b over the parallel
+ *     hands, w_p = 0 if flagged else weight (or 1), c_q = w_a V_a + w_b V_b;
+ *     samples with w_q > 0 are selected;
+ *   - b_q = uvw * nu / c; V from the 3x3 covariance of the centred selected
+ *     b_q (rows: basis vectors; v3 with V33 > 0 spans the residual axis, v1 is
+ *     the u axis projected into the plane, v2 = v3 x v1); R = B V^T;
+ *   - omega = |V11 V22 - V21 V12| (Eq. 11), xi = V31/V33, eta = V32/V33;
+ *   - convolutional gridding of c_q at (r1, r2) with the exponential of
+ *     semicircle kernel (W taps, beta_ES = 2.3 W) on a sigma N grid, stored as
+ *     the Hermitian half-plane grid H[k] = G[k] + conj(G[-k]), rows k2' >= 0.
+ * uvw_m:   dev float64 [n_bl][3], metres (UVW column).
+ * freq_hz: dev float64 [n_ch], strictly monotone (CHAN_FREQ).
+ * vis:     dev [n_bl][n_ch][n_pol] complex (float32 pairs, or float16 pairs
+ *          when the plan's vis_dtype is TOI_VIS_C16_CHANSCALE).
+ * chan_scale: dev float32 [n_ch] for C16_CHANSCALE, else NULL.
+ * weight:  dev float32 [n_bl][n_ch][n_pol] (WEIGHT_SPECTRUM, >= 0) or NULL
+ *          for unit weights.
+ * flag:    dev uint8 [n_bl][n_ch][n_pol], nonzero = flagged, or NULL.
+ * Errors: TOI_ERR_ARG (host checks); device: TOI_ERR_EMPTY, TOI_ERR_RANGE. */
+toi_status toi_grid(toi_plan_t plan, const double* uvw_m, const double* freq_hz,
+                    const void* vis, const float* chan_scale,
+                    const float* weight, const uint8_t* flag,
+                    int32_t n_bl, int32_t n_ch, int32_t slot);
+
+/* S4-S6 for grid slot `slot` (Section 4.1 stages 4-5; Sections 3.2-3.3):
+ * centred inverse 2-D FFT of the sigma N grid, cropped to N x N, Re,
+ * divided by psi_hat(j1) psi_hat(j2) omega sum_w; then the reduced SIN
+ * re-projection (x' = x + r0 z xi, y' = y + r0 z eta) gathered onto the
+ * standard plane by bilinear interpolation (pixels whose source is outside
+ * the tilted image are 0).  The result becomes the newest image of the
+ * plan's ring; it is also written to `image` (dev float32 [N][N]) unless
+ * image is NULL.  snap_info (dev float64 [16] or NULL) receives V (9, row
+ * major), omega, xi, eta, sum_w, n_vis, 0, 0.  Per-tile tLISI moments of the
+ * three youngest ring images are computed in the same pass. */
+toi_status toi_image(toi_plan_t plan, int32_t slot, float* image,
+                     double* snap_info);
+
+/* S7, one tLISI matrix from the three youngest images (Section 2, 4.5):
+ * D_a = I(t-1) - I(t-2), D_b = I(t) - I(t-1), per T x T tile
+ *   S = ((2 mu_a mu_b + C1)(2 s_ab + C2)) / ((mu_a^2 + mu_b^2 + C1)(s_a^2 + s_b^2 + C2)),
+ *   C1 = (0.01 L)^2, C2 = (0.03 L)^2, L = max |I| over the three images,
+ *   tLISI = (1 + S) / 2 in [0, 1] (1 = identical).
+ * image: dev float32 [N][N], or NULL / the pointer last written by
+ *        toi_image to use the image toi_image just produced (fused path).
+ *        Any other pointer is copied into the ring as the newest image.
+ * tlisi: dev float32 [N/T][N/T] output (written only when *valid = 1).
+ * valid: host int32: 0 for the first two images of the stream (fewer than
+ *        three images exist, Section 4.1), else 1. */
+toi_status tlisi_update(toi_plan_t plan, const float* image, float* tlisi,
+                        int32_t* valid);
+
+/* Forget the image history (the next two tlisi_update calls give valid=0). */
+toi_status tlisi_reset(toi_plan_t plan);
+
+/* S8 on a tLISI cube (Sections 2, 6.2, 6.3), evaluated in a fixed binary64
+ * order (no fused multiply-add) so that any implementation of the same order
+ * gives identical bits:
+ *   periodic:     per tile x_t = tLISI_t - mean; P_f = A_f^2 + B_f^2 with
+ *                 A_f, B_f the cosine/sine sums at f = 1..floor(S/2);
+ *                 score = max over f and h in {1,2,4,8} of
+ *                 sum_{i<=h, i f <= F} P_{i f} / sqrt(h); k = 5;
+ *   nonperiodic:  score = sum_t (1 - tLISI_t); k = 4;
+ *   threshold = mean + k * std over tiles (pairwise-tree sums, population
+ *   std); candidate tiles: score > threshold; 8-connected tiles merged into
+ *   boxes [x0, y0, x1, y1) in 0-based pixels (tile bounds times T), sorted
+ *   by (y0, x0, first tile in raster order).
+ * cube:      dev float32 [S][nty][ntx].
+ * stream:    cudaStream_t to run on (NULL = default stream).
+ * threshold: host float64 out.  boxes: host int32 [max_boxes][4] out.
+ * nboxes:    host int32 out, the number of boxes found (may exceed
+ *            max_boxes; only the first max_boxes are written).
+ * scores:    dev float64 [nty][ntx] out, or NULL.
+ * Allocates and frees its device scratch; synchronises `stream`. */
+toi_status tlisi_candidates(const float* cube, int32_t S, int32_t nty,
+                            int32_t ntx, int32_t tile, int32_t mode,
+                            void* stream, double* threshold, int32_t* boxes,
+                            int32_t* nboxes, int32_t max_boxes,
+                            double* scores);
+
+/* Adjoint of toi_image's linear map for grid slot `slot` (the paper's dirty
+ * image is the adjoint of the measurement operator, Section 1): given
+ * dL/dI for the standard-plane image (dev float32 [N][N]), writes
+ *   grad_sample: dev float32 [n_bl][n_ch][2], g_q = dL/dc_q as (re, im)
+ *                (c_q = w_q Vis_q, the weighted visibility), 0 for
+ *                unselected samples;
+ *   grad_weight: dev float32 [n_bl][n_ch] or NULL, dL/dw_q holding the
+ *                visibilities fixed: (Re(conj(g_q) Vis_q) * sum_w - <I, dL/dI>) / sum_w.
+ * Uses the uvw/freq/vis/weight/flag pointers of the last toi_grid call for
+ * that slot, which must still be valid. */
+toi_status toi_degrid_backward(toi_plan_t plan, int32_t slot,
+                               const float* grad_image, float* grad_sample,
+                               float* grad_weight);
+
+/* Copy of a plan-owned buffer, for checking intermediate stages:
+ * which = 0 grid slot `slot` (complex float32 [G/2][G], the Hermitian
+ * half-plane grid, rows k2' = 0..G/2-1, columns k1 = 0..G-1), 1 tilted-plane
+ * image of the last toi_image (float32 [N][N]), 2 snapshot record of slot
+ * `slot` (float64 [16], as snap_info), 3 newest ring image (float32 [N][N]).
+ * *nbytes receives the buffer size; when dst is not NULL, min(dst_bytes,
+ * size) bytes are copied to dst (device or host memory) after the plan's
+ * stream has finished its queued work. */
+toi_status toi_plan_buffer(toi_plan_t plan, int32_t which, int32_t slot, void* dst,
+                           int64_t dst_bytes, int64_t* nbytes);
+
+/* Device-time accounting per stage of this plan, measured with CUDA events
+ * recorded on the plan's stream around each stage's kernels.  Stages:
+ * 0 plane fit (3 kernels), 1 binning (3 kernels), 2 gridding, 3 FFT rows,
+ * 4 FFT columns + correction, 5 re-projection + tLISI moments, 6 tLISI
+ * finish / external-image moments.  Kernel launches are counted per stage
+ * whether or not timing is enabled. */
+toi_status toi_profile_enable(toi_plan_t plan, int32_t enable);
+
+/* Read and reset the accumulated milliseconds (ms[nstages], may be NULL) and
+ * launch counts (launches[nstages], may be NULL); waits for the recorded
+ * events. */
+toi_status toi_profile_read(toi_plan_t plan, double* ms, int64_t* launches, int32_t nstages);
+
+/* Synchronise the plan's stream and return (and clear) the device status
+ * word: TOI_OK, TOI_ERR_EMPTY or TOI_ERR_RANGE. */
+toi_status toi_sync_status(toi_plan_t plan);
+
+/* Human-readable text of the last error of this plan ("" if none); with a
+ * NULL plan, of the last error of a plan-less call on this thread. */
+const char* toi_last_error(toi_plan_t plan);
+
+/* Static text for a status code. */
+const char* toi_status_string(toi_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOI_H */

@@ -1,0 +1,250 @@
+"""ctypes binding of libtoi (include/toi.h), argument marshalling only.
+
+Every function keeps the C name and forwards device pointers (torch CUDA
+tensors or raw integers) and the current CUDA stream; all computation
+happens in the library's kernels.  The binding refuses to run without the
+compiled library: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libtoi.so")
+
+TOI_OK = 0
+TOI_ERR_ARG = 1
+TOI_ERR_CUDA = 2
+TOI_ERR_OOM = 3
+TOI_ERR_EMPTY = 4
+TOI_ERR_TIMEOUT = 5
+TOI_ERR_UNSUPPORTED = 6
+TOI_ERR_RANGE = 7
+TOI_VIS_C64 = 0
+TOI_VIS_C16_CHANSCALE = 1
+TOI_CAND_PERIODIC = 0
+TOI_CAND_NONPERIODIC = 1
+BUF_GRID, BUF_TILTED, BUF_SNAP, BUF_RING = 0, 1, 2, 3
+
+EXPORTS = ("toi_config_default", "toi_plan", "toi_plan_destroy", "toi_set_stream", "toi_grid",
+           "toi_image", "tlisi_update", "tlisi_reset", "tlisi_candidates",
+           "toi_degrid_backward", "toi_plan_buffer", "toi_profile_enable", "toi_profile_read",
+           "toi_sync_status", "toi_last_error", "toi_status_string")
+PROF_STAGES = ("prep", "bin", "grid", "fft_rows", "fft_cols", "reproject", "tlisi")
+
+
+class ToiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libtoi status {status}: {msg}")
+        self.status = status
+
+
+class toi_config(C.Structure):
+    _fields_ = [("image_size", C.c_int32), ("cell_arcsec", C.c_double),
+                ("max_baselines", C.c_int32), ("max_channels", C.c_int32),
+                ("n_pol", C.c_int32), ("vis_dtype", C.c_int32), ("kernel_support", C.c_int32),
+                ("oversample", C.c_int32), ("tlisi_tile", C.c_int32), ("grid_slots", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libtoi.so (built in-tree by paper_2512_06254_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2512_06254_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    P, I, D = C.c_void_p, C.c_int32, C.c_double
+    sig = {
+        "toi_config_default": [C.POINTER(toi_config), I, D, I, I, I],
+        "toi_plan": [C.POINTER(toi_config), P, C.POINTER(C.c_void_p)],
+        "toi_plan_destroy": [P],
+        "toi_set_stream": [P, P],
+        "toi_grid": [P, P, P, P, P, P, P, I, I, I],
+        "toi_image": [P, I, P, P],
+        "tlisi_update": [P, P, P, C.POINTER(I)],
+        "tlisi_reset": [P],
+        "tlisi_candidates": [P, I, I, I, I, I, P, C.POINTER(D), P, C.POINTER(I), I, P],
+        "toi_degrid_backward": [P, I, P, P, P],
+        "toi_plan_buffer": [P, I, I, P, C.c_int64, C.POINTER(C.c_int64)],
+        "toi_profile_enable": [P, I],
+        "toi_profile_read": [P, P, P, I],
+        "toi_sync_status": [P],
+        "toi_last_error": [P],
+        "toi_status_string": [I],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_char_p if name in ("toi_last_error", "toi_status_string") else C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(x) -> Optional[int]:
+    """Device/host address of a torch tensor, an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors passed to libtoi must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _dev(x, dtype=None, name="tensor"):
+    if x is None:
+        return None
+    if hasattr(x, "is_cuda"):
+        if not x.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if dtype is not None and x.dtype != dtype:
+            raise TypeError(f"{name} must have dtype {dtype}, got {x.dtype}")
+    return _ptr(x)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status: int, plan=None):
+    if status != TOI_OK:
+        msg = lib().toi_last_error(plan).decode() if plan is not None or True else ""
+        raise ToiError(status, msg)
+
+
+def config_default(image_size, cell_arcsec, max_baselines, max_channels, n_pol) -> toi_config:
+    cfg = toi_config()
+    _check(lib().toi_config_default(C.byref(cfg), image_size, cell_arcsec, max_baselines,
+                                    max_channels, n_pol))
+    return cfg
+
+
+class Plan:
+    """Owner of a toi_plan_t; methods map one-to-one onto the C entry points."""
+
+    def __init__(self, image_size: int, cell_arcsec: float, max_baselines: int,
+                 max_channels: int, n_pol: int, *, vis_dtype: int = TOI_VIS_C64,
+                 tlisi_tile: int = 32, grid_slots: int = 1, stream=None):
+        import torch
+        self.cfg = config_default(image_size, cell_arcsec, max_baselines, max_channels, n_pol)
+        self.cfg.vis_dtype = vis_dtype
+        self.cfg.tlisi_tile = tlisi_tile
+        self.cfg.grid_slots = grid_slots
+        self.N = image_size
+        self.T = tlisi_tile
+        h = C.c_void_p()
+        _check(lib().toi_plan(C.byref(self.cfg), _stream(stream), C.byref(h)))
+        self.handle = h.value
+        self._torch = torch
+
+    # ---------------------------------------------------------------- calls
+    def set_stream(self, stream):
+        _check(lib().toi_set_stream(self.handle, _stream(stream)), self.handle)
+
+    def grid(self, uvw, freq, vis, flag=None, weight=None, chan_scale=None, slot: int = 0,
+             n_bl: Optional[int] = None, n_ch: Optional[int] = None):
+        t = self._torch
+        nbl = n_bl if n_bl is not None else uvw.shape[0]
+        nch = n_ch if n_ch is not None else freq.shape[0]
+        _check(lib().toi_grid(self.handle, _dev(uvw, t.float64, "uvw"), _dev(freq, t.float64, "freq"),
+                              _dev(vis, None, "vis"), _dev(chan_scale, t.float32, "chan_scale"),
+                              _dev(weight, t.float32, "weight"), _dev(flag, t.uint8, "flag"),
+                              nbl, nch, slot), self.handle)
+
+    def image(self, slot: int = 0, out=None, snap_info=None):
+        t = self._torch
+        _check(lib().toi_image(self.handle, slot, _dev(out, t.float32, "image"),
+                               _dev(snap_info, t.float64, "snap_info")), self.handle)
+        return out
+
+    def tlisi_update(self, image=None, out=None) -> bool:
+        valid = C.c_int32(0)
+        _check(lib().tlisi_update(self.handle, _dev(image, None, "image"), _dev(out, None, "tlisi"),
+                                  C.byref(valid)), self.handle)
+        return bool(valid.value)
+
+    def tlisi_reset(self):
+        _check(lib().tlisi_reset(self.handle), self.handle)
+
+    def degrid_backward(self, grad_image, grad_sample, grad_weight=None, slot: int = 0):
+        _check(lib().toi_degrid_backward(self.handle, slot, _dev(grad_image), _dev(grad_sample),
+                                         _dev(grad_weight)), self.handle)
+
+    def buffer(self, which: int, slot: int = 0):
+        """Copy of a plan-owned buffer as a new CUDA tensor (see toi_plan_buffer)."""
+        t = self._torch
+        n = C.c_int64()
+        _check(lib().toi_plan_buffer(self.handle, which, slot, None, 0, C.byref(n)), self.handle)
+        G = 2 * self.N
+        if which == BUF_GRID:
+            out = t.empty(G // 2, G, dtype=t.complex64, device="cuda")
+        elif which == BUF_SNAP:
+            out = t.empty(16, dtype=t.float64, device="cuda")
+        else:
+            out = t.empty(self.N, self.N, dtype=t.float32, device="cuda")
+        _check(lib().toi_plan_buffer(self.handle, which, slot, out.data_ptr(),
+                                     out.numel() * out.element_size(), C.byref(n)), self.handle)
+        return out
+
+    def profile_enable(self, on: bool = True):
+        _check(lib().toi_profile_enable(self.handle, 1 if on else 0), self.handle)
+
+    def profile_read(self):
+        """{stage: (milliseconds, launches)} accumulated since the last read."""
+        n = len(PROF_STAGES)
+        ms = (C.c_double * n)()
+        la = (C.c_int64 * n)()
+        _check(lib().toi_profile_read(self.handle, C.cast(ms, C.c_void_p), C.cast(la, C.c_void_p), n),
+               self.handle)
+        return {k: (ms[i], la[i]) for i, k in enumerate(PROF_STAGES)}
+
+    def sync_status(self) -> int:
+        return lib().toi_sync_status(self.handle)
+
+    def last_error(self) -> str:
+        return lib().toi_last_error(self.handle).decode()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().toi_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tlisi_candidates(cube, tile: int, mode: int, max_boxes: int = 256, scores=None,
+                     stream=None):
+    """Candidate search on a device tLISI cube [S, nty, ntx] (float32).
+    Returns (threshold, boxes [n, 4] list, n_found)."""
+    import torch
+    if cube.dtype != torch.float32 or not cube.is_cuda or cube.dim() != 3:
+        raise ValueError("cube must be a 3-D float32 CUDA tensor")
+    S, nty, ntx = cube.shape
+    thr = C.c_double()
+    nb = C.c_int32()
+    boxes = (C.c_int32 * (4 * max(1, max_boxes)))()
+    _check(lib().tlisi_candidates(_ptr(cube), S, nty, ntx, tile, mode, _stream(stream),
+                                  C.byref(thr), C.cast(boxes, C.c_void_p), C.byref(nb), max_boxes,
+                                  _dev(scores, torch.float64, "scores")))
+    n = min(nb.value, max_boxes)
+    out = [[boxes[4 * i + j] for j in range(4)] for i in range(n)]
+    return thr.value, out, nb.value

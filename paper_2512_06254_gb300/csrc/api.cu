@@ -1,0 +1,470 @@
+// libtoi C ABI: argument validation, plan ownership and the call sequence of
+// each entry point (declared and documented in include/toi.h).
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "toi_internal.cuh"
+
+namespace toi {
+cudaError_t fft_configure();
+size_t candidates_scratch_bytes(int S, int nt);
+cudaError_t candidates_run(const float* cube, int S, int nty, int ntx, int T, int mode,
+                           cudaStream_t st, void* scratch, double* scores_out, int max_boxes,
+                           int* boxes_dev, double** thr_dev, int** nbox_dev);
+cudaError_t launch_ring_moments(toi_plan_s* p, const float* image, int cur, int prev1,
+                                int prev2, bool with_moments);
+cudaError_t launch_degrid_backward(toi_plan_s* p, Slot& s, const float* grad_image,
+                                   float* grad_sample, float* grad_weight);
+
+// psi_hat(f) = integral over |x| <= W/2 of psi(x) cos(2 pi x f) dx for the
+// exponential of semicircle psi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)).
+// With 2x/W = sin(theta) the integrand becomes
+//   (W/2) exp(beta (cos(theta) - 1)) cos(pi W f sin(theta)) cos(theta),
+// smooth on [-pi/2, pi/2], integrated by the midpoint rule.  Table entry j
+// holds 1 / psi_hat((j - N/2) / G).
+void es_fourier_table(int N, int G, int W, double beta_es, float* out) {
+  const int M = 2048;
+  const double pi = 3.14159265358979323846;
+  const double h = pi / M;
+  double* wt = new double[M];
+  double* sn = new double[M];
+  for (int i = 0; i < M; ++i) {
+    const double th = -0.5 * pi + (i + 0.5) * h;
+    wt[i] = 0.5 * W * exp(beta_es * (cos(th) - 1.0)) * cos(th) * h;
+    sn[i] = sin(th);
+  }
+  for (int j = 0; j < N; ++j) {
+    const double f = (double)(j - N / 2) / (double)G;
+    double acc = 0.0;
+    for (int i = 0; i < M; ++i) acc += wt[i] * cos(pi * W * f * sn[i]);
+    out[j] = (float)(1.0 / acc);
+  }
+  delete[] wt;
+  delete[] sn;
+}
+
+int prof_begin(toi_plan_s* p, int stage, int nlaunch) {
+  p->prof.launches[stage] += nlaunch;
+  if (!p->prof.on) return -1;
+  ProfState& q = p->prof;
+  if (q.used + 2 > (int)q.ev.size()) {   // pool exhausted: fold what is recorded
+    cudaEventSynchronize(q.ev[q.used - 1]);
+    for (size_t i = 0; i < q.stage_of_pair.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, q.ev[2 * i], q.ev[2 * i + 1]);
+      q.ms[q.stage_of_pair[i]] += ms;
+    }
+    q.stage_of_pair.clear();
+    q.used = 0;
+  }
+  const int tok = q.used;
+  cudaEventRecord(q.ev[tok], p->stream);
+  q.used += 2;
+  q.stage_of_pair.push_back(stage);
+  return tok;
+}
+
+void prof_end(toi_plan_s* p, int token) {
+  if (token < 0) return;
+  cudaEventRecord(p->prof.ev[token + 1], p->stream);
+}
+
+}  // namespace toi
+
+using toi::Slot;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+toi_status fail(toi_plan_s* p, toi_status s, const std::string& msg) {
+  if (p) p->err = msg; else g_last_error = msg;
+  return s;
+}
+
+toi_status cuda_fail(toi_plan_s* p, cudaError_t e, const char* where) {
+  return fail(p, TOI_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+template <typename T>
+toi_status dev_alloc(toi_plan_s* p, T** ptr, size_t count, const char* what) {
+  cudaError_t e = cudaMalloc((void**)ptr, sizeof(T) * (count ? count : 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(p, e == cudaErrorMemoryAllocation ? TOI_ERR_OOM : TOI_ERR_CUDA,
+                std::string("allocating ") + what + ": " + cudaGetErrorString(e));
+  }
+  return TOI_OK;
+}
+
+void free_plan(toi_plan_s* p) {
+  if (!p) return;
+  if (p->slots) {
+    for (int i = 0; i < p->nslot; ++i) {
+      cudaFree(p->slots[i].grid);
+      cudaFree(p->slots[i].snap);
+      cudaFree(p->slots[i].coef);
+    }
+    delete[] p->slots;
+  }
+  cudaFree(p->kch); cudaFree(p->kch_sum); cudaFree(p->mom);
+  cudaFree(p->tile_count); cudaFree(p->tile_offset); cudaFree(p->tile_cursor);
+  cudaFree(p->items); cudaFree(p->twiddle); cudaFree(p->corr); cudaFree(p->fft_tmp);
+  cudaFree(p->tilted);
+  for (int i = 0; i < 3; ++i) cudaFree(p->ring[i]);
+  cudaFree(p->ring_max); cudaFree(p->tile_mom); cudaFree(p->d_status);
+  for (cudaEvent_t ev : p->prof.ev) cudaEventDestroy(ev);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* toi_status_string(toi_status s) {
+  switch (s) {
+    case TOI_OK: return "ok";
+    case TOI_ERR_ARG: return "invalid argument";
+    case TOI_ERR_CUDA: return "CUDA error";
+    case TOI_ERR_OOM: return "out of device memory";
+    case TOI_ERR_EMPTY: return "no selected sample (sum of weights is zero)";
+    case TOI_ERR_TIMEOUT: return "bounded device wait timed out";
+    case TOI_ERR_UNSUPPORTED: return "unsupported configuration";
+    case TOI_ERR_RANGE: return "kernel footprint outside the grid or bad frequencies";
+  }
+  return "unknown status";
+}
+
+const char* toi_last_error(toi_plan_t plan) {
+  return plan ? plan->err.c_str() : g_last_error.c_str();
+}
+
+toi_status toi_config_default(toi_config* cfg, int32_t image_size, double cell_arcsec,
+                              int32_t max_baselines, int32_t max_channels, int32_t n_pol) {
+  if (!cfg) return fail(nullptr, TOI_ERR_ARG, "cfg is NULL");
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->image_size = image_size;
+  cfg->cell_arcsec = cell_arcsec;
+  cfg->max_baselines = max_baselines;
+  cfg->max_channels = max_channels;
+  cfg->n_pol = n_pol;
+  cfg->vis_dtype = TOI_VIS_C64;
+  cfg->kernel_support = 8;
+  cfg->oversample = 2;
+  cfg->tlisi_tile = 32;
+  cfg->grid_slots = 1;
+  return TOI_OK;
+}
+
+toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
+  if (!cfg || !out) return fail(nullptr, TOI_ERR_ARG, "cfg and out must be non-NULL");
+  *out = nullptr;
+  const toi_config c = *cfg;
+  if (c.image_size < 64)
+    return fail(nullptr, TOI_ERR_ARG, "image_size must be at least 64");
+  if (!is_pow2(c.image_size) || c.image_size > 4096)
+    return fail(nullptr, TOI_ERR_UNSUPPORTED, "image_size must be a power of two in [64, 4096]");
+  if (!(c.cell_arcsec > 0.0) || !isfinite(c.cell_arcsec))
+    return fail(nullptr, TOI_ERR_ARG, "cell_arcsec must be positive and finite");
+  if (c.max_baselines < 1 || c.max_channels < 1)
+    return fail(nullptr, TOI_ERR_ARG, "max_baselines and max_channels must be >= 1");
+  if (!(c.n_pol == 1 || c.n_pol == 2 || c.n_pol == 4))
+    return fail(nullptr, TOI_ERR_ARG, "n_pol must be 1, 2 or 4");
+  if (!(c.vis_dtype == TOI_VIS_C64 || c.vis_dtype == TOI_VIS_C16_CHANSCALE))
+    return fail(nullptr, TOI_ERR_ARG, "unknown vis_dtype");
+  if (c.kernel_support != 8)
+    return fail(nullptr, TOI_ERR_UNSUPPORTED, "kernel_support must be 8");
+  if (c.oversample != 2)
+    return fail(nullptr, TOI_ERR_UNSUPPORTED, "oversample must be 2");
+  if (c.tlisi_tile < 1 || c.tlisi_tile > c.image_size || c.image_size % c.tlisi_tile != 0)
+    return fail(nullptr, TOI_ERR_ARG, "tlisi_tile must divide image_size");
+  if (c.grid_slots < 1 || c.grid_slots > 16)
+    return fail(nullptr, TOI_ERR_ARG, "grid_slots must be in [1, 16]");
+  for (int i = 0; i < 6; ++i)
+    if (c.reserved[i] != 0) return fail(nullptr, TOI_ERR_ARG, "reserved fields must be zero");
+  const long long nchunk = (c.max_channels + toi::kChunk - 1) / toi::kChunk;
+  const long long items = 2LL * c.max_baselines * nchunk * toi::kItemsPerChunk;
+  if (items > (1LL << 30)) return fail(nullptr, TOI_ERR_ARG, "max_baselines x max_channels too large");
+
+  toi_plan_s* p = new (std::nothrow) toi_plan_s();
+  if (!p) return fail(nullptr, TOI_ERR_OOM, "host allocation failed");
+  p->cfg = c;
+  p->N = c.image_size;
+  p->G = c.oversample * c.image_size;
+  p->W = c.kernel_support;
+  p->T = c.tlisi_tile;
+  p->nslot = c.grid_slots;
+  p->beta_rad = c.cell_arcsec * toi::kArcsec;
+  p->beta_es = 2.30 * c.kernel_support;
+  p->stream = (cudaStream_t)cuda_stream;
+  p->ntiles_x = p->G / toi::kTile;
+  p->ntiles_y = (p->G / 2) / toi::kTile;
+  p->max_items = (int)items;
+  const int N = p->N, G = p->G;
+  const int nt = p->ntiles_x * p->ntiles_y;
+  const int ntl = (N / p->T) * (N / p->T);
+  toi_status st = TOI_OK;
+  cudaError_t e = toi::fft_configure();
+  if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "configuring FFT kernels"); free_plan(p); return r; }
+  p->slots = new (std::nothrow) Slot[p->nslot];
+  if (!p->slots) { free_plan(p); return fail(nullptr, TOI_ERR_OOM, "host allocation failed"); }
+#define TOI_ALLOC(ptr, n, what) \
+  if ((st = dev_alloc(p, &(ptr), (n), what)) != TOI_OK) { g_last_error = p->err; free_plan(p); return st; }
+  for (int i = 0; i < p->nslot; ++i) {
+    TOI_ALLOC(p->slots[i].grid, (size_t)(G / 2) * G, "grid slot");
+    TOI_ALLOC(p->slots[i].snap, toi::SNAP_LEN, "snapshot record");
+    TOI_ALLOC(p->slots[i].coef, (size_t)c.max_baselines, "baseline coefficients");
+  }
+  TOI_ALLOC(p->kch, (size_t)c.max_channels, "channel table");
+  TOI_ALLOC(p->kch_sum, 4, "channel sums");
+  TOI_ALLOC(p->mom, (size_t)c.max_baselines, "baseline moments");
+  TOI_ALLOC(p->tile_count, (size_t)nt, "tile counts");
+  TOI_ALLOC(p->tile_offset, (size_t)nt + 1, "tile offsets");
+  TOI_ALLOC(p->tile_cursor, (size_t)nt, "tile cursors");
+  TOI_ALLOC(p->items, (size_t)p->max_items, "grid work items");
+  TOI_ALLOC(p->twiddle, (size_t)G, "FFT twiddles");
+  TOI_ALLOC(p->corr, (size_t)N, "grid correction");
+  TOI_ALLOC(p->fft_tmp, (size_t)(G / 2) * N, "FFT intermediate");
+  TOI_ALLOC(p->tilted, (size_t)N * N, "tilted image");
+  for (int i = 0; i < 3; ++i) TOI_ALLOC(p->ring[i], (size_t)N * N, "image ring");
+  TOI_ALLOC(p->ring_max, 3, "ring maxima");
+  TOI_ALLOC(p->tile_mom, (size_t)ntl * 5, "tile moments");
+  TOI_ALLOC(p->d_status, 1, "status word");
+#undef TOI_ALLOC
+  // constant tables, computed in float64 on the host
+  float2* tw = new float2[G];
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < G; ++k) {
+    const double a = 2.0 * pi * (double)k / (double)G;
+    tw[k] = make_float2((float)cos(a), (float)sin(a));
+  }
+  float* corr = new float[N];
+  toi::es_fourier_table(N, G, p->W, p->beta_es, corr);
+  e = cudaMemcpy(p->twiddle, tw, sizeof(float2) * G, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->corr, corr, sizeof(float) * N, cudaMemcpyHostToDevice);
+  delete[] tw;
+  delete[] corr;
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->ring_max, 0, 3 * sizeof(unsigned int));
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemset(p->ring[i], 0, sizeof(float) * N * N);
+  if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "initialising plan tables"); free_plan(p); return r; }
+  *out = p;
+  return TOI_OK;
+}
+
+toi_status toi_plan_destroy(toi_plan_t plan) {
+  if (!plan) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  cudaStreamSynchronize(plan->stream);
+  free_plan(plan);
+  return TOI_OK;
+}
+
+toi_status toi_set_stream(toi_plan_t plan, void* cuda_stream) {
+  if (!plan) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  plan->stream = (cudaStream_t)cuda_stream;
+  return TOI_OK;
+}
+
+toi_status toi_grid(toi_plan_t p, const double* uvw_m, const double* freq_hz, const void* vis,
+                    const float* chan_scale, const float* weight, const uint8_t* flag,
+                    int32_t n_bl, int32_t n_ch, int32_t slot) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  if (!uvw_m || !freq_hz || !vis) return fail(p, TOI_ERR_ARG, "uvw, freq and vis must be non-NULL");
+  if (n_bl < 1 || n_bl > p->cfg.max_baselines)
+    return fail(p, TOI_ERR_ARG, "n_bl outside [1, max_baselines]");
+  if (n_ch < 1 || n_ch > p->cfg.max_channels)
+    return fail(p, TOI_ERR_ARG, "n_ch outside [1, max_channels]");
+  if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
+  const bool half = p->cfg.vis_dtype == TOI_VIS_C16_CHANSCALE;
+  if (half && !chan_scale) return fail(p, TOI_ERR_ARG, "chan_scale required for float16 visibilities");
+  if (!half && chan_scale) return fail(p, TOI_ERR_ARG, "chan_scale given for float32 visibilities");
+  Slot& s = p->slots[slot];
+  cudaError_t e = toi::launch_prep(p, s, uvw_m, freq_hz, weight, flag, n_bl, n_ch);
+  if (e != cudaSuccess) return cuda_fail(p, e, "toi_grid/prep");
+  e = toi::launch_grid(p, s, freq_hz, vis, chan_scale, weight, flag, n_bl, n_ch);
+  if (e != cudaSuccess) return cuda_fail(p, e, "toi_grid/grid");
+  s.uvw = uvw_m; s.freq = freq_hz; s.vis = vis; s.chan_scale = chan_scale;
+  s.weight = weight; s.flag = flag; s.nbl = n_bl; s.nch = n_ch; s.valid = true;
+  return TOI_OK;
+}
+
+toi_status toi_image(toi_plan_t p, int32_t slot, float* image, double* snap_info) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
+  Slot& s = p->slots[slot];
+  if (!s.valid) return fail(p, TOI_ERR_ARG, "slot has not been gridded");
+  cudaError_t e = toi::launch_fft(p, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "toi_image/fft");
+  const int cur = (int)(p->nimg % 3);
+  const int prev1 = (int)((p->nimg + 2) % 3), prev2 = (int)((p->nimg + 1) % 3);
+  e = toi::launch_reproject_moments(p, s, image, p->nimg >= 2, cur, prev1, prev2);
+  if (e != cudaSuccess) return cuda_fail(p, e, "toi_image/reproject");
+  if (snap_info) {
+    e = cudaMemcpyAsync(snap_info, s.snap, sizeof(double) * toi::SNAP_LEN,
+                        cudaMemcpyDeviceToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "toi_image/snap_info");
+  }
+  p->nimg += 1;
+  p->last_image = image ? image : p->ring[cur];
+  p->fused_pending = true;
+  return TOI_OK;
+}
+
+toi_status tlisi_update(toi_plan_t p, const float* image, float* tlisi, int32_t* valid) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  if (!valid) return fail(p, TOI_ERR_ARG, "valid must be non-NULL");
+  const bool fused = p->fused_pending && (image == nullptr || image == p->last_image);
+  if (!fused) {
+    if (!image) return fail(p, TOI_ERR_ARG, "no image given and none pending from toi_image");
+    const int cur = (int)(p->nimg % 3);
+    const int prev1 = (int)((p->nimg + 2) % 3), prev2 = (int)((p->nimg + 1) % 3);
+    cudaError_t e = toi::launch_ring_moments(p, image, cur, prev1, prev2, p->nimg >= 2);
+    if (e != cudaSuccess) return cuda_fail(p, e, "tlisi_update/moments");
+    p->nimg += 1;
+  }
+  p->fused_pending = false;
+  if (p->nimg < 3) { *valid = 0; return TOI_OK; }
+  if (!tlisi) return fail(p, TOI_ERR_ARG, "tlisi must be non-NULL");
+  const int cur = (int)((p->nimg - 1) % 3);
+  const int prev1 = (int)((p->nimg + 1) % 3), prev2 = (int)(p->nimg % 3);
+  cudaError_t e = toi::launch_tlisi_finalize(p, tlisi, cur, prev1, prev2);
+  if (e != cudaSuccess) return cuda_fail(p, e, "tlisi_update/finish");
+  *valid = 1;
+  return TOI_OK;
+}
+
+toi_status tlisi_reset(toi_plan_t p) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  p->nimg = 0;
+  p->fused_pending = false;
+  p->last_image = nullptr;
+  return TOI_OK;
+}
+
+toi_status tlisi_candidates(const float* cube, int32_t S, int32_t nty, int32_t ntx, int32_t tile,
+                            int32_t mode, void* stream, double* threshold, int32_t* boxes,
+                            int32_t* nboxes, int32_t max_boxes, double* scores) {
+  if (!cube || !threshold || !nboxes) return fail(nullptr, TOI_ERR_ARG, "cube, threshold and nboxes must be non-NULL");
+  if (S < 1 || nty < 1 || ntx < 1 || tile < 1) return fail(nullptr, TOI_ERR_ARG, "S, nty, ntx, tile must be >= 1");
+  if ((long long)nty * ntx > (1 << 20)) return fail(nullptr, TOI_ERR_ARG, "too many tiles");
+  if (mode != TOI_CAND_PERIODIC && mode != TOI_CAND_NONPERIODIC) return fail(nullptr, TOI_ERR_ARG, "unknown mode");
+  if (max_boxes < 0 || (max_boxes > 0 && !boxes)) return fail(nullptr, TOI_ERR_ARG, "boxes must hold max_boxes entries");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nt = nty * ntx;
+  const size_t bytes = toi::candidates_scratch_bytes(S, nt) + sizeof(int) * 4 * (size_t)(max_boxes + 1);
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, bytes, st);
+  if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(nullptr, e, "tlisi_candidates/scratch"); }
+  int* boxes_dev = (int*)((char*)scratch + toi::candidates_scratch_bytes(S, nt));
+  double* thr_dev = nullptr;
+  int* nbox_dev = nullptr;
+  e = toi::candidates_run(cube, S, nty, ntx, tile, mode, st, scratch, scores, max_boxes, boxes_dev,
+                          &thr_dev, &nbox_dev);
+  int nb = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(threshold, thr_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nb, nbox_dev, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && max_boxes > 0 && nb > 0) {
+    const int ncopy = nb < max_boxes ? nb : max_boxes;
+    e = cudaMemcpyAsync(boxes, boxes_dev, sizeof(int) * 4 * (size_t)ncopy, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFreeAsync(scratch, st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "tlisi_candidates");
+  *nboxes = nb;
+  return TOI_OK;
+}
+
+toi_status toi_degrid_backward(toi_plan_t p, int32_t slot, const float* grad_image,
+                               float* grad_sample, float* grad_weight) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
+  if (!grad_image || !grad_sample) return fail(p, TOI_ERR_ARG, "grad_image and grad_sample must be non-NULL");
+  Slot& s = p->slots[slot];
+  if (!s.valid) return fail(p, TOI_ERR_ARG, "slot has not been gridded");
+  cudaError_t e = toi::launch_degrid_backward(p, s, grad_image, grad_sample, grad_weight);
+  if (e == cudaErrorNotSupported) return fail(p, TOI_ERR_UNSUPPORTED, "toi_degrid_backward not available");
+  if (e != cudaSuccess) return cuda_fail(p, e, "toi_degrid_backward");
+  return TOI_OK;
+}
+
+toi_status toi_plan_buffer(toi_plan_t p, int32_t which, int32_t slot, void* dst,
+                           int64_t dst_bytes, int64_t* nbytes) {
+  if (!p || !nbytes) return fail(p, TOI_ERR_ARG, "plan and nbytes must be non-NULL");
+  if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
+  const int64_t NN = (int64_t)p->N * p->N;
+  const void* src = nullptr;
+  switch (which) {
+    case 0: src = p->slots[slot].grid; *nbytes = (int64_t)(p->G / 2) * p->G * 8; break;
+    case 1: src = p->tilted; *nbytes = NN * 4; break;
+    case 2: src = p->slots[slot].snap; *nbytes = toi::SNAP_LEN * 8; break;
+    case 3: src = p->ring[(p->nimg + 2) % 3]; *nbytes = NN * 4; break;
+    default: return fail(p, TOI_ERR_ARG, "unknown buffer");
+  }
+  if (dst) {
+    if (dst_bytes < 0) return fail(p, TOI_ERR_ARG, "dst_bytes must be >= 0");
+    const size_t n = (size_t)(dst_bytes < *nbytes ? dst_bytes : *nbytes);
+    cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDefault, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "toi_plan_buffer");
+  }
+  return TOI_OK;
+}
+
+toi_status toi_profile_enable(toi_plan_t p, int32_t enable) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  if (enable && p->prof.ev.empty()) {
+    p->prof.ev.resize(4096);
+    for (auto& ev : p->prof.ev) {
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return cuda_fail(p, e, "toi_profile_enable");
+    }
+  }
+  p->prof.on = enable != 0;
+  return TOI_OK;
+}
+
+toi_status toi_profile_read(toi_plan_t p, double* ms, int64_t* launches, int32_t nstages) {
+  if (!p || nstages < 0) return fail(p, TOI_ERR_ARG, "bad arguments");
+  toi::ProfState& q = p->prof;
+  if (q.used > 0) {
+    cudaError_t e = cudaEventSynchronize(q.ev[q.used - 1]);
+    if (e != cudaSuccess) return cuda_fail(p, e, "toi_profile_read");
+    for (size_t i = 0; i < q.stage_of_pair.size(); ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, q.ev[2 * i], q.ev[2 * i + 1]);
+      q.ms[q.stage_of_pair[i]] += t;
+    }
+    q.stage_of_pair.clear();
+    q.used = 0;
+  }
+  for (int i = 0; i < nstages && i < toi::PROF_NSTAGE; ++i) {
+    if (ms) ms[i] = q.ms[i];
+    if (launches) launches[i] = q.launches[i];
+    q.ms[i] = 0.0;
+    q.launches[i] = 0;
+  }
+  return TOI_OK;
+}
+
+toi_status toi_sync_status(toi_plan_t p) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(p, e, "toi_sync_status");
+  int st = 0;
+  e = cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(p, e, "toi_sync_status");
+  if (st == TOI_DEV_EMPTY) return fail(p, TOI_ERR_EMPTY, "no sample with positive weight");
+  if (st == TOI_DEV_RANGE)
+    return fail(p, TOI_ERR_RANGE, "kernel footprint outside the grid, non-monotone frequencies or bin overflow");
+  return TOI_OK;
+}
+
+}  // extern "C"

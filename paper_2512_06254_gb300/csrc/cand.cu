@@ -1,0 +1,259 @@
+// S8: candidate search on the tLISI cube (Section 2: Fourier transform along
+// time, harmonic summing, significance map, 5 sigma, connected tiles to
+// bounding boxes; Section 6.3: sum of (1 - tLISI), 4 sigma).
+//
+// Every floating-point step is binary64 with an explicit rounding intrinsic
+// (__dadd_rn, __dmul_rn, __ddiv_rn, __dsqrt_rn), so nothing is contracted into
+// a fused multiply-add and the evaluation order below is the whole
+// specification of the result:
+//   twiddles   cos, sin of 2 pi m / S: quadrant q = floor(4m / S),
+//              a = 4m - qS, r = (pi/2 * a) / S, 13-term Taylor series in r^2
+//              by Horner from the highest term, then the quadrant's swap/sign;
+//   mean       sequential sum over t of (double) tLISI, divided by S;
+//   P_f        A = sum_t x_t cos_{ft mod S}, B = sum_t x_t sin_{ft mod S}
+//              (sequential in t, x_t = tLISI_t - mean), P_f = A*A + B*B;
+//   score      max over f = 1..S/2, h in {1,2,4,8} of
+//              (sum_{i=1..h, i f <= S/2} P_{i f}) / sqrt(h)   (periodic)
+//              or sequential sum over t of (1 - tLISI_t)       (non-periodic);
+//   threshold  pairwise-tree sums (split at lo + n/2) for the mean and the
+//              population variance over tiles; thr = mean + k * sqrt(var).
+#include <limits.h>
+
+#include "toi_internal.cuh"
+
+namespace toi {
+namespace {
+
+constexpr int kTaylorTerms = 13;
+constexpr double kPi2 = 1.5707963267948966;   // binary64 nearest pi/2
+
+__global__ void twiddle_kernel(int S, double* __restrict__ ct, double* __restrict__ st) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= S) return;
+  double fact[2 * kTaylorTerms + 2];
+  fact[0] = 1.0;
+  for (int n = 1; n < 2 * kTaylorTerms + 2; ++n) fact[n] = __dmul_rn(fact[n - 1], (double)n);
+  const long long m4 = 4LL * m;
+  const int q = (int)(m4 / S);
+  const long long a = m4 - (long long)q * S;
+  const double r = __ddiv_rn(__dmul_rn(kPi2, (double)a), (double)S);
+  const double r2 = __dmul_rn(r, r);
+  const int K = kTaylorTerms - 1;
+  double c = __ddiv_rn((K % 2 == 0) ? 1.0 : -1.0, fact[2 * K]);
+  double s = __ddiv_rn((K % 2 == 0) ? 1.0 : -1.0, fact[2 * K + 1]);
+  for (int k = K - 1; k >= 0; --k) {
+    const double sg = (k % 2 == 0) ? 1.0 : -1.0;
+    c = __dadd_rn(__dmul_rn(c, r2), __ddiv_rn(sg, fact[2 * k]));
+    s = __dadd_rn(__dmul_rn(s, r2), __ddiv_rn(sg, fact[2 * k + 1]));
+  }
+  s = __dmul_rn(s, r);
+  double cc, ss;
+  if (q == 0) { cc = c; ss = s; }
+  else if (q == 1) { cc = -s; ss = c; }
+  else if (q == 2) { cc = -c; ss = -s; }
+  else { cc = s; ss = -c; }
+  ct[m] = cc;
+  st[m] = ss;
+}
+
+__global__ void mean_kernel(const float* __restrict__ cube, int S, int nt, int mode,
+                            double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nt) return;
+  double acc = 0.0;
+  if (mode == TOI_CAND_NONPERIODIC) {
+    for (int t = 0; t < S; ++t) acc = __dadd_rn(acc, __dsub_rn(1.0, (double)cube[(size_t)t * nt + k]));
+    out[k] = acc;
+  } else {
+    for (int t = 0; t < S; ++t) acc = __dadd_rn(acc, (double)cube[(size_t)t * nt + k]);
+    out[k] = __ddiv_rn(acc, (double)S);
+  }
+}
+
+// One thread per (f, tile): the power P_f of the mean-removed series.
+__global__ void power_kernel(const float* __restrict__ cube, int S, int nt, int F,
+                             const double* __restrict__ mu, const double* __restrict__ ct,
+                             const double* __restrict__ st, double* __restrict__ P) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)F * nt) return;
+  const int k = (int)(id % nt);
+  const int f = (int)(id / nt) + 1;
+  const double m = mu[k];
+  double A = 0.0, B = 0.0;
+  int idx = 0;   // (f * t) mod S, advanced incrementally
+  for (int t = 0; t < S; ++t) {
+    const double x = __dsub_rn((double)cube[(size_t)t * nt + k], m);
+    A = __dadd_rn(A, __dmul_rn(x, ct[idx]));
+    B = __dadd_rn(B, __dmul_rn(x, st[idx]));
+    idx += f;
+    if (idx >= S) idx -= S;
+  }
+  P[(size_t)f * nt + k] = __dadd_rn(__dmul_rn(A, A), __dmul_rn(B, B));
+}
+
+__global__ void harmonic_kernel(const double* __restrict__ P, int nt, int F,
+                                double* __restrict__ score) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nt) return;
+  const int hs[4] = {1, 2, 4, 8};
+  double roots[4];
+  for (int i = 0; i < 4; ++i) roots[i] = __dsqrt_rn((double)hs[i]);
+  double best = 0.0;
+  for (int f = 1; f <= F; ++f) {
+    for (int hi = 0; hi < 4; ++hi) {
+      double H = 0.0;
+      for (int i = 1; i <= hs[hi]; ++i) {
+        if (i * f > F) break;
+        H = __dadd_rn(H, P[(size_t)(i * f) * nt + k]);
+      }
+      best = fmax(best, __ddiv_rn(H, roots[hi]));
+    }
+  }
+  score[k] = best;
+}
+
+__device__ double pairwise_sum(const double* a, int lo, int hi) {
+  const int n = hi - lo;
+  if (n <= 0) return 0.0;
+  if (n == 1) return a[lo];
+  const int mid = lo + n / 2;
+  return __dadd_rn(pairwise_sum(a, lo, mid), pairwise_sum(a, mid, hi));
+}
+
+// One block: threshold, candidate mask, 8-connected labelling (label = first
+// tile of the component in raster order), boxes sorted by (y0, x0, label).
+__global__ void __launch_bounds__(1024)
+label_kernel(const double* __restrict__ score, int nty, int ntx, int T, double ksig,
+             double* __restrict__ work, int* __restrict__ lab, int* __restrict__ bb,
+             double* __restrict__ thr_out, int* __restrict__ nbox_out, int* __restrict__ boxes,
+             int max_boxes) {
+  const int nt = nty * ntx;
+  __shared__ double s_thr;
+  __shared__ int s_nroot;
+  if (threadIdx.x == 0) {
+    const double n = (double)nt;
+    const double mu = __ddiv_rn(pairwise_sum(score, 0, nt), n);
+    for (int k = 0; k < nt; ++k) {
+      const double d = __dsub_rn(score[k], mu);
+      work[k] = __dmul_rn(d, d);
+    }
+    const double var = __ddiv_rn(pairwise_sum(work, 0, nt), n);
+    const double sd = __dsqrt_rn(var);
+    s_thr = __dadd_rn(mu, __dmul_rn(ksig, sd));
+    *thr_out = s_thr;
+    s_nroot = 0;
+  }
+  __syncthreads();
+  const double thr = s_thr;
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    lab[k] = score[k] > thr ? k : INT_MAX;
+    bb[4 * k + 0] = INT_MAX; bb[4 * k + 1] = INT_MAX;
+    bb[4 * k + 2] = -1; bb[4 * k + 3] = -1;
+  }
+  __syncthreads();
+  for (int iter = 0; iter < nt + 1; ++iter) {
+    int changed = 0;
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+      const int l = lab[k];
+      if (l == INT_MAX) continue;
+      const int y = k / ntx, x = k % ntx;
+      int m = l;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int yy = y + dy, xx = x + dx;
+          if (yy < 0 || yy >= nty || xx < 0 || xx >= ntx) continue;
+          const int ln = lab[yy * ntx + xx];
+          if (ln < m) m = ln;
+        }
+      if (m < l) { atomicMin(&lab[k], m); changed = 1; }
+    }
+    if (!__syncthreads_or(changed)) break;
+  }
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    const int l = lab[k];
+    if (l == INT_MAX) continue;
+    const int y = k / ntx, x = k % ntx;
+    atomicMin(&bb[4 * l + 0], x);
+    atomicMin(&bb[4 * l + 1], y);
+    atomicMax(&bb[4 * l + 2], x);
+    atomicMax(&bb[4 * l + 3], y);
+    if (l == k) atomicAdd(&s_nroot, 1);
+  }
+  __syncthreads();
+  // rank of each root by (y0, x0, label)
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    if (lab[k] != k) continue;
+    const int x0 = bb[4 * k], y0 = bb[4 * k + 1];
+    int rank = 0;
+    for (int j = 0; j < nt; ++j) {
+      if (lab[j] != j || j == k) continue;
+      const int xj = bb[4 * j], yj = bb[4 * j + 1];
+      if (yj < y0 || (yj == y0 && (xj < x0 || (xj == x0 && j < k)))) ++rank;
+    }
+    if (rank < max_boxes) {
+      boxes[4 * rank + 0] = x0 * T;
+      boxes[4 * rank + 1] = y0 * T;
+      boxes[4 * rank + 2] = (bb[4 * k + 2] + 1) * T;
+      boxes[4 * rank + 3] = (bb[4 * k + 3] + 1) * T;
+    }
+  }
+  if (threadIdx.x == 0) *nbox_out = s_nroot;
+}
+
+}  // namespace
+
+// Scratch layout (bytes) for S slices of an nt-tile cube.
+size_t candidates_scratch_bytes(int S, int nt) {
+  const int F = S / 2;
+  size_t b = 0;
+  b += sizeof(double) * (size_t)S * 2;          // twiddles
+  b += sizeof(double) * (size_t)nt;             // mean / score
+  b += sizeof(double) * (size_t)(F + 1) * nt;   // P
+  b += sizeof(double) * (size_t)nt;             // work
+  b += sizeof(double) * 2;                      // threshold + pad
+  b += sizeof(int) * (size_t)nt * 5;            // labels + boxes by root
+  b += sizeof(int) * 4;                         // count
+  return b + 256;
+}
+
+cudaError_t candidates_run(const float* cube, int S, int nty, int ntx, int T, int mode,
+                           cudaStream_t st, void* scratch, double* scores_out, int max_boxes,
+                           int* boxes_dev, double** thr_dev, int** nbox_dev) {
+  const int nt = nty * ntx;
+  const int F = S / 2;
+  char* p = reinterpret_cast<char*>(scratch);
+  auto take = [&](size_t bytes) {
+    void* r = p;
+    p += (bytes + 15) & ~(size_t)15;
+    return r;
+  };
+  double* ct = (double*)take(sizeof(double) * S);
+  double* stw = (double*)take(sizeof(double) * S);
+  double* mean = (double*)take(sizeof(double) * nt);
+  double* P = (double*)take(sizeof(double) * (size_t)(F + 1) * nt);
+  double* work = (double*)take(sizeof(double) * nt);
+  double* thr = (double*)take(sizeof(double) * 2);
+  int* lab = (int*)take(sizeof(int) * nt);
+  int* bb = (int*)take(sizeof(int) * 4 * nt);
+  int* nbox = (int*)take(sizeof(int) * 4);
+  double* score = scores_out ? scores_out : mean;
+  mean_kernel<<<(nt + 255) / 256, 256, 0, st>>>(cube, S, nt, mode, mode == TOI_CAND_NONPERIODIC ? score : mean);
+  if (mode == TOI_CAND_PERIODIC) {
+    if (F > 0) {
+      twiddle_kernel<<<(S + 255) / 256, 256, 0, st>>>(S, ct, stw);
+      const long long n = (long long)F * nt;
+      power_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cube, S, nt, F, mean, ct, stw, P);
+      harmonic_kernel<<<(nt + 255) / 256, 256, 0, st>>>(P, nt, F, score);
+    } else {
+      cudaMemsetAsync(score, 0, sizeof(double) * nt, st);
+    }
+  }
+  const double k = mode == TOI_CAND_PERIODIC ? 5.0 : 4.0;
+  label_kernel<<<1, 1024, 0, st>>>(score, nty, ntx, T, k, work, lab, bb, thr, nbox, boxes_dev,
+                                   max_boxes);
+  *thr_dev = thr;
+  *nbox_dev = nbox;
+  return cudaGetLastError();
+}
+
+}  // namespace toi

@@ -1,0 +1,155 @@
+// Internal declarations shared by the libtoi translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "toi.h"
+
+namespace toi {
+
+constexpr double kCLight = 299792458.0;
+constexpr double kArcsec = 3.14159265358979323846 / 648000.0;
+
+// Gridding tiles: the half-plane grid (G/2 rows x G columns) is split into
+// kTile x kTile tiles; one CTA owns one tile.
+constexpr int kTile = 64;
+// Channels per gridding work item (one warp-sized chunk of one track).
+constexpr int kChunk = 32;
+// Upper bound on work items per (track, chunk) used to size the bin store.
+constexpr int kItemsPerChunk = 8;
+
+// Layout of the per-slot snapshot record (float64).
+enum SnapField {
+  SNAP_V = 0,       // 9 values, row major
+  SNAP_OMEGA = 9,
+  SNAP_XI = 10,
+  SNAP_ETA = 11,
+  SNAP_SUMW = 12,
+  SNAP_NVIS = 13,
+  SNAP_LEN = 16
+};
+
+// Per-baseline record written by the plane fit: coefficients of the grid
+// coordinates, g1 = G/2 + a1 k, g2 = G/2 + a2 k, k = nu / c (float64), and r3.
+struct BaselineCoef {
+  double a1, a2, r3, pad;
+};
+
+// Per-baseline moment record of the selected samples.
+struct BaselineMoments {
+  double sk_desel;    // sum of k over deselected channels
+  double sk2_desel;   // sum of k^2 over deselected channels
+  double sumw;        // sum of weights (float64)
+  long long ndesel;   // number of deselected channels
+};
+
+struct GridItem {
+  int track;   // 2 * baseline + (0: upper half-plane track, 1: its mirror)
+  int chunk;   // channel chunk index (kChunk channels)
+};
+
+struct Slot {
+  float2* grid = nullptr;          // [G/2][G] Hermitian half-plane grid
+  double* snap = nullptr;          // [SNAP_LEN]
+  BaselineCoef* coef = nullptr;    // [max_bl]
+  // pointers of the last toi_grid call (for the adjoint)
+  const double* uvw = nullptr;
+  const double* freq = nullptr;
+  const void* vis = nullptr;
+  const float* chan_scale = nullptr;
+  const float* weight = nullptr;
+  const uint8_t* flag = nullptr;
+  int nbl = 0, nch = 0;
+  bool valid = false;
+};
+
+// Per-stage device-time accounting with CUDA events on the plan's stream.
+enum ProfStage {
+  PROF_PREP = 0, PROF_BIN, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_REPROJECT,
+  PROF_TLISI, PROF_NSTAGE
+};
+
+struct ProfState {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;       // pre-created pool
+  std::vector<int> stage_of_pair;    // stage of each recorded (start, stop) pair
+  int used = 0;                      // events consumed
+  double ms[PROF_NSTAGE] = {0};
+  long long launches[PROF_NSTAGE] = {0};   // kernel launches per stage (always counted)
+};
+
+}  // namespace toi
+
+struct toi_plan_s {
+  toi_config cfg;
+  int N = 0, G = 0, W = 0, T = 0, nslot = 0;
+  double beta_rad = 0.0;       // cell size in radians
+  double beta_es = 0.0;        // ES kernel shape
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  toi::Slot* slots = nullptr;
+  // shared scratch
+  double* kch = nullptr;                 // [max_ch] k = nu / c
+  double* kch_sum = nullptr;             // [4]: sum k, sum k^2 over all channels, kmax
+  toi::BaselineMoments* mom = nullptr;   // [max_bl]
+  int* tile_count = nullptr;             // [ntiles]
+  int* tile_offset = nullptr;            // [ntiles + 1]
+  int* tile_cursor = nullptr;            // [ntiles]
+  toi::GridItem* items = nullptr;        // [max_items]
+  int max_items = 0;
+  int ntiles_x = 0, ntiles_y = 0;
+  float2* twiddle = nullptr;             // [G] exp(+2 pi i k / G)
+  float* corr = nullptr;                 // [N] 1 / psi_hat((j - N/2) / G)
+  float2* fft_tmp = nullptr;             // [G/2][N] rows after pass 1
+  float* tilted = nullptr;               // [N][N]
+  float* ring[3] = {nullptr, nullptr, nullptr};
+  unsigned int* ring_max = nullptr;      // [3] float bits of max |I|
+  double* tile_mom = nullptr;            // [ntl][6]
+  int* d_status = nullptr;               // device status word
+  long long nimg = 0;                    // images in the ring since reset
+  const float* last_image = nullptr;     // output pointer of the last toi_image
+  bool fused_pending = false;
+  toi::ProfState prof;
+};
+
+namespace toi {
+
+// ------------------------------------------------------------- launches --
+// prep.cu
+cudaError_t launch_prep(toi_plan_s* p, Slot& s, const double* uvw, const double* freq,
+                        const float* weight, const uint8_t* flag, int nbl, int nch);
+// grid.cu
+cudaError_t launch_grid(toi_plan_s* p, Slot& s, const double* freq, const void* vis,
+                        const float* chan_scale, const float* weight, const uint8_t* flag,
+                        int nbl, int nch);
+// fft.cu
+cudaError_t launch_fft(toi_plan_s* p, Slot& s);
+// finish.cu
+cudaError_t launch_reproject_moments(toi_plan_s* p, Slot& s, float* image_out,
+                                     bool with_moments, int cur, int prev1, int prev2);
+cudaError_t launch_ring_moments(toi_plan_s* p, const float* image, int cur, int prev1,
+                                int prev2);
+cudaError_t launch_tlisi_finalize(toi_plan_s* p, float* tlisi, int cur, int prev1, int prev2);
+
+// host-side constant tables (api.cu)
+void es_fourier_table(int N, int G, int W, double beta_es, float* out);
+
+// Profiling: prof_begin returns a token (-1 when off) for prof_end.
+int prof_begin(toi_plan_s* p, int stage, int nlaunch);
+void prof_end(toi_plan_s* p, int token);
+
+// Device helpers -----------------------------------------------------------
+__device__ __forceinline__ void set_status(int* st, int code) {
+  atomicCAS(st, 0, code);
+}
+
+}  // namespace toi
+
+// Status codes written by kernels into the device status word.
+#define TOI_DEV_EMPTY 4
+#define TOI_DEV_RANGE 7

@@ -1,0 +1,60 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every
+function include/toi.h declares, and rejects bad arguments on the host
+before touching the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libtoi():
+    from paper_2512_06254_gb300 import build
+    if not build.up_to_date():
+        build.build()
+    import paper_2512_06254_gb300 as toi
+    return toi
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "toi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(libtoi):
+    names = declared_functions()
+    assert len(names) >= 14
+    L = C.CDLL(libtoi.binding.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in toi.h but not exported"
+    assert set(names) == set(libtoi.binding.EXPORTS)
+
+
+def test_host_validation_without_gpu(libtoi):
+    from paper_2512_06254_gb300 import binding as b
+    L = libtoi.lib()
+    h = C.c_void_p()
+    cases = [((100, 2.0, 10, 10, 4), libtoi.TOI_ERR_UNSUPPORTED),
+             ((32, 2.0, 10, 10, 4), libtoi.TOI_ERR_ARG),
+             ((128, -1.0, 10, 10, 4), libtoi.TOI_ERR_ARG),
+             ((128, 2.0, 0, 10, 4), libtoi.TOI_ERR_ARG),
+             ((128, 2.0, 10, 10, 3), libtoi.TOI_ERR_ARG)]
+    for args, want in cases:
+        cfg = b.config_default(*args)
+        assert L.toi_plan(C.byref(cfg), None, C.byref(h)) == want
+        assert L.toi_last_error(None)
+    cfg = b.config_default(128, 2.0, 10, 10, 4)
+    cfg.tlisi_tile = 48
+    assert L.toi_plan(C.byref(cfg), None, C.byref(h)) == libtoi.TOI_ERR_ARG
+    cfg = b.config_default(128, 2.0, 10, 10, 4)
+    cfg.reserved[2] = 1
+    assert L.toi_plan(C.byref(cfg), None, C.byref(h)) == libtoi.TOI_ERR_ARG
+    assert L.toi_grid(None, None, None, None, None, None, None, 1, 1, 0) == libtoi.TOI_ERR_ARG
+    assert L.tlisi_candidates(None, 1, 1, 1, 1, 0, None, None, None, None, 0, None) == libtoi.TOI_ERR_ARG
+    assert L.toi_status_string(libtoi.TOI_ERR_RANGE)
