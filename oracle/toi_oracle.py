@@ -101,9 +101,14 @@ def svd_basis(B_sel: np.ndarray) -> np.ndarray:
     the paper leaves them open): v3 = right singular vector of the smallest
     singular value with V33 > 0; v1 = e_u projected onto the plane and
     normalised (e_v if e_u is within 0.999 of the normal); v2 = v3 x v1, so
-    (v1, v2, v3) is right-handed."""
+    (v1, v2, v3) is right-handed.  A sample cloud of rank <= 1 (second
+    singular value <= 1e-6 of the first) fixes no plane: V = I."""
     Bt = B_sel - B_sel.mean(axis=0, keepdims=True)
-    _, _, Vt = np.linalg.svd(Bt, full_matrices=False)
+    if Bt.shape[0] < 3:
+        Bt = np.vstack([Bt, np.zeros((3 - Bt.shape[0], 3))])
+    _, sv, Vt = np.linalg.svd(Bt, full_matrices=False)
+    if not sv[1] > 1e-6 * sv[0]:
+        return np.eye(3)
     v3 = Vt[2].copy()
     if v3[2] < 0:
         v3 = -v3

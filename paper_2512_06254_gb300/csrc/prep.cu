@@ -198,9 +198,15 @@ __global__ void prep_finalize_kernel(const double* __restrict__ uvw, int nbl, in
       C[1][0] = C[0][1]; C[2][0] = C[0][2]; C[2][1] = C[1][2];
       double E[3][3];
       jacobi3(C, E);
-      int imin = 0;
-      for (int i = 1; i < 3; ++i)
+      int imin = 0, imax = 0;
+      for (int i = 1; i < 3; ++i) {
         if (C[i][i] < C[imin][imin]) imin = i;
+        if (C[i][i] > C[imax][imax]) imax = i;
+      }
+      const int imid = (imin == imax) ? (imin + 1) % 3 : 3 - imin - imax;
+      // rank <= 1 (second singular value <= 1e-6 of the first): no plane, V = I
+      const double lmax = fmax(C[imax][imax], 0.0), lmid = fmax(C[imid][imid], 0.0);
+      const bool degenerate = !(sqrt(lmid) > 1e-6 * sqrt(lmax));
       double v3[3] = {E[0][imin], E[1][imin], E[2][imin]};
       double nn = sqrt(v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2]);
       for (int i = 0; i < 3; ++i) v3[i] /= nn;
@@ -214,7 +220,8 @@ __global__ void prep_finalize_kernel(const double* __restrict__ uvw, int nbl, in
       for (int i = 0; i < 3; ++i) v1[i] /= nn;
       const double v2[3] = {v3[1] * v1[2] - v3[2] * v1[1], v3[2] * v1[0] - v3[0] * v1[2],
                             v3[0] * v1[1] - v3[1] * v1[0]};
-      for (int i = 0; i < 3; ++i) { V[0][i] = v1[i]; V[1][i] = v2[i]; V[2][i] = v3[i]; }
+      if (!degenerate)
+        for (int i = 0; i < 3; ++i) { V[0][i] = v1[i]; V[1][i] = v2[i]; V[2][i] = v3[i]; }
     } else {
       set_status(status, TOI_DEV_EMPTY);
     }

@@ -33,4 +33,6 @@ def gpu_image(plan, dsnap, slot=0, out=True):
 
 def rel_err(a, b):
     """max |a - b| / max |b|."""
-    return float(np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), 1e-300))
+    a = np.asarray(a)
+    a = a.astype(np.complex128) if np.iscomplexobj(a) else a.astype(np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))

@@ -51,6 +51,14 @@ def test_svd_coplanar_identity():
     assert O.omega_of(V) == pytest.approx(1.0, abs=1e-15)
 
 
+def test_svd_degenerate_cloud_is_identity():
+    """One sample, or samples on one line through the mean, fix no plane:
+    the basis falls back to V = I (standard 2-D imaging)."""
+    assert np.array_equal(O.svd_basis(np.array([[572.8, 636.5, 71.9]])), np.eye(3))
+    t = np.linspace(1.0, 2.0, 50)[:, None]
+    assert np.array_equal(O.svd_basis(t * np.array([[300.0, -20.0, 5.0]])), np.eye(3))
+
+
 def test_svd_matches_covariance_eigenvectors():
     """The smallest-variance direction of the centred cloud (eigenvector of
     the 3x3 covariance) equals the third basis row."""
