@@ -240,7 +240,7 @@ def run_ours(args):
                "config": {"workload": WORKLOAD, "snapshots_per_step": S,
                           "resident_pool": args.pool, "image": N_IMG, "grid": G,
                           "tlisi_tile": T, "candidate_mode": "periodic",
-                          "l2": "inputs larger than L2 (297 MB per snapshot, 120 distinct)",
+                          "l2": "inputs larger than L2 (297 MB per snapshot, 40 distinct = one pulsar period)",
                           "parallelism": f"replicas{world}"},
                "roofline": roofline, "stages": stages, "gpu_launches": int(launches),
                "candidates_found": found[2] if found else None,
@@ -332,7 +332,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--snapshots", type=int, default=1500)
-    ap.add_argument("--pool", type=int, default=120)
+    ap.add_argument("--pool", type=int, default=40)
     ap.add_argument("--host-pool", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--e2e-warmup", type=int, default=1)

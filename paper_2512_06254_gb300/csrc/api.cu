@@ -14,8 +14,6 @@ size_t candidates_scratch_bytes(int S, int nt);
 cudaError_t candidates_run(const float* cube, int S, int nty, int ntx, int T, int mode,
                            cudaStream_t st, void* scratch, double* scores_out, int max_boxes,
                            int* boxes_dev, double** thr_dev, int** nbox_dev);
-cudaError_t launch_ring_moments(toi_plan_s* p, const float* image, int cur, int prev1,
-                                int prev2, bool with_moments);
 cudaError_t launch_degrid_backward(toi_plan_s* p, Slot& s, const float* grad_image,
                                    float* grad_sample, float* grad_weight);
 
@@ -113,9 +111,8 @@ void free_plan(toi_plan_s* p) {
     }
     delete[] p->slots;
   }
-  cudaFree(p->kch); cudaFree(p->kch_sum); cudaFree(p->mom);
-  cudaFree(p->tile_count); cudaFree(p->tile_offset); cudaFree(p->tile_cursor);
-  cudaFree(p->items); cudaFree(p->twiddle); cudaFree(p->corr); cudaFree(p->fft_tmp);
+  cudaFree(p->kch); cudaFree(p->kf); cudaFree(p->kch_sum); cudaFree(p->mom);
+  cudaFree(p->twiddle); cudaFree(p->corr); cudaFree(p->fft_tmp);
   cudaFree(p->tilted);
   for (int i = 0; i < 3; ++i) cudaFree(p->ring[i]);
   cudaFree(p->ring_max); cudaFree(p->tile_mom); cudaFree(p->d_status);
@@ -188,9 +185,8 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     return fail(nullptr, TOI_ERR_ARG, "grid_slots must be in [1, 16]");
   for (int i = 0; i < 6; ++i)
     if (c.reserved[i] != 0) return fail(nullptr, TOI_ERR_ARG, "reserved fields must be zero");
-  const long long nchunk = (c.max_channels + toi::kChunk - 1) / toi::kChunk;
-  const long long items = 2LL * c.max_baselines * nchunk * toi::kItemsPerChunk;
-  if (items > (1LL << 30)) return fail(nullptr, TOI_ERR_ARG, "max_baselines x max_channels too large");
+  if ((long long)c.max_baselines * c.max_channels * c.n_pol > (1LL << 40))
+    return fail(nullptr, TOI_ERR_ARG, "max_baselines x max_channels too large");
 
   toi_plan_s* p = new (std::nothrow) toi_plan_s();
   if (!p) return fail(nullptr, TOI_ERR_OOM, "host allocation failed");
@@ -203,11 +199,7 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   p->beta_rad = c.cell_arcsec * toi::kArcsec;
   p->beta_es = 2.30 * c.kernel_support;
   p->stream = (cudaStream_t)cuda_stream;
-  p->ntiles_x = p->G / toi::kTile;
-  p->ntiles_y = (p->G / 2) / toi::kTile;
-  p->max_items = (int)items;
   const int N = p->N, G = p->G;
-  const int nt = p->ntiles_x * p->ntiles_y;
   const int ntl = (N / p->T) * (N / p->T);
   toi_status st = TOI_OK;
   cudaError_t e = toi::fft_configure();
@@ -222,12 +214,9 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     TOI_ALLOC(p->slots[i].coef, (size_t)c.max_baselines, "baseline coefficients");
   }
   TOI_ALLOC(p->kch, (size_t)c.max_channels, "channel table");
-  TOI_ALLOC(p->kch_sum, 4, "channel sums");
+  TOI_ALLOC(p->kf, (size_t)c.max_channels, "channel table (float pairs)");
+  TOI_ALLOC(p->kch_sum, 2 * ((size_t)c.max_channels + 255) / 256 + 2, "channel sums");
   TOI_ALLOC(p->mom, (size_t)c.max_baselines, "baseline moments");
-  TOI_ALLOC(p->tile_count, (size_t)nt, "tile counts");
-  TOI_ALLOC(p->tile_offset, (size_t)nt + 1, "tile offsets");
-  TOI_ALLOC(p->tile_cursor, (size_t)nt, "tile cursors");
-  TOI_ALLOC(p->items, (size_t)p->max_items, "grid work items");
   TOI_ALLOC(p->twiddle, (size_t)G, "FFT twiddles");
   TOI_ALLOC(p->corr, (size_t)N, "grid correction");
   TOI_ALLOC(p->fft_tmp, (size_t)(G / 2) * N, "FFT intermediate");
@@ -284,6 +273,10 @@ toi_status toi_grid(toi_plan_t p, const double* uvw_m, const double* freq_hz, co
   const bool half = p->cfg.vis_dtype == TOI_VIS_C16_CHANSCALE;
   if (half && !chan_scale) return fail(p, TOI_ERR_ARG, "chan_scale required for float16 visibilities");
   if (!half && chan_scale) return fail(p, TOI_ERR_ARG, "chan_scale given for float32 visibilities");
+  if (((uintptr_t)uvw_m & 7) || ((uintptr_t)freq_hz & 7) || ((uintptr_t)vis & (half ? 3 : 7)) ||
+      ((uintptr_t)weight & 3) || ((uintptr_t)chan_scale & 3) ||
+      (p->cfg.n_pol == 4 && ((uintptr_t)flag & 3)))
+    return fail(p, TOI_ERR_ARG, "misaligned input pointer (element alignment; flags of 4 pols: 4 bytes)");
   Slot& s = p->slots[slot];
   cudaError_t e = toi::launch_prep(p, s, uvw_m, freq_hz, weight, flag, n_bl, n_ch);
   if (e != cudaSuccess) return cuda_fail(p, e, "toi_grid/prep");

@@ -5,16 +5,23 @@
 // real), so the grid is stored as its Hermitian half-plane
 //     H[k] = G[k] + conj(G[-k]),   rows k2' = k2 - G/2 in [0, G/2),
 // i.e. every sample contributes c_q at +k_q and conj(c_q) at -k_q, each
-// clipped to the upper half-plane.  A baseline's samples lie on a radial
-// track g(k) = G/2 + a k (k = nu / c), so each baseline gives two tracks: the
-// one in the upper half-plane and its mirror, which only reaches the stored
-// rows near k2' = 0.
+// clipped to the stored rows.  A baseline's samples lie on a radial track
+// g(k) = G/2 + a k (k = nu / c); each baseline gives the track in the upper
+// half-plane and its mirror, which only reaches rows near k2' = 0.
 //
-// Work distribution.  The stored grid is cut into kTile x kTile tiles owned
-// by one CTA each.  A binning pass lists, for every tile, the (track,
-// 32-channel chunk) pairs whose kernel footprints touch it; the tile's CTA
-// accumulates those samples in shared memory and writes the tile once (no
-// global atomics, every cell written exactly once, empty tiles as zeros).
+// Work distribution.  One warp per (track, channel segment); lane l walks a
+// contiguous run of channels.  Consecutive channels of a track move by a
+// small fraction of a cell, so each lane keeps the W x W footprint of its
+// current sample in registers and accumulates successive samples there with
+// register FMAs only.  When the track moves on by a cell, the column (or
+// row) it leaves behind is complete and is added to the grid with one vector
+// reduction per non-zero cell, and the window slides by one cell.  Grid
+// traffic is therefore about W cells per cell of track length instead of
+// W^2 per sample; the 67 MB
+// half-plane grid of a 2048^2 image stays resident in L2 for these
+// reductions, and the streamed visibilities are read with evict-first loads.
+// The grid is cleared before gridding.  Cell sums are exact up to float32
+// rounding order (the reductions commute).
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -23,8 +30,9 @@
 namespace toi {
 namespace {
 
-constexpr int kGridThreads = 256;
-constexpr int kW = 8;   // kernel support compiled in (validated in toi_plan)
+constexpr int kW = 8;             // kernel support compiled in (validated in toi_plan)
+constexpr int kWin = kW;          // register window side (the footprint itself)
+constexpr int kWarps = 2;         // warps per block
 
 struct TrackGeom {
   double s1, s2;   // signed coefficients: g1 = G/2 + s1 k, y = s2 k (row coordinate)
@@ -41,100 +49,28 @@ __device__ __forceinline__ TrackGeom track_geom(const BaselineCoef& cf, int mirr
   return t;
 }
 
-// Tile rectangle touched by the footprints of one chunk of a track (false
-// when none of the stored grid is touched).  Coordinates are clamped in
-// float64 before any integer conversion, so footprints far outside the grid
-// (an oversized cell, reported through the status word) stay harmless.
-__device__ __forceinline__ bool chunk_tiles(const TrackGeom& t, double kA, double kB, int G,
-                                            int W, int ntx, int nty, int& tx0, int& tx1,
-                                            int& ty0, int& ty1) {
-  const double kmin = fmin(kA, kB), kmax = fmax(kA, kB);
-  const double g1a = 0.5 * G + t.s1 * kmin, g1b = 0.5 * G + t.s1 * kmax;
-  const double ya = t.s2 * kmin, yb = t.s2 * kmax;
-  const double hw = 0.5 * W;
-  const double x0 = ceil(fmin(g1a, g1b) - hw);
-  const double x1 = ceil(fmax(g1a, g1b) - hw) + (W - 1);
-  const double y0 = ceil(fmin(ya, yb) - hw);
-  const double y1 = ceil(fmax(ya, yb) - hw) + (W - 1);
-  if (!(x1 >= 0.0 && x0 <= G - 1.0 && y1 >= 0.0 && y0 <= 0.5 * G - 1.0)) return false;
-  tx0 = (int)fmax(x0, 0.0) / kTile;
-  tx1 = (int)fmin(x1, G - 1.0) / kTile;
-  ty0 = (int)fmax(y0, 0.0) / kTile;
-  ty1 = (int)fmin(y1, 0.5 * G - 1.0) / kTile;
-  return tx0 <= tx1 && ty0 <= ty1 && tx1 < ntx && ty1 < nty;
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-__global__ void bin_count_kernel(const BaselineCoef* __restrict__ coef,
-                                 const double* __restrict__ kch, int nbl, int nch, int G, int W,
-                                 int ntx, int nty, int* __restrict__ tile_count) {
-  const int nchunk = (nch + kChunk - 1) / kChunk;
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (long long)2 * nbl * nchunk) return;
-  const int track = (int)(id / nchunk), chunk = (int)(id % nchunk);
-  const TrackGeom t = track_geom(coef[track >> 1], track & 1);
-  const int c0 = chunk * kChunk, c1 = min(nch, c0 + kChunk) - 1;
-  int tx0, tx1, ty0, ty1;
-  if (!chunk_tiles(t, kch[c0], kch[c1], G, W, ntx, nty, tx0, tx1, ty0, ty1)) return;
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&tile_count[ty * ntx + tx], 1);
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-// Exclusive scan of the tile counts (one block), capacity check.
-__global__ void bin_scan_kernel(const int* __restrict__ count, int n, int* __restrict__ offset,
-                                int* __restrict__ cursor, int capacity, int* status) {
-  __shared__ int part[1024];
-  const int per = (n + 1023) / 1024;
-  const int lo = threadIdx.x * per, hi = min(n, lo + per);
-  int s = 0;
-  for (int i = lo; i < hi; ++i) s += count[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int d = 1; d < 1024; d <<= 1) {
-    const int v = (int)threadIdx.x >= d ? part[threadIdx.x - d] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  int run = part[threadIdx.x] - s;
-  for (int i = lo; i < hi; ++i) {
-    offset[i] = run;
-    cursor[i] = 0;
-    run += count[i];
-  }
-  if (threadIdx.x == 1023) {
-    offset[n] = part[1023];
-    if (part[1023] > capacity) set_status(status, TOI_DEV_RANGE);
-  }
+// Exponential of semicircle psi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)) with
+// bl2 = beta * log2(e).
+__device__ __forceinline__ float es_kernel(float x, float bl2) {
+  const float z = x * (2.0f / kW);
+  const float t = fmaxf(1.0f - z * z, 0.0f);
+  return ex2_approx(bl2 * (sqrt_approx(t) - 1.0f));
 }
 
-__global__ void bin_fill_kernel(const BaselineCoef* __restrict__ coef,
-                                const double* __restrict__ kch, int nbl, int nch, int G, int W,
-                                int ntx, int nty, const int* __restrict__ offset,
-                                int* __restrict__ cursor, GridItem* __restrict__ items,
-                                int capacity) {
-  const int nchunk = (nch + kChunk - 1) / kChunk;
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (long long)2 * nbl * nchunk) return;
-  const int track = (int)(id / nchunk), chunk = (int)(id % nchunk);
-  const TrackGeom t = track_geom(coef[track >> 1], track & 1);
-  const int c0 = chunk * kChunk, c1 = min(nch, c0 + kChunk) - 1;
-  int tx0, tx1, ty0, ty1;
-  if (!chunk_tiles(t, kch[c0], kch[c1], G, W, ntx, nty, tx0, tx1, ty0, ty1)) return;
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx) {
-      const int tile = ty * ntx + tx;
-      const int pos = offset[tile] + atomicAdd(&cursor[tile], 1);
-      if (pos < capacity) items[pos] = GridItem{track, chunk};
-    }
-}
-
-// Exponential of semicircle, psi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)),
-// written as exp(-beta z^2 / (1 + sqrt(1 - z^2))) to avoid cancellation.
-__device__ __forceinline__ float es_kernel(float x, float inv_half_w, float beta) {
-  const float z = x * inv_half_w;
-  const float z2 = fminf(z * z, 1.0f);
-  const float s = sqrtf(1.0f - z2);
-  return expf(-beta * z2 / (1.0f + s));
+__device__ __forceinline__ void red_add(float2* p, float2 v) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y));
 }
 
 __device__ __forceinline__ void parallel_hands(int npol, int& pa, int& pb) {
@@ -146,92 +82,243 @@ __device__ __forceinline__ void parallel_hands(int npol, int& pa, int& pb) {
 template <bool HALF>
 __device__ __forceinline__ float2 load_vis(const void* vis, size_t idx, float scale) {
   if (HALF) {
-    const float2 f = __half22float2(reinterpret_cast<const __half2*>(vis)[idx]);
+    const unsigned int raw = __ldcs(reinterpret_cast<const unsigned int*>(vis) + idx);
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&raw));
     return make_float2(f.x * scale, f.y * scale);
   } else {
-    return reinterpret_cast<const float2*>(vis)[idx];
+    return __ldcs(reinterpret_cast<const float2*>(vis) + idx);
   }
 }
 
+// A lane's W x W register window.  Window column i sits at absolute grid
+// column ox + sx * i and row j at oy + sy * j, with (sx, sy) the direction the
+// lane's track moves in, so the window only ever slides forwards.
+struct Window {
+  float2 a[kWin][kWin];   // a[row][col]
+};
+
+__device__ __forceinline__ void flush_cell(float2* __restrict__ H, int G, int x, int y, float2 v) {
+  if ((v.x != 0.f || v.y != 0.f) && x >= 0 && x < G && y >= 0 && y < (G >> 1))
+    red_add(H + (size_t)y * G + x, v);
+}
+
+__device__ __forceinline__ void flush_all(Window& w, float2* __restrict__ H, int G, int ox, int oy,
+                                       int sx, int sy) {
+#pragma unroll
+  for (int j = 0; j < kWin; ++j)
+#pragma unroll
+    for (int i = 0; i < kWin; ++i) {
+      flush_cell(H, G, ox + sx * i, oy + sy * j, w.a[j][i]);
+      w.a[j][i] = make_float2(0.f, 0.f);
+    }
+}
+
+// slide one column forwards: column 0 is final
+__device__ __forceinline__ void slide_x(Window& w, float2* __restrict__ H, int G, int ox, int oy,
+                                        int sy) {
+#pragma unroll
+  for (int j = 0; j < kWin; ++j) {
+    flush_cell(H, G, ox, oy + sy * j, w.a[j][0]);
+#pragma unroll
+    for (int i = 0; i < kWin - 1; ++i) w.a[j][i] = w.a[j][i + 1];
+    w.a[j][kWin - 1] = make_float2(0.f, 0.f);
+  }
+}
+
+// slide one row forwards: row 0 is final
+__device__ __forceinline__ void slide_y(Window& w, float2* __restrict__ H, int G, int ox, int oy,
+                                        int sx) {
+#pragma unroll
+  for (int i = 0; i < kWin; ++i) flush_cell(H, G, ox + sx * i, oy, w.a[0][i]);
+#pragma unroll
+  for (int j = 0; j < kWin - 1; ++j)
+#pragma unroll
+    for (int i = 0; i < kWin; ++i) w.a[j][i] = w.a[j + 1][i];
+#pragma unroll
+  for (int i = 0; i < kWin; ++i) w.a[kWin - 1][i] = make_float2(0.f, 0.f);
+}
+
+struct Sample {
+  float2 c;      // weighted visibility
+  float2 k;      // k = nu / c of its channel (float pair)
+  bool sel;      // w_q > 0
+};
+
 template <bool HALF>
-__global__ void __launch_bounds__(kGridThreads)
-grid_tiles_kernel(const BaselineCoef* __restrict__ coef, const double* __restrict__ kch,
-                  const void* __restrict__ vis, const float* __restrict__ chan_scale,
-                  const float* __restrict__ weight, const uint8_t* __restrict__ flag, int nch,
-                  int npol, int G, float beta_es, const int* __restrict__ offset,
-                  const GridItem* __restrict__ items, int capacity, int ntx,
-                  float2* __restrict__ H) {
-  __shared__ float2 acc[kTile * kTile];
-  const int tile = blockIdx.x;
-  const int tx = tile % ntx, ty = tile / ntx;
-  const int x0 = tx * kTile, y0 = ty * kTile;
-  for (int i = threadIdx.x; i < kTile * kTile; i += kGridThreads) acc[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-  const int lo = offset[tile];
-  const int hi = min(offset[tile + 1], capacity);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ Sample load_sample(const void* vis, const float* chan_scale,
+                                              const float* weight, const uint8_t* flag,
+                                              const float2* kf, size_t o, int ch, int npol,
+                                              int pa, int pb) {
+  Sample s;
+  s.k = kf[ch];
+  bool fa = false, fb = false;
+  if (flag) {
+    if (npol == 4) {   // the four flag bytes of a record as one aligned word
+      const unsigned int f4 = __ldcs(reinterpret_cast<const unsigned int*>(flag + o));
+      fa = (f4 & 0xffu) != 0;
+      fb = (f4 >> 24) != 0;
+    } else {
+      fa = __ldcs(flag + o + pa) != 0;
+      fb = __ldcs(flag + o + pb) != 0;
+    }
+  }
+  float wa = fa ? 0.f : (weight ? __ldcs(weight + o + pa) : 1.f);
+  float wb = fb ? 0.f : (weight ? __ldcs(weight + o + pb) : 1.f);
+  if (pa == pb) wb = 0.f;
+  s.sel = wa + wb > 0.f;
+  const float sc = HALF ? chan_scale[ch] : 1.f;
+  const float2 va = load_vis<HALF>(vis, o + pa, sc);
+  s.c = make_float2(wa * va.x, wa * va.y);
+  if (pa != pb) {
+    const float2 vb = load_vis<HALF>(vis, o + pb, sc);
+    s.c.x += wb * vb.x;
+    s.c.y += wb * vb.y;
+  }
+  return s;
+}
+
+// Tap origin of one axis.  The coordinate is g = c0 + 4 + s k with s (per
+// track) and k = nu / c (per channel) known in float64, each held here as an
+// unevaluated float sum hi + lo.  The product and the sum are formed with
+// error-free transformations (Dekker / Knuth two-product and two-sum), so
+// the first tap index q = ceil(g - 4) and the offset f = q - (g - 4) in [0, 1)
+// carry about 2^-44 relative accuracy: the float64 result, from float32
+// arithmetic.  c0 is an exact integer (G/2 - 4 or -4).
+__device__ __forceinline__ void tap_origin(float shi, float slo, float khi, float klo, float c0,
+                                           int& q, float& f) {
+  const float p = __fmul_rn(shi, khi);
+  const float e = __fmaf_rn(shi, khi, -p);
+  const float l = __fmaf_rn(shi, klo, __fmaf_rn(slo, khi, e));
+  const float A = __fadd_rn(c0, p);
+  const float bb = __fsub_rn(A, c0);
+  const float err = __fadd_rn(__fsub_rn(c0, __fsub_rn(A, bb)), __fsub_rn(p, bb));
+  const float L = __fadd_rn(l, err);
+  float qf = ceilf(A);
+  float fr = __fsub_rn(__fsub_rn(qf, A), L);
+  if (fr < 0.f) { qf += 1.f; fr += 1.f; }
+  else if (fr >= 1.f) { qf -= 1.f; fr -= 1.f; }
+  q = (int)qf;
+  f = fr;
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(kWarps * 32, 5)
+grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restrict__ kf,
+                   const void* __restrict__ vis, const float* __restrict__ chan_scale,
+                   const float* __restrict__ weight, const uint8_t* __restrict__ flag, int nbl,
+                   int nch, int npol, int G, float bl2, int run, int nseg,
+                   float2* __restrict__ H) {
+  const int warp = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= 2 * nbl * nseg) return;
+  // warps [0, nbl * nseg) walk the upper-half tracks, the rest their mirrors
+  // (most mirror warps exit at once, so they are kept out of the busy blocks)
+  const int seg = warp % nseg;
+  const int track = warp / nseg;
+  const int mirror = track >= nbl ? 1 : 0;
+  const int bl = track - mirror * nbl;
+  const TrackGeom t = track_geom(coef[bl], mirror);
+  const float2 kfirst = kf[0], klast = kf[nch - 1];
+  const double kf0 = (double)kfirst.x + (double)kfirst.y;
+  const double kf1 = (double)klast.x + (double)klast.y;
+  // the mirror track only reaches the stored rows when it passes within
+  // W/2 + 1 cells of k2' = 0
+  if (mirror && fabs(t.s2) * fmin(kf0, kf1) > 0.5 * kW + 1.0) return;
+  // a track far outside the grid (an oversized cell, reported by the plane
+  // fit) stores nothing
+  const double reach = fmax(fabs(t.s1), fabs(t.s2)) * fmax(kf0, kf1);
+  if (!(reach < 2.0 * G)) return;
+  const int c_begin = (seg * 32 + lane) * run;
+  const int c_end = min(nch, c_begin + run);
+  if (c_begin >= nch) return;
   int pa, pb;
   parallel_hands(npol, pa, pb);
-  const float inv_hw = 2.0f / kW;
-  for (int it = lo + warp; it < hi; it += kGridThreads / 32) {
-    const GridItem item = items[it];
-    const int ch = item.chunk * kChunk + lane;
-    if (ch >= nch) continue;
-    const int bl = item.track >> 1;
-    const size_t o = ((size_t)bl * nch + ch) * npol;
-    const bool fa = flag ? flag[o + pa] != 0 : false;
-    const bool fb = flag ? flag[o + pb] != 0 : false;
-    float wa = fa ? 0.f : (weight ? weight[o + pa] : 1.f);
-    float wb = fb ? 0.f : (weight ? weight[o + pb] : 1.f);
-    if (pa == pb) wb = 0.f;
-    if (!(wa + wb > 0.f)) continue;
-    const float sc = HALF ? chan_scale[ch] : 1.f;
-    const float2 va = load_vis<HALF>(vis, o + pa, sc);
-    float2 c = make_float2(wa * va.x, wa * va.y);
-    if (pa != pb) {
-      const float2 vb = load_vis<HALF>(vis, o + pb, sc);
-      c.x += wb * vb.x;
-      c.y += wb * vb.y;
-    }
-    const TrackGeom t = track_geom(coef[bl], item.track & 1);
-    if (t.conj) c.y = -c.y;
-    const double k = kch[ch];
-    const double g1 = 0.5 * G + t.s1 * k;
-    const double y = t.s2 * k;
-    const double kx0d = ceil(g1 - 0.5 * kW), ky0d = ceil(y - 0.5 * kW);
-    // a footprint entirely outside this tile contributes nothing (this also
-    // keeps the integer conversion below in range for far-away samples)
-    if (kx0d + (kW - 1) < x0 || kx0d > x0 + (kTile - 1) || ky0d + (kW - 1) < y0 ||
-        ky0d > y0 + (kTile - 1))
-      continue;
-    const float fx = (float)(kx0d - g1), fy = (float)(ky0d - y);
-    const int kx0 = (int)kx0d - x0, ky0 = (int)ky0d - y0;
-    float px[kW], py[kW];
+  const float s1hi = (float)t.s1, s1lo = (float)(t.s1 - (double)s1hi);
+  const float s2hi = (float)t.s2, s2lo = (float)(t.s2 - (double)s2hi);
+  const float cx = (float)(G / 2 - kW / 2), cy = (float)(-kW / 2);
+  const double dk = kf1 - kf0;
+  const int sx = (t.s1 * dk >= 0.0) ? 1 : -1;
+  const int sy = (t.s2 * dk >= 0.0) ? 1 : -1;
+
+  Window w;
 #pragma unroll
-    for (int i = 0; i < kW; ++i) {
-      px[i] = es_kernel(fx + (float)i, inv_hw, beta_es);
-      py[i] = es_kernel(fy + (float)i, inv_hw, beta_es);
-    }
+  for (int j = 0; j < kWin; ++j)
 #pragma unroll
-    for (int j = 0; j < kW; ++j) {
-      const int r = ky0 + j;
-      if (r < 0 || r >= kTile) continue;
-      const float2 cy = make_float2(c.x * py[j], c.y * py[j]);
-#pragma unroll
-      for (int i = 0; i < kW; ++i) {
-        const int col = kx0 + i;
-        if (col < 0 || col >= kTile) continue;
-        float2* cell = &acc[r * kTile + col];
-        atomicAdd(&cell->x, cy.x * px[i]);
-        atomicAdd(&cell->y, cy.y * px[i]);
+    for (int i = 0; i < kWin; ++i) w.a[j][i] = make_float2(0.f, 0.f);
+  int ox, oy;
+  {
+    const float2 k = kf[c_begin];
+    int qx, qy;
+    float f;
+    tap_origin(s1hi, s1lo, k.x, k.y, cx, qx, f);
+    tap_origin(s2hi, s2lo, k.x, k.y, cy, qy, f);
+    ox = sx > 0 ? qx : qx + kW - 1;
+    oy = sy > 0 ? qy : qy + kW - 1;
+  }
+  const size_t obase = (size_t)bl * nch * npol;
+  const Sample none{make_float2(0.f, 0.f), make_float2(0.f, 0.f), false};
+  // three samples in flight ahead of the one being gridded
+  Sample s0 = load_sample<HALF>(vis, chan_scale, weight, flag, kf, obase + (size_t)c_begin * npol,
+                                c_begin, npol, pa, pb);
+  Sample s1 = c_begin + 1 < c_end
+                  ? load_sample<HALF>(vis, chan_scale, weight, flag, kf,
+                                      obase + (size_t)(c_begin + 1) * npol, c_begin + 1, npol, pa, pb)
+                  : none;
+  Sample s2 = c_begin + 2 < c_end
+                  ? load_sample<HALF>(vis, chan_scale, weight, flag, kf,
+                                      obase + (size_t)(c_begin + 2) * npol, c_begin + 2, npol, pa, pb)
+                  : none;
+#pragma unroll 1
+  for (int ch = c_begin; ch < c_end; ++ch) {
+    const Sample s3 = ch + 3 < c_end
+                          ? load_sample<HALF>(vis, chan_scale, weight, flag, kf,
+                                              obase + (size_t)(ch + 3) * npol, ch + 3, npol, pa, pb)
+                          : none;
+    if (s0.sel) {
+      const float2 k = s0.k;
+      int kx0, ky0;
+      float fx, fy;
+      tap_origin(s1hi, s1lo, k.x, k.y, cx, kx0, fx);
+      tap_origin(s2hi, s2lo, k.x, k.y, cy, ky0, fy);
+      // footprint start in window coordinates and the offset of the window's
+      // first tap from the sample, in the direction of travel
+      int dx = sx > 0 ? kx0 - ox : ox - (kx0 + kW - 1);
+      int dy = sy > 0 ? ky0 - oy : oy - (ky0 + kW - 1);
+      const float fxs = sx > 0 ? fx - 0.5f * kW : fx + 0.5f * kW - 1.0f;
+      const float fys = sy > 0 ? fy - 0.5f * kW : fy + 0.5f * kW - 1.0f;
+      if (dx < 0 || dy < 0 || dx >= kWin || dy >= kWin) {
+        flush_all(w, H, G, ox, oy, sx, sy);
+        ox = sx > 0 ? kx0 : kx0 + kW - 1;
+        oy = sy > 0 ? ky0 : ky0 + kW - 1;
+        dx = 0;
+        dy = 0;
       }
+      while (dx > 0) { slide_x(w, H, G, ox, oy, sy); ox += sx; --dx; }
+      while (dy > 0) { slide_y(w, H, G, ox, oy, sx); oy += sy; --dy; }
+      float2 c = s0.c;
+      if (t.conj) c.y = -c.y;
+      const float fsx = (float)sx, fsy = (float)sy;
+      float px[kW];
+      float2 b[kW];
+#pragma unroll
+      for (int m = 0; m < kW; ++m) {
+        px[m] = es_kernel(fxs + fsx * (float)m, bl2);
+        const float py = es_kernel(fys + fsy * (float)m, bl2);
+        b[m] = make_float2(c.x * py, c.y * py);
+      }
+#pragma unroll
+      for (int j = 0; j < kWin; ++j)
+#pragma unroll
+        for (int i = 0; i < kWin; ++i) {
+          w.a[j][i].x = fmaf(px[i], b[j].x, w.a[j][i].x);
+          w.a[j][i].y = fmaf(px[i], b[j].y, w.a[j][i].y);
+        }
     }
+    s0 = s1;
+    s1 = s2;
+    s2 = s3;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kTile * kTile; i += kGridThreads) {
-    const int r = i / kTile, col = i % kTile;
-    H[(size_t)(y0 + r) * G + x0 + col] = acc[i];
-  }
+  flush_all(w, H, G, ox, oy, sx, sy);
 }
 
 }  // namespace
@@ -240,32 +327,28 @@ cudaError_t launch_grid(toi_plan_s* p, Slot& s, const double* freq, const void* 
                         const float* chan_scale, const float* weight, const uint8_t* flag,
                         int nbl, int nch) {
   (void)freq;
-  const int ntx = p->ntiles_x, nty = p->ntiles_y, nt = ntx * nty;
-  const int tok = prof_begin(p, PROF_BIN, 3);
-  cudaError_t e = cudaMemsetAsync(p->tile_count, 0, sizeof(int) * nt, p->stream);
+  const int G = p->G;
+  const int tok = prof_begin(p, PROF_GRID, 1);
+  cudaError_t e = cudaMemsetAsync(s.grid, 0, sizeof(float2) * (size_t)(G / 2) * G, p->stream);
   if (e != cudaSuccess) return e;
-  const int nchunk = (nch + kChunk - 1) / kChunk;
-  const long long nwork = (long long)2 * nbl * nchunk;
-  const int blocks = (int)((nwork + 255) / 256);
-  bin_count_kernel<<<blocks, 256, 0, p->stream>>>(s.coef, p->kch, nbl, nch, p->G, p->W, ntx, nty,
-                                                  p->tile_count);
-  bin_scan_kernel<<<1, 1024, 0, p->stream>>>(p->tile_count, nt, p->tile_offset, p->tile_cursor,
-                                             p->max_items, p->d_status);
-  bin_fill_kernel<<<blocks, 256, 0, p->stream>>>(s.coef, p->kch, nbl, nch, p->G, p->W, ntx, nty,
-                                                 p->tile_offset, p->tile_cursor, p->items,
-                                                 p->max_items);
-  prof_end(p, tok);
-  const int tok2 = prof_begin(p, PROF_GRID, 1);
+  // channel runs per lane: each track is split into segments of 32 lanes so
+  // that there are several warps per SM slot (runs of at least 16 channels)
+  int run = (nch + 63) / 64;
+  if (run < 16) run = 16;
+  const int nseg = (nch + 32 * run - 1) / (32 * run);
+  const long long nwarps = 2LL * nbl * nseg;
+  const int blocks = (int)((nwarps + kWarps - 1) / kWarps);
+  const float bl2 = (float)(p->beta_es * 1.4426950408889634);
   const bool half = p->cfg.vis_dtype == TOI_VIS_C16_CHANSCALE;
   if (half)
-    grid_tiles_kernel<true><<<nt, kGridThreads, 0, p->stream>>>(
-        s.coef, p->kch, vis, chan_scale, weight, flag, nch, p->cfg.n_pol, p->G,
-        (float)p->beta_es, p->tile_offset, p->items, p->max_items, ntx, s.grid);
+    grid_tracks_kernel<true><<<blocks, kWarps * 32, 0, p->stream>>>(
+        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, G, bl2, run, nseg,
+        s.grid);
   else
-    grid_tiles_kernel<false><<<nt, kGridThreads, 0, p->stream>>>(
-        s.coef, p->kch, vis, chan_scale, weight, flag, nch, p->cfg.n_pol, p->G,
-        (float)p->beta_es, p->tile_offset, p->items, p->max_items, ntx, s.grid);
-  prof_end(p, tok2);
+    grid_tracks_kernel<false><<<blocks, kWarps * 32, 0, p->stream>>>(
+        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, G, bl2, run, nseg,
+        s.grid);
+  prof_end(p, tok);
   return cudaGetLastError();
 }
 

@@ -37,34 +37,31 @@ __device__ void block_reduce(double (&v)[NV], double* sh) {
   __syncthreads();
 }
 
-// k = nu / c per channel, all-channel sums of k and k^2, monotonicity.
+// k = nu / c per channel, per-block sums of k and k^2, monotonicity.
 __global__ void prep_channels_kernel(const double* __restrict__ freq, int nch,
-                                     double* __restrict__ kch, double* __restrict__ ksum,
-                                     int* status) {
+                                     double* __restrict__ kch, float2* __restrict__ kf,
+                                     double* __restrict__ kpart, int* status) {
   __shared__ double sh[2 * 256];
+  const int c = blockIdx.x * 256 + threadIdx.x;
   double v[2] = {0.0, 0.0};
   bool bad = false;
-  const double f0 = freq[0];
-  const double dir = nch > 1 ? freq[nch - 1] - f0 : 1.0;
-  for (int c = threadIdx.x; c < nch; c += 256) {
+  if (c < nch) {
+    const double dir = nch > 1 ? freq[nch - 1] - freq[0] : 1.0;
     const double f = freq[c];
     const double k = f / kCLight;
     kch[c] = k;
-    v[0] = __dadd_rn(v[0], k);
-    v[1] = __dadd_rn(v[1], __dmul_rn(k, k));
+    const float hi = (float)k;
+    kf[c] = make_float2(hi, (float)(k - (double)hi));
+    v[0] = k;
+    v[1] = __dmul_rn(k, k);
     if (!(f > 0.0)) bad = true;
-    if (c + 1 < nch) {
-      const double d = freq[c + 1] - f;
-      if (!(d * dir > 0.0)) bad = true;
-    }
+    if (c + 1 < nch && !((freq[c + 1] - f) * dir > 0.0)) bad = true;
   }
   if (bad) set_status(status, TOI_DEV_RANGE);
   block_reduce<256, 2>(v, sh);
   if (threadIdx.x == 0) {
-    ksum[0] = v[0];
-    ksum[1] = v[1];
-    const double ka = freq[0] / kCLight, kb = freq[nch - 1] / kCLight;
-    ksum[2] = ka > kb ? ka : kb;
+    kpart[2 * blockIdx.x] = v[0];
+    kpart[2 * blockIdx.x + 1] = v[1];
   }
 }
 
@@ -158,15 +155,23 @@ __device__ void jacobi3(double a[3][3], double e[3][3]) {
 }
 
 __global__ void prep_finalize_kernel(const double* __restrict__ uvw, int nbl, int nch,
-                                     const double* __restrict__ ksum,
-                                     const BaselineMoments* __restrict__ mom, double beta_rad,
-                                     int G, int W, double* __restrict__ snap,
-                                     BaselineCoef* __restrict__ coef, int* status) {
+                                     const double* __restrict__ kpart, int nkblk,
+                                     const BaselineMoments* __restrict__ mom,
+                                     double* __restrict__ snap, int* status) {
   constexpr int NT = 256;
   __shared__ double sh[11 * NT];
-  __shared__ double Vs[9];
-  __shared__ int empty;
-  const double skall = ksum[0], sk2all = ksum[1];
+  __shared__ double ks[2];
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nkblk; ++i) {
+      a = __dadd_rn(a, kpart[2 * i]);
+      b = __dadd_rn(b, kpart[2 * i + 1]);
+    }
+    ks[0] = a;
+    ks[1] = b;
+  }
+  __syncthreads();
+  const double skall = ks[0], sk2all = ks[1];
   double v[11];
   for (int i = 0; i < 11; ++i) v[i] = 0.0;
   for (int b = threadIdx.x; b < nbl; b += NT) {
@@ -184,7 +189,7 @@ __global__ void prep_finalize_kernel(const double* __restrict__ uvw, int nbl, in
   block_reduce<NT, 11>(v, sh);
   if (threadIdx.x == 0) {
     const double N = v[0];
-    empty = (N <= 0.0 || v[10] <= 0.0) ? 1 : 0;
+    const int empty = (N <= 0.0 || v[10] <= 0.0) ? 1 : 0;
     double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     if (!empty) {
       const double m1[3] = {v[1], v[2], v[3]};
@@ -226,7 +231,7 @@ __global__ void prep_finalize_kernel(const double* __restrict__ uvw, int nbl, in
       set_status(status, TOI_DEV_EMPTY);
     }
     for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) { snap[SNAP_V + 3 * i + j] = V[i][j]; Vs[3 * i + j] = V[i][j]; }
+      for (int j = 0; j < 3; ++j) snap[SNAP_V + 3 * i + j] = V[i][j];
     snap[SNAP_OMEGA] = fabs(V[0][0] * V[1][1] - V[1][0] * V[0][1]);
     snap[SNAP_XI] = V[2][0] / V[2][2];
     snap[SNAP_ETA] = V[2][1] / V[2][2];
@@ -235,37 +240,50 @@ __global__ void prep_finalize_kernel(const double* __restrict__ uvw, int nbl, in
     snap[14] = 0.0;
     snap[15] = 0.0;
   }
-  __syncthreads();
-  const double kmax = ksum[2];
+}
+
+// Per baseline: R = V uvw (float64), grid coefficients a1 = -r1 beta G,
+// a2 = r2 beta G, and the check that every footprint stays on the grid.
+__global__ void prep_coef_kernel(const double* __restrict__ uvw, int nbl, int nch,
+                                 const double* __restrict__ kch, const double* __restrict__ snap,
+                                 double beta_rad, int G, int W, BaselineCoef* __restrict__ coef,
+                                 int* status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbl) return;
+  double Vs[9];
+  for (int i = 0; i < 9; ++i) Vs[i] = snap[SNAP_V + i];
+  const bool empty = !(snap[SNAP_SUMW] > 0.0);
+  const double kmax = fmax(kch[0], kch[nch - 1]);
   const double lim = 0.5 * G - 0.5 * W;
   const double scale = beta_rad * (double)G;
-  bool bad = false;
-  for (int b = threadIdx.x; b < nbl; b += NT) {
-    const double x = uvw[3 * b], y = uvw[3 * b + 1], z = uvw[3 * b + 2];
-    const double r1 = Vs[0] * x + Vs[1] * y + Vs[2] * z;
-    const double r2 = Vs[3] * x + Vs[4] * y + Vs[5] * z;
-    const double r3 = Vs[6] * x + Vs[7] * y + Vs[8] * z;
-    BaselineCoef cf;
-    cf.a1 = empty ? 0.0 : -r1 * scale;
-    cf.a2 = empty ? 0.0 : r2 * scale;
-    cf.r3 = r3;
-    cf.pad = 0.0;
-    coef[b] = cf;
-    if (fabs(cf.a1) * kmax > lim || fabs(cf.a2) * kmax > lim) bad = true;
-  }
-  if (bad) set_status(status, TOI_DEV_RANGE);
+  const double x = uvw[3 * b], y = uvw[3 * b + 1], z = uvw[3 * b + 2];
+  const double r1 = Vs[0] * x + Vs[1] * y + Vs[2] * z;
+  const double r2 = Vs[3] * x + Vs[4] * y + Vs[5] * z;
+  const double r3 = Vs[6] * x + Vs[7] * y + Vs[8] * z;
+  BaselineCoef cf;
+  cf.a1 = empty ? 0.0 : -r1 * scale;
+  cf.a2 = empty ? 0.0 : r2 * scale;
+  cf.r3 = r3;
+  cf.pad = 0.0;
+  coef[b] = cf;
+  if (fabs(cf.a1) * kmax > lim || fabs(cf.a2) * kmax > lim) set_status(status, TOI_DEV_RANGE);
 }
 
 }  // namespace
 
 cudaError_t launch_prep(toi_plan_s* p, Slot& s, const double* uvw, const double* freq,
                         const float* weight, const uint8_t* flag, int nbl, int nch) {
-  const int tok = prof_begin(p, PROF_PREP, 3);
-  prep_channels_kernel<<<1, 256, 0, p->stream>>>(freq, nch, p->kch, p->kch_sum, p->d_status);
+  const int tok = prof_begin(p, PROF_PREP, 4);
+  const int nkblk = (nch + 255) / 256;
+  prep_channels_kernel<<<nkblk, 256, 0, p->stream>>>(freq, nch, p->kch, p->kf, p->kch_sum,
+                                                     p->d_status);
   prep_baselines_kernel<<<nbl, kPrepThreads, 0, p->stream>>>(flag, weight, p->kch, nch,
                                                              p->cfg.n_pol, p->mom);
-  prep_finalize_kernel<<<1, 256, 0, p->stream>>>(uvw, nbl, nch, p->kch_sum, p->mom, p->beta_rad,
-                                                 p->G, p->W, s.snap, s.coef, p->d_status);
+  prep_finalize_kernel<<<1, 256, 0, p->stream>>>(uvw, nbl, nch, p->kch_sum, nkblk, p->mom, s.snap,
+                                                 p->d_status);
+  prep_coef_kernel<<<(nbl + 127) / 128, 128, 0, p->stream>>>(uvw, nbl, nch, p->kch, s.snap,
+                                                             p->beta_rad, p->G, p->W, s.coef,
+                                                             p->d_status);
   prof_end(p, tok);
   return cudaGetLastError();
 }

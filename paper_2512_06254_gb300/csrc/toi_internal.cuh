@@ -14,13 +14,6 @@ namespace toi {
 constexpr double kCLight = 299792458.0;
 constexpr double kArcsec = 3.14159265358979323846 / 648000.0;
 
-// Gridding tiles: the half-plane grid (G/2 rows x G columns) is split into
-// kTile x kTile tiles; one CTA owns one tile.
-constexpr int kTile = 64;
-// Channels per gridding work item (one warp-sized chunk of one track).
-constexpr int kChunk = 32;
-// Upper bound on work items per (track, chunk) used to size the bin store.
-constexpr int kItemsPerChunk = 8;
 
 // Layout of the per-slot snapshot record (float64).
 enum SnapField {
@@ -47,11 +40,6 @@ struct BaselineMoments {
   long long ndesel;   // number of deselected channels
 };
 
-struct GridItem {
-  int track;   // 2 * baseline + (0: upper half-plane track, 1: its mirror)
-  int chunk;   // channel chunk index (kChunk channels)
-};
-
 struct Slot {
   float2* grid = nullptr;          // [G/2][G] Hermitian half-plane grid
   double* snap = nullptr;          // [SNAP_LEN]
@@ -69,6 +57,7 @@ struct Slot {
 
 // Per-stage device-time accounting with CUDA events on the plan's stream.
 enum ProfStage {
+  // PROF_BIN is reserved (the gridder needs no binning pass)
   PROF_PREP = 0, PROF_BIN, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_REPROJECT,
   PROF_TLISI, PROF_NSTAGE
 };
@@ -95,14 +84,9 @@ struct toi_plan_s {
   toi::Slot* slots = nullptr;
   // shared scratch
   double* kch = nullptr;                 // [max_ch] k = nu / c
-  double* kch_sum = nullptr;             // [4]: sum k, sum k^2 over all channels, kmax
+  float2* kf = nullptr;                  // [max_ch] k as an unevaluated float sum hi + lo
+  double* kch_sum = nullptr;             // [2 * ceil(max_ch / 256)] per-block sums of k, k^2
   toi::BaselineMoments* mom = nullptr;   // [max_bl]
-  int* tile_count = nullptr;             // [ntiles]
-  int* tile_offset = nullptr;            // [ntiles + 1]
-  int* tile_cursor = nullptr;            // [ntiles]
-  toi::GridItem* items = nullptr;        // [max_items]
-  int max_items = 0;
-  int ntiles_x = 0, ntiles_y = 0;
   float2* twiddle = nullptr;             // [G] exp(+2 pi i k / G)
   float* corr = nullptr;                 // [N] 1 / psi_hat((j - N/2) / G)
   float2* fft_tmp = nullptr;             // [G/2][N] rows after pass 1
@@ -133,7 +117,7 @@ cudaError_t launch_fft(toi_plan_s* p, Slot& s);
 cudaError_t launch_reproject_moments(toi_plan_s* p, Slot& s, float* image_out,
                                      bool with_moments, int cur, int prev1, int prev2);
 cudaError_t launch_ring_moments(toi_plan_s* p, const float* image, int cur, int prev1,
-                                int prev2);
+                                int prev2, bool with_moments);
 cudaError_t launch_tlisi_finalize(toi_plan_s* p, float* tlisi, int cur, int prev1, int prev2);
 
 // host-side constant tables (api.cu)
