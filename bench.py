@@ -5,8 +5,8 @@ One step = one observation of 1500 snapshots (2016 baselines x 4096 channels
 x 4 pols, 2048^2 image, 8 s dumps): for every snapshot the plane fit,
 gridding, inverse FFT, grid correction, re-projection and tLISI (S1-S7),
 then the periodic candidate search over the 1498-slice tLISI cube (S8).
-Inputs are seeded synthetic snapshots resident in HBM (a pool of 120
-distinct snapshots = 3 pulsar periods, each 297 MB, larger than L2); the
+Inputs are seeded synthetic snapshots resident in HBM (a pool of 40
+distinct snapshots = one pulsar period, each 297 MB, larger than L2); the
 metric is snapshots/s.  See the design doc for the roofline model.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]

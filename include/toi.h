@@ -128,7 +128,9 @@ toi_status toi_grid(toi_plan_t plan, const double* uvw_m, const double* freq_hz,
  * standard plane by bilinear interpolation (pixels whose source is outside
  * the tilted image are 0).  The result becomes the newest image of the
  * plan's ring; it is also written to `image` (dev float32 [N][N]) unless
- * image is NULL.  snap_info (dev float64 [16] or NULL) receives V (9, row
+ * image is NULL.  The call consumes the slot's grid (it is cleared while
+ * being transformed): imaging a slot again needs a new toi_grid, and
+ * gridding a slot that has not been imaged starts it from zero.  snap_info (dev float64 [16] or NULL) receives V (9, row
  * major), omega, xi, eta, sum_w, n_vis, 0, 0.  Per-tile tLISI moments of the
  * three youngest ring images are computed in the same pass. */
 toi_status toi_image(toi_plan_t plan, int32_t slot, float* image,

@@ -111,7 +111,7 @@ void free_plan(toi_plan_s* p) {
     }
     delete[] p->slots;
   }
-  cudaFree(p->kch); cudaFree(p->kf); cudaFree(p->kch_sum); cudaFree(p->mom);
+  cudaFree(p->kch); cudaFree(p->kf); cudaFree(p->kch_sum); cudaFree(p->bpart);
   cudaFree(p->twiddle); cudaFree(p->corr); cudaFree(p->fft_tmp);
   cudaFree(p->tilted);
   for (int i = 0; i < 3; ++i) cudaFree(p->ring[i]);
@@ -216,7 +216,7 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   TOI_ALLOC(p->kch, (size_t)c.max_channels, "channel table");
   TOI_ALLOC(p->kf, (size_t)c.max_channels, "channel table (float pairs)");
   TOI_ALLOC(p->kch_sum, 2 * ((size_t)c.max_channels + 255) / 256 + 2, "channel sums");
-  TOI_ALLOC(p->mom, (size_t)c.max_baselines, "baseline moments");
+  TOI_ALLOC(p->bpart, 11 * (((size_t)c.max_baselines + 7) / 8), "plane-fit partial sums");
   TOI_ALLOC(p->twiddle, (size_t)G, "FFT twiddles");
   TOI_ALLOC(p->corr, (size_t)N, "grid correction");
   TOI_ALLOC(p->fft_tmp, (size_t)(G / 2) * N, "FFT intermediate");
@@ -242,6 +242,8 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->ring_max, 0, 3 * sizeof(unsigned int));
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemset(p->ring[i], 0, sizeof(float) * N * N);
+  for (int i = 0; i < p->nslot && e == cudaSuccess; ++i)
+    e = cudaMemset(p->slots[i].grid, 0, sizeof(float2) * (size_t)(G / 2) * G);
   if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "initialising plan tables"); free_plan(p); return r; }
   *out = p;
   return TOI_OK;
@@ -278,7 +280,12 @@ toi_status toi_grid(toi_plan_t p, const double* uvw_m, const double* freq_hz, co
       (p->cfg.n_pol == 4 && ((uintptr_t)flag & 3)))
     return fail(p, TOI_ERR_ARG, "misaligned input pointer (element alignment; flags of 4 pols: 4 bytes)");
   Slot& s = p->slots[slot];
-  cudaError_t e = toi::launch_prep(p, s, uvw_m, freq_hz, weight, flag, n_bl, n_ch);
+  cudaError_t e;
+  if (s.valid) {   // re-gridded before being imaged: start from zero again
+    e = cudaMemsetAsync(s.grid, 0, sizeof(float2) * (size_t)(p->G / 2) * p->G, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "toi_grid/clear");
+  }
+  e = toi::launch_prep(p, s, uvw_m, freq_hz, weight, flag, n_bl, n_ch);
   if (e != cudaSuccess) return cuda_fail(p, e, "toi_grid/prep");
   e = toi::launch_grid(p, s, freq_hz, vis, chan_scale, weight, flag, n_bl, n_ch);
   if (e != cudaSuccess) return cuda_fail(p, e, "toi_grid/grid");
@@ -291,9 +298,10 @@ toi_status toi_image(toi_plan_t p, int32_t slot, float* image, double* snap_info
   if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
   if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
   Slot& s = p->slots[slot];
-  if (!s.valid) return fail(p, TOI_ERR_ARG, "slot has not been gridded");
+  if (!s.valid) return fail(p, TOI_ERR_ARG, "slot has not been gridded since its last toi_image");
   cudaError_t e = toi::launch_fft(p, s);
   if (e != cudaSuccess) return cuda_fail(p, e, "toi_image/fft");
+  s.valid = false;   // the row pass consumed (and cleared) the grid
   const int cur = (int)(p->nimg % 3);
   const int prev1 = (int)((p->nimg + 2) % 3), prev2 = (int)((p->nimg + 1) % 3);
   e = toi::launch_reproject_moments(p, s, image, p->nimg >= 2, cur, prev1, prev2);
@@ -380,7 +388,7 @@ toi_status toi_degrid_backward(toi_plan_t p, int32_t slot, const float* grad_ima
   if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
   if (!grad_image || !grad_sample) return fail(p, TOI_ERR_ARG, "grad_image and grad_sample must be non-NULL");
   Slot& s = p->slots[slot];
-  if (!s.valid) return fail(p, TOI_ERR_ARG, "slot has not been gridded");
+  if (!s.uvw) return fail(p, TOI_ERR_ARG, "slot has not been gridded");
   cudaError_t e = toi::launch_degrid_backward(p, s, grad_image, grad_sample, grad_weight);
   if (e == cudaErrorNotSupported) return fail(p, TOI_ERR_UNSUPPORTED, "toi_degrid_backward not available");
   if (e != cudaSuccess) return cuda_fail(p, e, "toi_degrid_backward");

@@ -8,18 +8,28 @@
 // stored as H = G + conj(G(-k)), hence the 1/2).
 //   Pass 1 (rows, along k1'): T[k2', j1'] = sum_{k1'} H[k2', k1'] e^{..}; only
 //            the N central j1' are written, as (-1)^j1' Z[j1' mod G] of the
-//            plain inverse DFT Z of the row.
-//   Pass 2 (columns, along k2'): the column sequence is Hermitian in k2', so
-//            the full length-G sequence is rebuilt in shared memory from the
-//            stored half, transformed, and 1/2 Re of the N central outputs is
-//            multiplied by 1/psi_hat(j1') 1/psi_hat(j2') / (omega sum w).
+//            plain inverse DFT Z of the row.  Rows beyond the last one any
+//            footprint reached are zero and skipped (input pruning); each row
+//            read is cleared in the grid, which leaves the slot zeroed for the
+//            next gridding.
+//   Pass 2 (columns, along k2'): each column sequence is Hermitian in k2', so
+//            its transform is real; two columns a, b are transformed together
+//            as Z = U_a + i U_b (Re -> column a, Im -> column b), rebuilt over
+//            the full length G from the stored half.  1/2 of the N central
+//            outputs is multiplied by 1/psi_hat(j1') 1/psi_hat(j2') /
+//            (omega sum w).
 // Each transform is a Stockham autosort FFT in shared memory: radix-8 passes
-// (then one radix-4 or radix-2 pass) whose butterflies run in registers, with
-// float32 twiddles e^{+2 pi i m / G} tabulated in float64 at plan time.
+// (then one radix-4 or radix-2 pass) whose butterflies run in registers,
+// twiddles from a float32 table e^{+2 pi i m / G} made in float64 at plan time
+// (three table reads per radix-8 butterfly, the other powers by products).
+// Shared memory is padded by one slot per eight to avoid bank conflicts of
+// the strided Stockham stores.
 #include "toi_internal.cuh"
 
 namespace toi {
 namespace {
+
+__device__ __forceinline__ int pad(int a) { return a + (a >> 3); }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -57,7 +67,6 @@ __device__ __forceinline__ void dft8(float2* v) {
   t[5] = make_float2(r * (t[5].x - t[5].y), r * (t[5].x + t[5].y));    // * (1+i)/sqrt2
   t[6] = cmuli(t[6]);                                                  // * i
   t[7] = make_float2(-r * (t[7].x + t[7].y), r * (t[7].x - t[7].y));   // * (-1+i)/sqrt2
-  // two 4-point transforms on the halves; results in bit-reversed order
   float2 a[4] = {t[0], t[1], t[2], t[3]};
   float2 b[4] = {t[4], t[5], t[6], t[7]};
   dft4(a);
@@ -73,12 +82,31 @@ __device__ __forceinline__ void dftR(float2* v) {
   else dft2(v);
 }
 
-// One Stockham pass of radix R over `nseq` sequences of length G in shared
-// memory (in place: all loads, barrier, all stores, barrier).  BPT =
-// butterflies per thread = nseq * G / R / blockDim.x.
+// twiddle powers w^r, r = 1..R-1, with w = e^{+2 pi i step / G}
+template <int R>
+__device__ __forceinline__ void twiddles(const float2* __restrict__ tw, int step, float2* w) {
+  if (R == 8) {
+    const float2 w1 = __ldg(tw + step), w2 = __ldg(tw + 2 * step), w4 = __ldg(tw + 4 * step);
+    w[1] = w1; w[2] = w2; w[4] = w4;
+    w[3] = cmul(w2, w1);
+    w[5] = cmul(w4, w1);
+    w[6] = cmul(w4, w2);
+    w[7] = cmul(w4, w[3]);
+  } else if (R == 4) {
+    const float2 w1 = __ldg(tw + step), w2 = __ldg(tw + 2 * step);
+    w[1] = w1; w[2] = w2;
+    w[3] = cmul(w2, w1);
+  } else {
+    w[1] = __ldg(tw + step);
+  }
+}
+
+// One Stockham pass of radix R over `nseq` padded sequences of length G in
+// shared memory (in place: all loads, barrier, all stores, barrier).
 template <int G, int R, int BPT>
 __device__ __forceinline__ void stockham_pass(float2* x, int nseq, int Ns, const float2* __restrict__ tw) {
-  constexpr int NB = G / R;   // butterflies per sequence
+  constexpr int NB = G / R;       // butterflies per sequence
+  constexpr int LEN = G + G / 8;  // padded sequence length
   float2 v[BPT][R];
   int jj[BPT], ss[BPT];
 #pragma unroll
@@ -88,14 +116,15 @@ __device__ __forceinline__ void stockham_pass(float2* x, int nseq, int Ns, const
     jj[b] = j;
     ss[b] = seq;
     if (seq < nseq) {
-      const float2* xs = x + (size_t)seq * G;
+      const float2* xs = x + (size_t)seq * LEN;
       const int k = j & (Ns - 1);
-      const int step = (G / (Ns * R)) * k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float2 val = xs[j + r * NB];
-        if (r > 0 && k > 0) val = cmul(val, __ldg(tw + step * r));
-        v[b][r] = val;
+      for (int r = 0; r < R; ++r) v[b][r] = xs[pad(j + r * NB)];
+      if (k > 0) {
+        float2 w[R];
+        twiddles<R>(tw, (G / (Ns * R)) * k, w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
       }
       dftR<R>(v[b]);
     }
@@ -104,12 +133,12 @@ __device__ __forceinline__ void stockham_pass(float2* x, int nseq, int Ns, const
 #pragma unroll
   for (int b = 0; b < BPT; ++b) {
     if (ss[b] < nseq) {
-      float2* xs = x + (size_t)ss[b] * G;
+      float2* xs = x + (size_t)ss[b] * LEN;
       const int j = jj[b];
       const int k = j & (Ns - 1);
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) xs[base + r * Ns] = v[b][r];
+      for (int r = 0; r < R; ++r) xs[pad(base + r * Ns)] = v[b][r];
     }
   }
   __syncthreads();
@@ -137,6 +166,11 @@ __device__ __forceinline__ void fft_smem(float2* x, const float2* __restrict__ t
   }
 }
 
+__device__ __forceinline__ int row_limit(const double* snap, int G) {
+  const int r = (int)ceil(snap[SNAP_ROWMAX]);
+  return r < G / 2 ? r : G / 2 - 1;
+}
+
 template <int G>
 struct RowCfg {
   static constexpr int NT = (G / 8 < 64) ? 64 : (G / 8 > 512 ? 512 : G / 8);
@@ -144,27 +178,42 @@ struct RowCfg {
 
 template <int G>
 __global__ void __launch_bounds__(RowCfg<G>::NT)
-fft_rows_kernel(const float2* __restrict__ H, int N, const float2* __restrict__ tw,
-                float2* __restrict__ T) {
+fft_rows_kernel(float2* __restrict__ H, int N, const float2* __restrict__ tw,
+                const double* __restrict__ snap, float2* __restrict__ T) {
   extern __shared__ float2 x[];
   const int row = blockIdx.x;
-  const float2* src = H + (size_t)row * G;
-  for (int n = threadIdx.x; n < G; n += blockDim.x) x[n] = src[n];
+  if (row > row_limit(snap, G)) return;
+  float2* src = H + (size_t)row * G;
+  constexpr int PER = (G + RowCfg<G>::NT - 1) / RowCfg<G>::NT;
+  float2 v[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {   // all loads first, then the stores
+    const int n = threadIdx.x + u * RowCfg<G>::NT;
+    v[u] = n < G ? src[n] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int n = threadIdx.x + u * RowCfg<G>::NT;
+    if (n < G) x[pad(n)] = v[u];
+  }
   __syncthreads();
   fft_smem<G, 1, RowCfg<G>::NT>(x, tw);
   float2* dst = T + (size_t)row * N;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
     const int jp = j - N / 2;
-    float2 v = x[jp < 0 ? jp + G : jp];
+    float2 v = x[pad(jp < 0 ? jp + G : jp)];
     if (jp & 1) { v.x = -v.x; v.y = -v.y; }
     dst[j] = v;
   }
+  // leave the grid slot cleared for the next gridding
+  for (int n = threadIdx.x; n < G; n += blockDim.x) src[n] = make_float2(0.f, 0.f);
 }
 
 template <int G>
 struct ColCfg {
-  static constexpr int CW = (G >= 8192) ? 2 : 4;
+  static constexpr int CW = 4;            // columns per block: two complex transforms
   static constexpr int NT = 512;
+  static constexpr int LEN = G + G / 8;
 };
 
 template <int G>
@@ -172,49 +221,63 @@ __global__ void __launch_bounds__(ColCfg<G>::NT)
 fft_cols_kernel(const float2* __restrict__ T, int N, const float2* __restrict__ tw,
                 const float* __restrict__ corr, const double* __restrict__ snap,
                 float* __restrict__ out) {
-  constexpr int CW = ColCfg<G>::CW;
+  constexpr int CW = ColCfg<G>::CW, LEN = ColCfg<G>::LEN;
   extern __shared__ float2 x[];
   const int col0 = blockIdx.x * CW;
   constexpr int half = G / 2;
-  for (int e = threadIdx.x; e < half * CW; e += blockDim.x) {
-    const int r = e / CW, c = e - r * CW;
-    const float2 v = T[(size_t)r * N + col0 + c];
-    float2* xs = x + (size_t)c * G;
-    xs[r] = v;
-    if (r > 0) xs[G - r] = make_float2(v.x, -v.y);
-    else xs[half] = make_float2(0.f, 0.f);
+  const int rmax = row_limit(snap, G);
+  for (int e = threadIdx.x; e < half * 2; e += blockDim.x) {
+    const int r = e >> 1, pr = e & 1;     // row, column pair
+    float2* xs = x + (size_t)pr * LEN;
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+    if (r <= rmax) {
+      const float4 ab = *reinterpret_cast<const float4*>(T + (size_t)r * N + col0 + 2 * pr);
+      a = make_float2(ab.x, ab.y);
+      b = make_float2(ab.z, ab.w);
+    }
+    // Z[r] = U_a[r] + i U_b[r];  Z[-r] = conj(U_a[r]) + i conj(U_b[r])
+    xs[pad(r)] = make_float2(a.x - b.y, a.y + b.x);
+    if (r > 0) xs[pad(G - r)] = make_float2(a.x + b.y, b.x - a.y);
+    else xs[pad(half)] = make_float2(0.f, 0.f);
   }
   __syncthreads();
-  fft_smem<G, CW, ColCfg<G>::NT>(x, tw);
+  fft_smem<G, 2, ColCfg<G>::NT>(x, tw);
   const double omega = snap[SNAP_OMEGA], sumw = snap[SNAP_SUMW];
   const float norm = sumw > 0.0 ? (float)(0.5 / (omega * sumw)) : 0.f;
-  for (int e = threadIdx.x; e < N * CW; e += blockDim.x) {
-    const int j2 = e / CW, c = e - j2 * CW;
+  const float ca = corr[col0], cb = corr[col0 + 1], cc = corr[col0 + 2], cd = corr[col0 + 3];
+  for (int j2 = threadIdx.x; j2 < N; j2 += blockDim.x) {
     const int jp = j2 - N / 2;
-    const float v = x[(size_t)c * G + (jp < 0 ? jp + G : jp)].x;
-    out[(size_t)j2 * N + col0 + c] = v * (norm * corr[col0 + c] * corr[j2]);
+    const int m = pad(jp < 0 ? jp + G : jp);
+    const float2 z0 = x[m], z1 = x[LEN + m];
+    const float s = norm * corr[j2];
+    float4 o;
+    o.x = z0.x * (s * ca);
+    o.y = z0.y * (s * cb);
+    o.z = z1.x * (s * cc);
+    o.w = z1.y * (s * cd);
+    *reinterpret_cast<float4*>(out + (size_t)j2 * N + col0) = o;
   }
 }
 
 template <int G>
 cudaError_t configure_g() {
   cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       G * (int)sizeof(float2));
+                                       (G + G / 8) * (int)sizeof(float2));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(fft_cols_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              ColCfg<G>::CW * G * (int)sizeof(float2));
+                              2 * ColCfg<G>::LEN * (int)sizeof(float2));
 }
 
 template <int G>
 void launch_g(toi_plan_s* p, Slot& s) {
   const int N = p->N;
   int tok = prof_begin(p, PROF_FFT_ROWS, 1);
-  fft_rows_kernel<G><<<G / 2, RowCfg<G>::NT, G * sizeof(float2), p->stream>>>(s.grid, N, p->twiddle,
-                                                                             p->fft_tmp);
+  fft_rows_kernel<G><<<G / 2, RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
+      s.grid, N, p->twiddle, s.snap, p->fft_tmp);
   prof_end(p, tok);
   tok = prof_begin(p, PROF_FFT_COLS, 1);
   constexpr int CW = ColCfg<G>::CW;
-  fft_cols_kernel<G><<<N / CW, ColCfg<G>::NT, CW * G * sizeof(float2), p->stream>>>(
+  fft_cols_kernel<G><<<N / CW, ColCfg<G>::NT, 2 * ColCfg<G>::LEN * sizeof(float2), p->stream>>>(
       p->fft_tmp, N, p->twiddle, p->corr, s.snap, p->tilted);
   prof_end(p, tok);
 }

@@ -27,18 +27,23 @@ namespace {
 
 constexpr int kFinThreads = 256;
 
-template <int NT, int NV>
-__device__ void block_reduce_d(double (&v)[NV], double* sh) {
-  for (int i = 0; i < NV; ++i) sh[i * NT + threadIdx.x] = v[i];
+// Fixed-order block reduction: float32 warp shuffles (32 lanes x 4 pixels),
+// then the eight warp totals in float64, in warp order.
+template <int NV>
+__device__ void block_reduce_d(float (&v)[NV], double (*sh)[NV], double (&out)[NV]) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+  if (lane == 0)
+    for (int i = 0; i < NV; ++i) sh[wib][i] = (double)v[i];
   __syncthreads();
-  for (int s = NT / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s)
-      for (int i = 0; i < NV; ++i)
-        sh[i * NT + threadIdx.x] = sh[i * NT + threadIdx.x] + sh[i * NT + threadIdx.x + s];
-    __syncthreads();
-  }
-  for (int i = 0; i < NV; ++i) v[i] = sh[i * NT];
-  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NV; ++i) {
+      double a = 0.0;
+      for (int wdx = 0; wdx < kFinThreads / 32; ++wdx) a += sh[wdx][i];
+      out[i] = a;
+    }
 }
 
 template <bool REPRO>
@@ -48,7 +53,7 @@ image_tile_kernel(const float* __restrict__ src, int N, int T, const double* __r
                   const float* __restrict__ ring_p1, const float* __restrict__ ring_p2,
                   float* __restrict__ image_out, int with_moments,
                   double* __restrict__ tile_mom, unsigned int* __restrict__ max_cur) {
-  __shared__ double sh[5 * kFinThreads];
+  __shared__ double sh[kFinThreads / 32][5];
   __shared__ float kk[3];
   __shared__ unsigned int smax;
   const int ntx = N / T;
@@ -75,7 +80,9 @@ image_tile_kernel(const float* __restrict__ src, int N, int T, const double* __r
       for (int it = 0; it < 3; ++it) {
         const float u1 = D1 + e1, u2 = D2 + e2;
         const float q = b2 * (u1 * u1 + u2 * u2);
-        const float z = q / (1.0f + sqrtf(1.0f - q));
+        float rt;
+        asm("sqrt.approx.f32 %0, %1;" : "=f"(rt) : "f"(1.0f - q));
+        const float z = __fdividef(q, 1.0f + rt);
         e1 = -K1 * z;
         e2 = -K2 * z;
       }
@@ -112,8 +119,9 @@ image_tile_kernel(const float* __restrict__ src, int N, int T, const double* __r
   // order-free max of |I| (float bits of non-negative floats order like ints)
   atomicMax(&smax, __float_as_uint(mx));
   if (with_moments) {
-    double v5[5] = {sa, sb, saa, sbb, sab};
-    block_reduce_d<kFinThreads, 5>(v5, sh);
+    float f5[5] = {sa, sb, saa, sbb, sab};
+    double v5[5];
+    block_reduce_d<5>(f5, sh, v5);
     if (threadIdx.x == 0)
       for (int i = 0; i < 5; ++i) tile_mom[(size_t)blockIdx.x * 5 + i] = v5[i];
   } else {

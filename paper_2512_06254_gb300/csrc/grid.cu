@@ -20,8 +20,8 @@
 // W^2 per sample; the 67 MB
 // half-plane grid of a 2048^2 image stays resident in L2 for these
 // reductions, and the streamed visibilities are read with evict-first loads.
-// The grid is cleared before gridding.  Cell sums are exact up to float32
-// rounding order (the reductions commute).
+// The grid starts from zero (the FFT row pass clears what it reads).  Cell
+// sums are exact up to float32 rounding order (the reductions commute).
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -201,14 +201,103 @@ __device__ __forceinline__ void tap_origin(float shi, float slo, float khi, floa
   f = fr;
 }
 
+// Coordinates and kernel values of one sample, ready to be accumulated.
+struct Prepared {
+  float px[kW];    // x taps in the direction of travel
+  float2 b[kW];    // c * y taps in the direction of travel
+  int kx0, ky0;    // first tap (absolute grid index) on each axis
+};
+
+__device__ __forceinline__ void prepare(const Sample& s, float s1hi, float s1lo, float s2hi,
+                                        float s2lo, float cx, float cy, int sx, int sy, bool conj,
+                                        float bl2, Prepared& p) {
+  float fx, fy;
+  tap_origin(s1hi, s1lo, s.k.x, s.k.y, cx, p.kx0, fx);
+  tap_origin(s2hi, s2lo, s.k.x, s.k.y, cy, p.ky0, fy);
+  // offset of the first tap in the direction of travel from the sample
+  const float fxs = sx > 0 ? fx - 0.5f * kW : fx + 0.5f * kW - 1.0f;
+  const float fys = sy > 0 ? fy - 0.5f * kW : fy + 0.5f * kW - 1.0f;
+  const float fsx = (float)sx, fsy = (float)sy;
+  float2 c = s.sel ? s.c : make_float2(0.f, 0.f);
+  if (conj) c.y = -c.y;
+#pragma unroll
+  for (int m = 0; m < kW; ++m) {
+    p.px[m] = es_kernel(fxs + fsx * (float)m, bl2);
+    const float py = es_kernel(fys + fsy * (float)m, bl2);
+    p.b[m] = make_float2(c.x * py, c.y * py);
+  }
+}
+
+// Per-lane shared-memory staging of the visibility stream: each lane keeps
+// two stages of kStage samples in flight with cp.async (completion tracked by
+// async-copy groups, so no register waits on outstanding loads).
+constexpr int kStage = 8;
+
+// Stage layout (per warp, struct of arrays so lane l's 4- and 8-byte words
+// fall in distinct banks): [stage][sample][lane].
+struct StageBuf {
+  float2 va[2][kStage][32];
+  float2 vb[2][kStage][32];
+  unsigned int f[2][kStage][32];
+  float wa[2][kStage][32];
+  float wb[2][kStage][32];
+};
+
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc, int bytes_tag) {
+  const unsigned int d = (unsigned int)__cvta_generic_to_shared(sdst);
+  if (bytes_tag == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 template <bool HALF>
-__global__ void __launch_bounds__(kWarps * 32, 5)
+__device__ __forceinline__ Sample read_staged(const StageBuf& sb, int sidx, int u, int lane,
+                                              const float* chan_scale, const float* weight,
+                                              const uint8_t* flag, const float2* kf, size_t o,
+                                              int ch, int npol, int pa, int pb) {
+  Sample s;
+  s.k = kf[ch];
+  bool fa = false, fb = false;
+  if (flag) {
+    if (npol == 4) {
+      const unsigned int f = sb.f[sidx][u][lane];
+      fa = (f & 0xffu) != 0;
+      fb = (f >> 24) != 0;
+    } else {
+      fa = flag[o + pa] != 0;
+      fb = flag[o + pb] != 0;
+    }
+  }
+  const float wa = fa ? 0.f : (weight ? sb.wa[sidx][u][lane] : 1.f);
+  float wb = fb ? 0.f : (weight ? sb.wb[sidx][u][lane] : 1.f);
+  if (pa == pb) wb = 0.f;
+  s.sel = wa + wb > 0.f;
+  float2 va = sb.va[sidx][u][lane], vbv = (pa != pb) ? sb.vb[sidx][u][lane] : make_float2(0.f, 0.f);
+  if (HALF) {
+    const float sc = chan_scale[ch];
+    const unsigned int ra = __float_as_uint(va.x), rb = __float_as_uint(vbv.x);
+    const float2 fa2 = __half22float2(*reinterpret_cast<const __half2*>(&ra));
+    const float2 fb2 = __half22float2(*reinterpret_cast<const __half2*>(&rb));
+    va = make_float2(fa2.x * sc, fa2.y * sc);
+    vbv = make_float2(fb2.x * sc, fb2.y * sc);
+  }
+  s.c = make_float2(wa * va.x + wb * vbv.x, wa * va.y + wb * vbv.y);
+  return s;
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(kWarps * 32)
 grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restrict__ kf,
                    const void* __restrict__ vis, const float* __restrict__ chan_scale,
                    const float* __restrict__ weight, const uint8_t* __restrict__ flag, int nbl,
                    int nch, int npol, int G, float bl2, int run, int nseg,
                    float2* __restrict__ H) {
-  const int warp = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  __shared__ StageBuf stage_all[kWarps];
+  const int wib = threadIdx.x >> 5;
+  const int warp = blockIdx.x * kWarps + wib;
   const int lane = threadIdx.x & 31;
   if (warp >= 2 * nbl * nseg) return;
   // warps [0, nbl * nseg) walk the upper-half tracks, the rest their mirrors
@@ -239,85 +328,99 @@ grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restri
   const double dk = kf1 - kf0;
   const int sx = (t.s1 * dk >= 0.0) ? 1 : -1;
   const int sy = (t.s2 * dk >= 0.0) ? 1 : -1;
+  const size_t obase = (size_t)bl * nch * npol;
+  StageBuf& sb = stage_all[wib];
+
+  // lane-private staging: lane l only ever touches st[stage][u][l]
 
   Window w;
 #pragma unroll
   for (int j = 0; j < kWin; ++j)
 #pragma unroll
     for (int i = 0; i < kWin; ++i) w.a[j][i] = make_float2(0.f, 0.f);
-  int ox, oy;
+
+  const int nchunk = (c_end - c_begin + kStage - 1) / kStage;
+  // staging helper: chunk q lands in stage q & 1
+  auto issue = [&](int q) {
+    if (q < nchunk) {
+      const int c0 = c_begin + q * kStage;
+      const int sidx = q & 1;
+#pragma unroll
+      for (int u = 0; u < kStage; ++u) {
+        const int ch = c0 + u;
+        if (ch < c_end) {
+          const size_t o = obase + (size_t)ch * npol;
+          const char* vb = reinterpret_cast<const char*>(vis);
+          const int vbytes = HALF ? 4 : 8;
+          cp_async(&sb.va[sidx][u][lane], vb + (o + pa) * vbytes, vbytes);
+          if (pa != pb) cp_async(&sb.vb[sidx][u][lane], vb + (o + pb) * vbytes, vbytes);
+          if (flag && npol == 4) cp_async(&sb.f[sidx][u][lane], flag + o, 4);
+          if (weight) {
+            cp_async(&sb.wa[sidx][u][lane], weight + o + pa, 4);
+            if (pa != pb) cp_async(&sb.wb[sidx][u][lane], weight + o + pb, 4);
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  issue(0);
+  issue(1);
+  cp_async_wait1();   // chunk 0 landed
+
+  Prepared cur;
   {
-    const float2 k = kf[c_begin];
-    int qx, qy;
-    float f;
-    tap_origin(s1hi, s1lo, k.x, k.y, cx, qx, f);
-    tap_origin(s2hi, s2lo, k.x, k.y, cy, qy, f);
-    ox = sx > 0 ? qx : qx + kW - 1;
-    oy = sy > 0 ? qy : qy + kW - 1;
+    const Sample s0 = read_staged<HALF>(sb, 0, 0, lane, chan_scale, weight, flag, kf,
+                                        obase + (size_t)c_begin * npol, c_begin, npol, pa, pb);
+    prepare(s0, s1hi, s1lo, s2hi, s2lo, cx, cy, sx, sy, t.conj, bl2, cur);
   }
-  const size_t obase = (size_t)bl * nch * npol;
+  int ox = sx > 0 ? cur.kx0 : cur.kx0 + kW - 1;
+  int oy = sy > 0 ? cur.ky0 : cur.ky0 + kW - 1;
   const Sample none{make_float2(0.f, 0.f), make_float2(0.f, 0.f), false};
-  // three samples in flight ahead of the one being gridded
-  Sample s0 = load_sample<HALF>(vis, chan_scale, weight, flag, kf, obase + (size_t)c_begin * npol,
-                                c_begin, npol, pa, pb);
-  Sample s1 = c_begin + 1 < c_end
-                  ? load_sample<HALF>(vis, chan_scale, weight, flag, kf,
-                                      obase + (size_t)(c_begin + 1) * npol, c_begin + 1, npol, pa, pb)
-                  : none;
-  Sample s2 = c_begin + 2 < c_end
-                  ? load_sample<HALF>(vis, chan_scale, weight, flag, kf,
-                                      obase + (size_t)(c_begin + 2) * npol, c_begin + 2, npol, pa, pb)
-                  : none;
 #pragma unroll 1
   for (int ch = c_begin; ch < c_end; ++ch) {
-    const Sample s3 = ch + 3 < c_end
-                          ? load_sample<HALF>(vis, chan_scale, weight, flag, kf,
-                                              obase + (size_t)(ch + 3) * npol, ch + 3, npol, pa, pb)
-                          : none;
-    if (s0.sel) {
-      const float2 k = s0.k;
-      int kx0, ky0;
-      float fx, fy;
-      tap_origin(s1hi, s1lo, k.x, k.y, cx, kx0, fx);
-      tap_origin(s2hi, s2lo, k.x, k.y, cy, ky0, fy);
-      // footprint start in window coordinates and the offset of the window's
-      // first tap from the sample, in the direction of travel
-      int dx = sx > 0 ? kx0 - ox : ox - (kx0 + kW - 1);
-      int dy = sy > 0 ? ky0 - oy : oy - (ky0 + kW - 1);
-      const float fxs = sx > 0 ? fx - 0.5f * kW : fx + 0.5f * kW - 1.0f;
-      const float fys = sy > 0 ? fy - 0.5f * kW : fy + 0.5f * kW - 1.0f;
-      if (dx < 0 || dy < 0 || dx >= kWin || dy >= kWin) {
-        flush_all(w, H, G, ox, oy, sx, sy);
-        ox = sx > 0 ? kx0 : kx0 + kW - 1;
-        oy = sy > 0 ? ky0 : ky0 + kW - 1;
-        dx = 0;
-        dy = 0;
+    const int rel = ch - c_begin;
+    const int q = rel / kStage, u = rel - q * kStage;
+    // the next sample (ch + 1) may start a new chunk: wait for it, and refill
+    // the stage that chunk q has just vacated
+    const int chn = ch + 1;
+    Sample sn = none;
+    if (chn < c_end) {
+      const int qn = q + (u + 1 == kStage ? 1 : 0);
+      const int un = (u + 1 == kStage) ? 0 : u + 1;
+      if (un == 0) {
+        // chunk q is fully read: refill its stage with chunk qn + 1, then wait
+        // until everything but that newest group (so chunk qn) has landed
+        issue(qn + 1);
+        cp_async_wait1();
       }
-      while (dx > 0) { slide_x(w, H, G, ox, oy, sy); ox += sx; --dx; }
-      while (dy > 0) { slide_y(w, H, G, ox, oy, sx); oy += sy; --dy; }
-      float2 c = s0.c;
-      if (t.conj) c.y = -c.y;
-      const float fsx = (float)sx, fsy = (float)sy;
-      float px[kW];
-      float2 b[kW];
-#pragma unroll
-      for (int m = 0; m < kW; ++m) {
-        px[m] = es_kernel(fxs + fsx * (float)m, bl2);
-        const float py = es_kernel(fys + fsy * (float)m, bl2);
-        b[m] = make_float2(c.x * py, c.y * py);
-      }
-#pragma unroll
-      for (int j = 0; j < kWin; ++j)
-#pragma unroll
-        for (int i = 0; i < kWin; ++i) {
-          w.a[j][i].x = fmaf(px[i], b[j].x, w.a[j][i].x);
-          w.a[j][i].y = fmaf(px[i], b[j].y, w.a[j][i].y);
-        }
+      sn = read_staged<HALF>(sb, qn & 1, un, lane, chan_scale, weight, flag, kf,
+                             obase + (size_t)chn * npol, chn, npol, pa, pb);
     }
-    s0 = s1;
-    s1 = s2;
-    s2 = s3;
+    // footprint start of the current sample in window coordinates
+    int dx = sx > 0 ? cur.kx0 - ox : ox - (cur.kx0 + kW - 1);
+    int dy = sy > 0 ? cur.ky0 - oy : oy - (cur.ky0 + kW - 1);
+    if (dx < 0 || dy < 0 || dx >= kWin || dy >= kWin) {
+      flush_all(w, H, G, ox, oy, sx, sy);
+      ox = sx > 0 ? cur.kx0 : cur.kx0 + kW - 1;
+      oy = sy > 0 ? cur.ky0 : cur.ky0 + kW - 1;
+      dx = 0;
+      dy = 0;
+    }
+    while (dx > 0) { slide_x(w, H, G, ox, oy, sy); ox += sx; --dx; }
+    while (dy > 0) { slide_y(w, H, G, ox, oy, sx); oy += sy; --dy; }
+    Prepared nxt;
+    prepare(sn, s1hi, s1lo, s2hi, s2lo, cx, cy, sx, sy, t.conj, bl2, nxt);
+#pragma unroll
+    for (int j = 0; j < kWin; ++j)
+#pragma unroll
+      for (int i = 0; i < kWin; ++i) {
+        w.a[j][i].x = fmaf(cur.px[i], cur.b[j].x, w.a[j][i].x);
+        w.a[j][i].y = fmaf(cur.px[i], cur.b[j].y, w.a[j][i].y);
+      }
+    cur = nxt;
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   flush_all(w, H, G, ox, oy, sx, sy);
 }
 
@@ -329,8 +432,8 @@ cudaError_t launch_grid(toi_plan_s* p, Slot& s, const double* freq, const void* 
   (void)freq;
   const int G = p->G;
   const int tok = prof_begin(p, PROF_GRID, 1);
-  cudaError_t e = cudaMemsetAsync(s.grid, 0, sizeof(float2) * (size_t)(G / 2) * G, p->stream);
-  if (e != cudaSuccess) return e;
+  // the slot is zero: cleared at plan creation, by the row pass of the
+  // previous toi_image, or by toi_grid when a gridded slot is re-gridded
   // channel runs per lane: each track is split into segments of 32 lanes so
   // that there are several warps per SM slot (runs of at least 16 channels)
   int run = (nch + 63) / 64;

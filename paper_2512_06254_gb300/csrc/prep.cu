@@ -65,187 +65,233 @@ __global__ void prep_channels_kernel(const double* __restrict__ freq, int nch,
   }
 }
 
-// Per-baseline: deselected channels (both parallel hands flagged or zero
-// weight) and the sum of weights.
-__global__ void prep_baselines_kernel(const uint8_t* __restrict__ flag,
-                                      const float* __restrict__ weight,
-                                      const double* __restrict__ kch, int nch, int npol,
-                                      BaselineMoments* __restrict__ mom) {
-  __shared__ double sh[4 * kPrepThreads];
-  const int bl = blockIdx.x;
-  int pa, pb;
-  parallel_hands(npol, pa, pb);
-  const size_t base = (size_t)bl * nch * npol;
-  double sk = 0.0, sk2 = 0.0, sw = 0.0;
-  long long nd = 0, cnt = 0;
-  for (int c = threadIdx.x; c < nch; c += kPrepThreads) {
-    const size_t o = base + (size_t)c * npol;
-    const bool fa = flag ? flag[o + pa] != 0 : false;
-    const bool fb = flag ? flag[o + pb] != 0 : false;
-    float wa, wb;
-    if (weight) {
-      wa = fa ? 0.f : weight[o + pa];
-      wb = fb ? 0.f : weight[o + pb];
-    } else {
-      wa = fa ? 0.f : 1.f;
-      wb = fb ? 0.f : 1.f;
-    }
-    const float wq = (pa == pb) ? wa : wa + wb;
-    if (wq > 0.f) {
-      if (weight) {
-        sw = __dadd_rn(sw, (pa == pb) ? (double)wa : __dadd_rn((double)wa, (double)wb));
-      } else {
-        cnt += (pa == pb) ? 1 : (int)(!fa) + (int)(!fb);
-      }
-    } else {
-      const double k = kch[c];
-      sk = __dadd_rn(sk, k);
-      sk2 = __dadd_rn(sk2, __dmul_rn(k, k));
-      nd += 1;
-    }
-  }
-  double v[4] = {sk, sk2, sw, (double)nd};
-  // counts are exact in float64 below 2^53
-  v[2] = weight ? v[2] : (double)cnt;
-  block_reduce<kPrepThreads, 4>(v, sh);
-  if (threadIdx.x == 0) {
-    mom[bl].sk_desel = v[0];
-    mom[bl].sk2_desel = v[1];
-    mom[bl].sumw = v[2];
-    mom[bl].ndesel = (long long)v[3];
-  }
-}
+// Per baseline (one warp): deselected channels (both parallel hands flagged
+// or zero weight) and the sum of weights; then each block folds its
+// baselines' contributions to the 11 plane-fit sums (count, first and second
+// moments, sum of weights) into one partial record, in a fixed order.
+constexpr int kMomWarps = 8;
 
-// Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations
-// (float64).  On return a holds the eigenvalues on its diagonal and the
-// columns of e the eigenvectors.
-__device__ void jacobi3(double a[3][3], double e[3][3]) {
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) e[i][j] = (i == j) ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
-    const double dia = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
-    if (off == 0.0 || off <= 1e-300 + 1e-18 * dia) break;
-    for (int p = 0; p < 2; ++p) {
-      for (int q = p + 1; q < 3; ++q) {
-        const double apq = a[p][q];
-        if (apq == 0.0) continue;
-        const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
-        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0);
-        const double s = t * c;
-        for (int k = 0; k < 3; ++k) {   // A <- A J (columns p, q)
-          const double akp = a[k][p], akq = a[k][q];
-          a[k][p] = c * akp - s * akq;
-          a[k][q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < 3; ++k) {   // A <- J^T A (rows p, q)
-          const double apk = a[p][k], aqk = a[q][k];
-          a[p][k] = c * apk - s * aqk;
-          a[q][k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < 3; ++k) {   // E <- E J
-          const double ekp = e[k][p], ekq = e[k][q];
-          e[k][p] = c * ekp - s * ekq;
-          e[k][q] = s * ekp + c * ekq;
-        }
-      }
-    }
-  }
-}
-
-__global__ void prep_finalize_kernel(const double* __restrict__ uvw, int nbl, int nch,
-                                     const double* __restrict__ kpart, int nkblk,
-                                     const BaselineMoments* __restrict__ mom,
-                                     double* __restrict__ snap, int* status) {
-  constexpr int NT = 256;
-  __shared__ double sh[11 * NT];
-  __shared__ double ks[2];
+__global__ void __launch_bounds__(kMomWarps * 32)
+prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict__ weight,
+                      const double* __restrict__ kch, const double* __restrict__ kpart, int nkblk,
+                      const double* __restrict__ uvw, int nbl, int nch, int npol,
+                      double* __restrict__ bpart) {
+  __shared__ double sk_all[2];
+  __shared__ double contrib[kMomWarps][11];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
     for (int i = 0; i < nkblk; ++i) {
       a = __dadd_rn(a, kpart[2 * i]);
       b = __dadd_rn(b, kpart[2 * i + 1]);
     }
-    ks[0] = a;
-    ks[1] = b;
+    sk_all[0] = a;
+    sk_all[1] = b;
   }
   __syncthreads();
-  const double skall = ks[0], sk2all = ks[1];
-  double v[11];
-  for (int i = 0; i < 11; ++i) v[i] = 0.0;
-  for (int b = threadIdx.x; b < nbl; b += NT) {
-    const BaselineMoments m = mom[b];
-    const double n = (double)(nch - m.ndesel);
-    const double s1 = skall - m.sk_desel;
-    const double s2 = sk2all - m.sk2_desel;
-    const double x = uvw[3 * b], y = uvw[3 * b + 1], z = uvw[3 * b + 2];
-    v[0] += n;
-    v[1] += x * s1; v[2] += y * s1; v[3] += z * s1;
-    v[4] += x * x * s2; v[5] += x * y * s2; v[6] += x * z * s2;
-    v[7] += y * y * s2; v[8] += y * z * s2; v[9] += z * z * s2;
-    v[10] += m.sumw;
-  }
-  block_reduce<NT, 11>(v, sh);
-  if (threadIdx.x == 0) {
-    const double N = v[0];
-    const int empty = (N <= 0.0 || v[10] <= 0.0) ? 1 : 0;
-    double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-    if (!empty) {
-      const double m1[3] = {v[1], v[2], v[3]};
-      double C[3][3];
-      C[0][0] = v[4] - m1[0] * m1[0] / N;
-      C[0][1] = v[5] - m1[0] * m1[1] / N;
-      C[0][2] = v[6] - m1[0] * m1[2] / N;
-      C[1][1] = v[7] - m1[1] * m1[1] / N;
-      C[1][2] = v[8] - m1[1] * m1[2] / N;
-      C[2][2] = v[9] - m1[2] * m1[2] / N;
-      C[1][0] = C[0][1]; C[2][0] = C[0][2]; C[2][1] = C[1][2];
-      double E[3][3];
-      jacobi3(C, E);
-      int imin = 0, imax = 0;
-      for (int i = 1; i < 3; ++i) {
-        if (C[i][i] < C[imin][imin]) imin = i;
-        if (C[i][i] > C[imax][imax]) imax = i;
+  const int bl = blockIdx.x * kMomWarps + wib;
+  double out[11];
+  for (int i = 0; i < 11; ++i) out[i] = 0.0;
+  if (bl < nbl) {
+    int pa, pb;
+    parallel_hands(npol, pa, pb);
+    const size_t base = (size_t)bl * nch * npol;
+    double sk = 0.0, sk2 = 0.0, sw = 0.0;
+    long long nd = 0, cnt = 0;
+    for (int c = lane; c < nch; c += 32) {
+      const size_t o = base + (size_t)c * npol;
+      bool fa = false, fb = false;
+      if (flag) {
+        if (npol == 4) {
+          const unsigned int f4 = __ldcs(reinterpret_cast<const unsigned int*>(flag + o));
+          fa = (f4 & 0xffu) != 0;
+          fb = (f4 >> 24) != 0;
+        } else {
+          fa = flag[o + pa] != 0;
+          fb = flag[o + pb] != 0;
+        }
       }
-      const int imid = (imin == imax) ? (imin + 1) % 3 : 3 - imin - imax;
-      // rank <= 1 (second singular value <= 1e-6 of the first): no plane, V = I
-      const double lmax = fmax(C[imax][imax], 0.0), lmid = fmax(C[imid][imid], 0.0);
-      const bool degenerate = !(sqrt(lmid) > 1e-6 * sqrt(lmax));
-      double v3[3] = {E[0][imin], E[1][imin], E[2][imin]};
-      double nn = sqrt(v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2]);
-      for (int i = 0; i < 3; ++i) v3[i] /= nn;
+      float wa, wb;
+      if (weight) {
+        wa = fa ? 0.f : weight[o + pa];
+        wb = fb ? 0.f : weight[o + pb];
+      } else {
+        wa = fa ? 0.f : 1.f;
+        wb = fb ? 0.f : 1.f;
+      }
+      const float wq = (pa == pb) ? wa : wa + wb;
+      if (wq > 0.f) {
+        if (weight) sw += (pa == pb) ? (double)wa : (double)wa + (double)wb;
+        else cnt += (pa == pb) ? 1 : (int)(!fa) + (int)(!fb);
+      } else {
+        const double k = kch[c];
+        sk += k;
+        sk2 += k * k;
+        nd += 1;
+      }
+    }
+    // fixed-order warp reduction
+    for (int off = 16; off > 0; off >>= 1) {
+      sk += __shfl_down_sync(0xffffffffu, sk, off);
+      sk2 += __shfl_down_sync(0xffffffffu, sk2, off);
+      sw += __shfl_down_sync(0xffffffffu, sw, off);
+      nd += __shfl_down_sync(0xffffffffu, nd, off);
+      cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+    }
+    if (lane == 0) {
+      const double n = (double)(nch - nd);
+      const double s1 = sk_all[0] - sk, s2 = sk_all[1] - sk2;
+      const double x = uvw[3 * bl], y = uvw[3 * bl + 1], z = uvw[3 * bl + 2];
+      out[0] = n;
+      out[1] = x * s1; out[2] = y * s1; out[3] = z * s1;
+      out[4] = x * x * s2; out[5] = x * y * s2; out[6] = x * z * s2;
+      out[7] = y * y * s2; out[8] = y * z * s2; out[9] = z * z * s2;
+      out[10] = weight ? sw : (double)cnt;
+    }
+  }
+  if (lane == 0)
+    for (int i = 0; i < 11; ++i) contrib[wib][i] = out[i];
+  __syncthreads();
+  if (threadIdx.x < 11) {
+    double a = 0.0;
+    for (int wdx = 0; wdx < kMomWarps; ++wdx) a += contrib[wdx][threadIdx.x];
+    bpart[(size_t)blockIdx.x * 11 + threadIdx.x] = a;
+  }
+}
+
+// Eigenvector of the smallest eigenvalue of the symmetric 3x3 C (float64
+// accuracy).  A float32 Jacobi solve gives an approximate vector u; the
+// float64 Rayleigh quotient l = u.Cu / u.u is then accurate to the square of
+// its error, and the null vector of C - l I is the largest cross product of
+// two of its rows.  Returns false when C has rank <= 1 (second singular value
+// <= 1e-6 of the first), where no plane is defined.
+__device__ bool smallest_eigvec(const double Cd[3][3], double v3[3]) {
+  double tr = fabs(Cd[0][0]) + fabs(Cd[1][1]) + fabs(Cd[2][2]);
+  if (!(tr > 0.0)) return false;
+  float a[3][3], e[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      a[i][j] = (float)(Cd[i][j] / tr);
+      e[i][j] = (i == j) ? 1.f : 0.f;
+    }
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    const float off = fabsf(a[0][1]) + fabsf(a[0][2]) + fabsf(a[1][2]);
+    if (off < 1e-30f) break;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        const float apq = a[p][q];
+        if (apq == 0.f) continue;
+        const float theta = (a[q][q] - a[p][p]) / (2.f * apq);
+        const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+        const float c = rsqrtf(t * t + 1.f), s = t * c;
+        for (int k = 0; k < 3; ++k) {
+          const float akp = a[k][p], akq = a[k][q];
+          a[k][p] = c * akp - s * akq;
+          a[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < 3; ++k) {
+          const float apk = a[p][k], aqk = a[q][k];
+          a[p][k] = c * apk - s * aqk;
+          a[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < 3; ++k) {
+          const float ekp = e[k][p], ekq = e[k][q];
+          e[k][p] = c * ekp - s * ekq;
+          e[k][q] = s * ekp + c * ekq;
+        }
+      }
+  }
+  int imin = 0, imax = 0;
+  for (int i = 1; i < 3; ++i) {
+    if (a[i][i] < a[imin][imin]) imin = i;
+    if (a[i][i] > a[imax][imax]) imax = i;
+  }
+  const int imid = (imin == imax) ? (imin + 1) % 3 : 3 - imin - imax;
+  const double lmax = fmax((double)a[imax][imax], 0.0), lmid = fmax((double)a[imid][imid], 0.0);
+  // rank <= 1: the float32 estimate is ample for this 1e-6 test
+  if (!(sqrt(lmid) > 1e-6 * sqrt(lmax))) return false;
+  const double u[3] = {e[0][imin], e[1][imin], e[2][imin]};
+  double Cu[3];
+  for (int i = 0; i < 3; ++i) Cu[i] = Cd[i][0] * u[0] + Cd[i][1] * u[1] + Cd[i][2] * u[2];
+  const double l = (u[0] * Cu[0] + u[1] * Cu[1] + u[2] * Cu[2]) / (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  double M[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) M[i][j] = Cd[i][j] - (i == j ? l : 0.0);
+  double best[3] = {0.0, 0.0, 0.0}, bn = -1.0;
+  for (int r = 0; r < 3; ++r) {
+    const double* m1 = M[r];
+    const double* m2 = M[(r + 1) % 3];
+    const double cx = m1[1] * m2[2] - m1[2] * m2[1];
+    const double cy = m1[2] * m2[0] - m1[0] * m2[2];
+    const double cz = m1[0] * m2[1] - m1[1] * m2[0];
+    const double nn = cx * cx + cy * cy + cz * cz;
+    if (nn > bn) { bn = nn; best[0] = cx; best[1] = cy; best[2] = cz; }
+  }
+  if (!(bn > 0.0)) {   // exactly diagonalised: u is already exact
+    for (int i = 0; i < 3; ++i) v3[i] = u[i];
+  } else {
+    for (int i = 0; i < 3; ++i) v3[i] = best[i];
+  }
+  const double inv = 1.0 / sqrt(v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2]);
+  for (int i = 0; i < 3; ++i) v3[i] *= inv;
+  return true;
+}
+
+__global__ void prep_finalize_kernel(const double* __restrict__ bpart, int nbpart,
+                                     double* __restrict__ snap, int* status) {
+  __shared__ double v[11];
+  if (threadIdx.x < 11) {
+    double a = 0.0;
+    for (int b = 0; b < nbpart; ++b) a += bpart[(size_t)b * 11 + threadIdx.x];
+    v[threadIdx.x] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double N = v[0];
+  const int empty = (N <= 0.0 || v[10] <= 0.0) ? 1 : 0;
+  double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  if (!empty) {
+    const double m1[3] = {v[1], v[2], v[3]};
+    double C[3][3];
+    C[0][0] = v[4] - m1[0] * m1[0] / N;
+    C[0][1] = v[5] - m1[0] * m1[1] / N;
+    C[0][2] = v[6] - m1[0] * m1[2] / N;
+    C[1][1] = v[7] - m1[1] * m1[1] / N;
+    C[1][2] = v[8] - m1[1] * m1[2] / N;
+    C[2][2] = v[9] - m1[2] * m1[2] / N;
+    C[1][0] = C[0][1]; C[2][0] = C[0][2]; C[2][1] = C[1][2];
+    double v3[3];
+    if (smallest_eigvec(C, v3)) {
       if (v3[2] < 0.0)
         for (int i = 0; i < 3; ++i) v3[i] = -v3[i];
       double e[3] = {1.0, 0.0, 0.0};
       if (fabs(v3[0]) > 0.999) { e[0] = 0.0; e[1] = 1.0; }
       const double d = e[0] * v3[0] + e[1] * v3[1] + e[2] * v3[2];
       double v1[3] = {e[0] - d * v3[0], e[1] - d * v3[1], e[2] - d * v3[2]};
-      nn = sqrt(v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]);
-      for (int i = 0; i < 3; ++i) v1[i] /= nn;
+      const double nn = 1.0 / sqrt(v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]);
+      for (int i = 0; i < 3; ++i) v1[i] *= nn;
       const double v2[3] = {v3[1] * v1[2] - v3[2] * v1[1], v3[2] * v1[0] - v3[0] * v1[2],
                             v3[0] * v1[1] - v3[1] * v1[0]};
-      if (!degenerate)
-        for (int i = 0; i < 3; ++i) { V[0][i] = v1[i]; V[1][i] = v2[i]; V[2][i] = v3[i]; }
-    } else {
-      set_status(status, TOI_DEV_EMPTY);
+      for (int i = 0; i < 3; ++i) { V[0][i] = v1[i]; V[1][i] = v2[i]; V[2][i] = v3[i]; }
     }
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) snap[SNAP_V + 3 * i + j] = V[i][j];
-    snap[SNAP_OMEGA] = fabs(V[0][0] * V[1][1] - V[1][0] * V[0][1]);
-    snap[SNAP_XI] = V[2][0] / V[2][2];
-    snap[SNAP_ETA] = V[2][1] / V[2][2];
-    snap[SNAP_SUMW] = empty ? 0.0 : v[10];
-    snap[SNAP_NVIS] = empty ? 0.0 : v[0];
-    snap[14] = 0.0;
-    snap[15] = 0.0;
+  } else {
+    set_status(status, TOI_DEV_EMPTY);
   }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) snap[SNAP_V + 3 * i + j] = V[i][j];
+  snap[SNAP_OMEGA] = fabs(V[0][0] * V[1][1] - V[1][0] * V[0][1]);
+  snap[SNAP_XI] = V[2][0] / V[2][2];
+  snap[SNAP_ETA] = V[2][1] / V[2][2];
+  snap[SNAP_SUMW] = empty ? 0.0 : v[10];
+  snap[SNAP_NVIS] = empty ? 0.0 : N;
+  snap[14] = 0.0;   // largest stored grid row touched (written by the coefficient kernel)
+  snap[15] = 0.0;
 }
 
 // Per baseline: R = V uvw (float64), grid coefficients a1 = -r1 beta G,
 // a2 = r2 beta G, and the check that every footprint stays on the grid.
 __global__ void prep_coef_kernel(const double* __restrict__ uvw, int nbl, int nch,
-                                 const double* __restrict__ kch, const double* __restrict__ snap,
+                                 const double* __restrict__ kch, double* __restrict__ snap,
                                  double beta_rad, int G, int W, BaselineCoef* __restrict__ coef,
                                  int* status) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -267,6 +313,10 @@ __global__ void prep_coef_kernel(const double* __restrict__ uvw, int nbl, int nc
   cf.pad = 0.0;
   coef[b] = cf;
   if (fabs(cf.a1) * kmax > lim || fabs(cf.a2) * kmax > lim) set_status(status, TOI_DEV_RANGE);
+  // largest stored row any footprint of this baseline reaches
+  const double rowmax = fmin(fabs(cf.a2) * kmax + 0.5 * W + 1.0, 0.5 * G);
+  atomicMax(reinterpret_cast<unsigned long long*>(snap + 14),
+            (unsigned long long)__double_as_longlong(rowmax));
 }
 
 }  // namespace
@@ -275,12 +325,12 @@ cudaError_t launch_prep(toi_plan_s* p, Slot& s, const double* uvw, const double*
                         const float* weight, const uint8_t* flag, int nbl, int nch) {
   const int tok = prof_begin(p, PROF_PREP, 4);
   const int nkblk = (nch + 255) / 256;
+  const int nbblk = (nbl + kMomWarps - 1) / kMomWarps;
   prep_channels_kernel<<<nkblk, 256, 0, p->stream>>>(freq, nch, p->kch, p->kf, p->kch_sum,
                                                      p->d_status);
-  prep_baselines_kernel<<<nbl, kPrepThreads, 0, p->stream>>>(flag, weight, p->kch, nch,
-                                                             p->cfg.n_pol, p->mom);
-  prep_finalize_kernel<<<1, 256, 0, p->stream>>>(uvw, nbl, nch, p->kch_sum, nkblk, p->mom, s.snap,
-                                                 p->d_status);
+  prep_baselines_kernel<<<nbblk, kMomWarps * 32, 0, p->stream>>>(
+      flag, weight, p->kch, p->kch_sum, nkblk, uvw, nbl, nch, p->cfg.n_pol, p->bpart);
+  prep_finalize_kernel<<<1, 32, 0, p->stream>>>(p->bpart, nbblk, s.snap, p->d_status);
   prep_coef_kernel<<<(nbl + 127) / 128, 128, 0, p->stream>>>(uvw, nbl, nch, p->kch, s.snap,
                                                              p->beta_rad, p->G, p->W, s.coef,
                                                              p->d_status);

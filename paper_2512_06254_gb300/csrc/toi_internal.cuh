@@ -23,6 +23,7 @@ enum SnapField {
   SNAP_ETA = 11,
   SNAP_SUMW = 12,
   SNAP_NVIS = 13,
+  SNAP_ROWMAX = 14,  // largest stored grid row reached by a footprint (+1 margin)
   SNAP_LEN = 16
 };
 
@@ -30,14 +31,6 @@ enum SnapField {
 // coordinates, g1 = G/2 + a1 k, g2 = G/2 + a2 k, k = nu / c (float64), and r3.
 struct BaselineCoef {
   double a1, a2, r3, pad;
-};
-
-// Per-baseline moment record of the selected samples.
-struct BaselineMoments {
-  double sk_desel;    // sum of k over deselected channels
-  double sk2_desel;   // sum of k^2 over deselected channels
-  double sumw;        // sum of weights (float64)
-  long long ndesel;   // number of deselected channels
 };
 
 struct Slot {
@@ -52,7 +45,7 @@ struct Slot {
   const float* weight = nullptr;
   const uint8_t* flag = nullptr;
   int nbl = 0, nch = 0;
-  bool valid = false;
+  bool valid = false;   // holds a grid from toi_grid that toi_image has not consumed
 };
 
 // Per-stage device-time accounting with CUDA events on the plan's stream.
@@ -86,7 +79,7 @@ struct toi_plan_s {
   double* kch = nullptr;                 // [max_ch] k = nu / c
   float2* kf = nullptr;                  // [max_ch] k as an unevaluated float sum hi + lo
   double* kch_sum = nullptr;             // [2 * ceil(max_ch / 256)] per-block sums of k, k^2
-  toi::BaselineMoments* mom = nullptr;   // [max_bl]
+  double* bpart = nullptr;               // [ceil(max_bl / 8)][11] plane-fit partial sums
   float2* twiddle = nullptr;             // [G] exp(+2 pi i k / G)
   float* corr = nullptr;                 // [N] 1 / psi_hat((j - N/2) / G)
   float2* fft_tmp = nullptr;             // [G/2][N] rows after pass 1

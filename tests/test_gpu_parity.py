@@ -46,12 +46,15 @@ def test_tiny_all_stages(tiny):
     w, snaps, ref = tiny
     plan = plan_for(w)
     for sn, r in zip(snaps, ref):
-        out = gpu_image(plan, to_dev(sn))
-        assert out["status"] == toi.TOI_OK
-        _check_geometry(out["info"], r)
-        H = plan.buffer(toi.BUF_GRID).cpu().numpy()
+        d = to_dev(sn)
+        plan.grid(d["uvw"], d["freq"], d["vis"], flag=d["flag"])
+        H = plan.buffer(toi.BUF_GRID).cpu().numpy()     # before toi_image consumes it
         Href = 2.0 * O.hermitian_half(r["grid"])[:-1]
         assert rel_err(H, Href) < IMG_TOL
+        out = gpu_image(plan, d)
+        assert out["status"] == toi.TOI_OK
+        _check_geometry(out["info"], r)
+        assert np.abs(plan.buffer(toi.BUF_GRID).cpu().numpy()).max() == 0.0   # consumed
         tilted = plan.buffer(toi.BUF_TILTED).cpu().numpy()
         assert rel_err(tilted, r["tilted"]) < IMG_TOL
         assert rel_err(out["image"], r["image"]) < IMG_TOL
@@ -196,6 +199,10 @@ def test_argument_errors_on_host():
     assert e.value.status == toi.TOI_ERR_ARG
     with pytest.raises(toi.ToiError):
         plan.image(slot=0)          # nothing gridded yet
+    plan.grid(sn["uvw"], sn["freq"], sn["vis"])
+    plan.image(slot=0)
+    with pytest.raises(toi.ToiError):
+        plan.image(slot=0)          # the grid was consumed
     with pytest.raises(toi.ToiError):
         plan.grid(sn["uvw"], sn["freq"], sn["vis"], slot=3)
     plan.close()
