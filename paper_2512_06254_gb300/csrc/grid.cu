@@ -15,7 +15,7 @@
 // current sample in registers and accumulates successive samples there with
 // register FMAs only.  When the track moves on by a cell, the column (or
 // row) it leaves behind is complete and is added to the grid with one vector
-// reduction per non-zero cell, and the window slides by one cell.  Grid
+// reduction per non-zero cell, and the (circular) window slides by one cell.  Grid
 // traffic is therefore about W cells per cell of track length instead of
 // W^2 per sample; the 67 MB
 // half-plane grid of a 2048^2 image stays resident in L2 for these
@@ -90,11 +90,14 @@ __device__ __forceinline__ float2 load_vis(const void* vis, size_t idx, float sc
   }
 }
 
-// A lane's W x W register window.  Window column i sits at absolute grid
-// column ox + sx * i and row j at oy + sy * j, with (sx, sy) the direction the
-// lane's track moves in, so the window only ever slides forwards.
+// A lane's W x W register window, kept circular: logical column i (in the
+// direction of travel sx) is physical column (i + rx) mod W and lies at
+// absolute grid column ox + sx * i; rows likewise with (ry, oy, sy).  A
+// slide flushes the physical column (row) that holds logical column (row) 0,
+// clears it for the incoming cells and advances the phase; nothing is moved
+// between registers.
 struct Window {
-  float2 a[kWin][kWin];   // a[row][col]
+  float2 a[kWin][kWin];   // a[physical row][physical column]
 };
 
 __device__ __forceinline__ void flush_cell(float2* __restrict__ H, int G, int x, int y, float2 v) {
@@ -102,40 +105,71 @@ __device__ __forceinline__ void flush_cell(float2* __restrict__ H, int G, int x,
     red_add(H + (size_t)y * G + x, v);
 }
 
-__device__ __forceinline__ void flush_all(Window& w, float2* __restrict__ H, int G, int ox, int oy,
-                                       int sx, int sy) {
-#pragma unroll
-  for (int j = 0; j < kWin; ++j)
-#pragma unroll
-    for (int i = 0; i < kWin; ++i) {
-      flush_cell(H, G, ox + sx * i, oy + sy * j, w.a[j][i]);
-      w.a[j][i] = make_float2(0.f, 0.f);
-    }
+// absolute coordinate of physical index p for phase r, origin o, direction s
+__device__ __forceinline__ int phys_to_abs(int p, int r, int o, int s) {
+  return o + s * ((p - r) & (kWin - 1));
 }
 
-// slide one column forwards: column 0 is final
-__device__ __forceinline__ void slide_x(Window& w, float2* __restrict__ H, int G, int ox, int oy,
-                                        int sy) {
+__device__ __forceinline__ void flush_all(Window& w, float2* __restrict__ H, int G, int ox, int oy,
+                                          int sx, int sy, int rx, int ry) {
 #pragma unroll
   for (int j = 0; j < kWin; ++j) {
-    flush_cell(H, G, ox, oy + sy * j, w.a[j][0]);
+    const int y = phys_to_abs(j, ry, oy, sy);
 #pragma unroll
-    for (int i = 0; i < kWin - 1; ++i) w.a[j][i] = w.a[j][i + 1];
-    w.a[j][kWin - 1] = make_float2(0.f, 0.f);
+    for (int i = 0; i < kWin; ++i) {
+      flush_cell(H, G, phys_to_abs(i, rx, ox, sx), y, w.a[j][i]);
+      w.a[j][i] = make_float2(0.f, 0.f);
+    }
   }
 }
 
-// slide one row forwards: row 0 is final
+template <int P>
+__device__ __forceinline__ void flush_col(Window& w, float2* __restrict__ H, int G, int x, int oy,
+                                          int sy, int ry) {
+#pragma unroll
+  for (int j = 0; j < kWin; ++j) {
+    flush_cell(H, G, x, phys_to_abs(j, ry, oy, sy), w.a[j][P]);
+    w.a[j][P] = make_float2(0.f, 0.f);
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void flush_row(Window& w, float2* __restrict__ H, int G, int y, int ox,
+                                          int sx, int rx) {
+#pragma unroll
+  for (int i = 0; i < kWin; ++i) {
+    flush_cell(H, G, phys_to_abs(i, rx, ox, sx), y, w.a[P][i]);
+    w.a[P][i] = make_float2(0.f, 0.f);
+  }
+}
+
+// slide one column forwards: physical column rx (logical column 0) is final
+__device__ __forceinline__ void slide_x(Window& w, float2* __restrict__ H, int G, int ox, int oy,
+                                        int sy, int rx, int ry) {
+  switch (rx) {
+    case 0: flush_col<0>(w, H, G, ox, oy, sy, ry); break;
+    case 1: flush_col<1>(w, H, G, ox, oy, sy, ry); break;
+    case 2: flush_col<2>(w, H, G, ox, oy, sy, ry); break;
+    case 3: flush_col<3>(w, H, G, ox, oy, sy, ry); break;
+    case 4: flush_col<4>(w, H, G, ox, oy, sy, ry); break;
+    case 5: flush_col<5>(w, H, G, ox, oy, sy, ry); break;
+    case 6: flush_col<6>(w, H, G, ox, oy, sy, ry); break;
+    default: flush_col<7>(w, H, G, ox, oy, sy, ry); break;
+  }
+}
+
 __device__ __forceinline__ void slide_y(Window& w, float2* __restrict__ H, int G, int ox, int oy,
-                                        int sx) {
-#pragma unroll
-  for (int i = 0; i < kWin; ++i) flush_cell(H, G, ox + sx * i, oy, w.a[0][i]);
-#pragma unroll
-  for (int j = 0; j < kWin - 1; ++j)
-#pragma unroll
-    for (int i = 0; i < kWin; ++i) w.a[j][i] = w.a[j + 1][i];
-#pragma unroll
-  for (int i = 0; i < kWin; ++i) w.a[kWin - 1][i] = make_float2(0.f, 0.f);
+                                        int sx, int rx, int ry) {
+  switch (ry) {
+    case 0: flush_row<0>(w, H, G, oy, ox, sx, rx); break;
+    case 1: flush_row<1>(w, H, G, oy, ox, sx, rx); break;
+    case 2: flush_row<2>(w, H, G, oy, ox, sx, rx); break;
+    case 3: flush_row<3>(w, H, G, oy, ox, sx, rx); break;
+    case 4: flush_row<4>(w, H, G, oy, ox, sx, rx); break;
+    case 5: flush_row<5>(w, H, G, oy, ox, sx, rx); break;
+    case 6: flush_row<6>(w, H, G, oy, ox, sx, rx); break;
+    default: flush_row<7>(w, H, G, oy, ox, sx, rx); break;
+  }
 }
 
 struct Sample {
@@ -201,31 +235,23 @@ __device__ __forceinline__ void tap_origin(float shi, float slo, float khi, floa
   f = fr;
 }
 
-// Coordinates and kernel values of one sample, ready to be accumulated.
+// Coordinates and kernel-argument bases of one sample.
 struct Prepared {
-  float px[kW];    // x taps in the direction of travel
-  float2 b[kW];    // c * y taps in the direction of travel
+  float2 c;        // weighted visibility (conjugated for a mirror track)
+  float fxs, fys;  // offset of the first tap (direction of travel) from the sample
   int kx0, ky0;    // first tap (absolute grid index) on each axis
 };
 
 __device__ __forceinline__ void prepare(const Sample& s, float s1hi, float s1lo, float s2hi,
                                         float s2lo, float cx, float cy, int sx, int sy, bool conj,
-                                        float bl2, Prepared& p) {
+                                        Prepared& p) {
   float fx, fy;
   tap_origin(s1hi, s1lo, s.k.x, s.k.y, cx, p.kx0, fx);
   tap_origin(s2hi, s2lo, s.k.x, s.k.y, cy, p.ky0, fy);
-  // offset of the first tap in the direction of travel from the sample
-  const float fxs = sx > 0 ? fx - 0.5f * kW : fx + 0.5f * kW - 1.0f;
-  const float fys = sy > 0 ? fy - 0.5f * kW : fy + 0.5f * kW - 1.0f;
-  const float fsx = (float)sx, fsy = (float)sy;
-  float2 c = s.sel ? s.c : make_float2(0.f, 0.f);
-  if (conj) c.y = -c.y;
-#pragma unroll
-  for (int m = 0; m < kW; ++m) {
-    p.px[m] = es_kernel(fxs + fsx * (float)m, bl2);
-    const float py = es_kernel(fys + fsy * (float)m, bl2);
-    p.b[m] = make_float2(c.x * py, c.y * py);
-  }
+  p.fxs = sx > 0 ? fx - 0.5f * kW : fx + 0.5f * kW - 1.0f;
+  p.fys = sy > 0 ? fy - 0.5f * kW : fy + 0.5f * kW - 1.0f;
+  p.c = s.sel ? s.c : make_float2(0.f, 0.f);
+  if (conj) p.c.y = -p.c.y;
 }
 
 // Per-lane shared-memory staging of the visibility stream: each lane keeps
@@ -372,10 +398,20 @@ grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restri
   {
     const Sample s0 = read_staged<HALF>(sb, 0, 0, lane, chan_scale, weight, flag, kf,
                                         obase + (size_t)c_begin * npol, c_begin, npol, pa, pb);
-    prepare(s0, s1hi, s1lo, s2hi, s2lo, cx, cy, sx, sy, t.conj, bl2, cur);
+    prepare(s0, s1hi, s1lo, s2hi, s2lo, cx, cy, sx, sy, t.conj, cur);
   }
   int ox = sx > 0 ? cur.kx0 : cur.kx0 + kW - 1;
   int oy = sy > 0 ? cur.ky0 : cur.ky0 + kW - 1;
+  int rx = 0, ry = 0;
+  const float fsx = (float)sx, fsy = (float)sy;
+  // offset of physical column p from the first tap, in the direction of
+  // travel: sx * ((p - rx) mod W); refreshed whenever the phase changes
+  float ofx[kWin], ofy[kWin];
+#pragma unroll
+  for (int p = 0; p < kWin; ++p) {
+    ofx[p] = fsx * (float)p;
+    ofy[p] = fsy * (float)p;
+  }
   const Sample none{make_float2(0.f, 0.f), make_float2(0.f, 0.f), false};
 #pragma unroll 1
   for (int ch = c_begin; ch < c_end; ++ch) {
@@ -401,27 +437,51 @@ grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restri
     int dx = sx > 0 ? cur.kx0 - ox : ox - (cur.kx0 + kW - 1);
     int dy = sy > 0 ? cur.ky0 - oy : oy - (cur.ky0 + kW - 1);
     if (dx < 0 || dy < 0 || dx >= kWin || dy >= kWin) {
-      flush_all(w, H, G, ox, oy, sx, sy);
+      flush_all(w, H, G, ox, oy, sx, sy, rx, ry);
       ox = sx > 0 ? cur.kx0 : cur.kx0 + kW - 1;
       oy = sy > 0 ? cur.ky0 : cur.ky0 + kW - 1;
+      rx = 0;
+      ry = 0;
       dx = 0;
       dy = 0;
+#pragma unroll
+      for (int p = 0; p < kWin; ++p) {
+        ofx[p] = fsx * (float)p;
+        ofy[p] = fsy * (float)p;
+      }
     }
-    while (dx > 0) { slide_x(w, H, G, ox, oy, sy); ox += sx; --dx; }
-    while (dy > 0) { slide_y(w, H, G, ox, oy, sx); oy += sy; --dy; }
+    if (dx > 0) {
+      do { slide_x(w, H, G, ox, oy, sy, rx, ry); ox += sx; rx = (rx + 1) & (kWin - 1); } while (--dx > 0);
+#pragma unroll
+      for (int p = 0; p < kWin; ++p) ofx[p] = fsx * (float)((p - rx) & (kWin - 1));
+    }
+    if (dy > 0) {
+      do { slide_y(w, H, G, ox, oy, sx, rx, ry); oy += sy; ry = (ry + 1) & (kWin - 1); } while (--dy > 0);
+#pragma unroll
+      for (int p = 0; p < kWin; ++p) ofy[p] = fsy * (float)((p - ry) & (kWin - 1));
+    }
     Prepared nxt;
-    prepare(sn, s1hi, s1lo, s2hi, s2lo, cx, cy, sx, sy, t.conj, bl2, nxt);
+    prepare(sn, s1hi, s1lo, s2hi, s2lo, cx, cy, sx, sy, t.conj, nxt);
+    // kernel values in physical order: physical index p holds tap (p - r) mod W
+    float px[kWin];
+    float2 b[kWin];
+#pragma unroll
+    for (int p = 0; p < kWin; ++p) {
+      px[p] = es_kernel(cur.fxs + ofx[p], bl2);
+      const float py = es_kernel(cur.fys + ofy[p], bl2);
+      b[p] = make_float2(cur.c.x * py, cur.c.y * py);
+    }
 #pragma unroll
     for (int j = 0; j < kWin; ++j)
 #pragma unroll
       for (int i = 0; i < kWin; ++i) {
-        w.a[j][i].x = fmaf(cur.px[i], cur.b[j].x, w.a[j][i].x);
-        w.a[j][i].y = fmaf(cur.px[i], cur.b[j].y, w.a[j][i].y);
+        w.a[j][i].x = fmaf(px[i], b[j].x, w.a[j][i].x);
+        w.a[j][i].y = fmaf(px[i], b[j].y, w.a[j][i].y);
       }
     cur = nxt;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
-  flush_all(w, H, G, ox, oy, sx, sy);
+  flush_all(w, H, G, ox, oy, sx, sy, rx, ry);
 }
 
 }  // namespace
