@@ -325,6 +325,28 @@ def run_reference(args):
                               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def profile_case(args):
+    """Small case for ncu captures: one MeerKAT-shaped snapshot resident on the
+    device, `--profile-case` passes of toi_grid + toi_image + tlisi_update."""
+    import torch
+
+    import paper_2512_06254_gb300 as toi
+    from paper_2512_06254_gb300 import synth
+    w = synth.meerkat_workload()
+    p = synth.make_snapshot(w, 3, device="cuda", uvw_index=3)
+    plan = toi.Plan(w.image_size, w.cell_arcsec, w.n_bl, w.n_chan, w.n_pol)
+    out = torch.empty(w.image_size // 32, w.image_size // 32, device="cuda")
+    for _ in range(args.profile_case):
+        plan.grid(p["uvw"], p["freq"], p["vis"], flag=p["flag"])
+        plan.image(0, None)
+        plan.tlisi_update(None, out)
+    torch.cuda.synchronize()
+    st = plan.sync_status()
+    print("profile case done, status", st)
+    if st != toi.TOI_OK:
+        raise SystemExit(1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,7 +360,12 @@ def main():
     ap.add_argument("--e2e-warmup", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=0,
+                    help="run N imaging passes of one snapshot (for ncu) and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
