@@ -178,6 +178,32 @@ toi_status tlisi_candidates(const float* cube, int32_t S, int32_t nty,
                             int32_t* nboxes, int32_t max_boxes,
                             double* scores);
 
+/* tlisi_candidates without any device allocation.  The paper has no
+ * counterpart; this serves callers that cannot allocate device memory when
+ * they search for candidates: a real-time pipeline that must not stall
+ * (cudaMalloc may synchronise the device), an application whose device
+ * memory is wholly owned by its own allocator, or code running where
+ * allocation is not permitted.
+ *
+ * Same arguments, outputs and results as tlisi_candidates.  The scratch is
+ * one fixed 16 MiB device array compiled into the library (every GPU that
+ * loads the library holds it until the process exits).  A cube whose search
+ * needs more than that (scratch grows as about 8 (S/2 + 1) nty ntx bytes,
+ * e.g. 64 x 64 tiles up to about 960 slices) is rejected with TOI_ERR_ARG
+ * and a message giving the size; use tlisi_candidates for those.  The
+ * array's device address is looked up once per device, with that device
+ * current, on the first call made there, so make that first call before any
+ * stream capture.  All calls on a device share the one array: calls whose
+ * GPU work overlaps (other streams, other host threads) race and must be
+ * serialised by the caller.  The array keeps the last call's contents; the
+ * search writes every scratch word before reading it, so nothing needs
+ * clearing.  Synchronises `stream`. */
+toi_status tlisi_candidates_noalloc(const float* cube, int32_t S, int32_t nty,
+                                    int32_t ntx, int32_t tile, int32_t mode,
+                                    void* stream, double* threshold, int32_t* boxes,
+                                    int32_t* nboxes, int32_t max_boxes,
+                                    double* scores);
+
 /* Adjoint of toi_image's linear map for grid slot `slot` (the paper's dirty
  * image is the adjoint of the measurement operator, Section 1): given
  * dL/dI for the standard-plane image (dev float32 [N][N]), writes

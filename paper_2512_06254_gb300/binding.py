@@ -30,6 +30,7 @@ BUF_GRID, BUF_TILTED, BUF_SNAP, BUF_RING = 0, 1, 2, 3
 
 EXPORTS = ("toi_config_default", "toi_plan", "toi_plan_destroy", "toi_set_stream", "toi_grid",
            "toi_image", "tlisi_update", "tlisi_reset", "tlisi_candidates",
+           "tlisi_candidates_noalloc",
            "toi_degrid_backward", "toi_plan_buffer", "toi_profile_enable", "toi_profile_read",
            "toi_sync_status", "toi_last_error", "toi_status_string")
 PROF_STAGES = ("prep", "bin", "grid", "fft_rows", "fft_cols", "reproject", "tlisi")
@@ -72,6 +73,7 @@ def lib():
         "tlisi_update": [P, P, P, C.POINTER(I)],
         "tlisi_reset": [P],
         "tlisi_candidates": [P, I, I, I, I, I, P, C.POINTER(D), P, C.POINTER(I), I, P],
+        "tlisi_candidates_noalloc": [P, I, I, I, I, I, P, C.POINTER(D), P, C.POINTER(I), I, P],
         "toi_degrid_backward": [P, I, P, P, P],
         "toi_plan_buffer": [P, I, I, P, C.c_int64, C.POINTER(C.c_int64)],
         "toi_profile_enable": [P, I],
@@ -245,6 +247,25 @@ def tlisi_candidates(cube, tile: int, mode: int, max_boxes: int = 256, scores=No
     _check(lib().tlisi_candidates(_ptr(cube), S, nty, ntx, tile, mode, _stream(stream),
                                   C.byref(thr), C.cast(boxes, C.c_void_p), C.byref(nb), max_boxes,
                                   _dev(scores, torch.float64, "scores")))
+    n = min(nb.value, max_boxes)
+    out = [[boxes[4 * i + j] for j in range(4)] for i in range(n)]
+    return thr.value, out, nb.value
+
+
+def tlisi_candidates_noalloc(cube, tile: int, mode: int, max_boxes: int = 256, scores=None,
+                             stream=None):
+    """tlisi_candidates using the library's fixed device scratch (no
+    allocation; see toi.h for the size limit and sharing rules)."""
+    import torch
+    if cube.dtype != torch.float32 or not cube.is_cuda or cube.dim() != 3:
+        raise ValueError("cube must be a 3-D float32 CUDA tensor")
+    S, nty, ntx = cube.shape
+    thr = C.c_double()
+    nb = C.c_int32()
+    boxes = (C.c_int32 * (4 * max(1, max_boxes)))()
+    _check(lib().tlisi_candidates_noalloc(_ptr(cube), S, nty, ntx, tile, mode, _stream(stream),
+                                          C.byref(thr), C.cast(boxes, C.c_void_p), C.byref(nb),
+                                          max_boxes, _dev(scores, torch.float64, "scores")))
     n = min(nb.value, max_boxes)
     out = [[boxes[4 * i + j] for j in range(4)] for i in range(n)]
     return thr.value, out, nb.value

@@ -122,6 +122,10 @@ void free_plan(toi_plan_s* p) {
 
 }  // namespace
 
+namespace toi {
+void set_planless_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace toi
+
 extern "C" {
 
 const char* toi_status_string(toi_status s) {
