@@ -22,7 +22,12 @@ It is a plain, slow, step-by-step restatement of the method in float64:
                              connected tiles -> bounding boxes, in a fixed FP64
                              evaluation order so that another implementation
                              of the same order reproduces it bit for bit.
-  adjoint                   degridding = exact adjoint of gridding
+  adjoint                   reverse mode of S2..S6 (Section 1 names the
+                             adjoint route to gradients): bilinear transpose,
+                             correction, forward DFT, ES degridding (the
+                             exact adjoint of gridding); sample, visibility
+                             and weight gradients with the plane fit fixed;
+                             point-source chain rule
 
 Exact-definition routines used as pins: ``dirty_image_dft`` (the 2-D dirty
 image of Section 3.2 evaluated by brute force).
@@ -34,6 +39,9 @@ Parity status per function (pins live in tests/):
   tlisi: parity unpinned against the paper (its formula is not printed);
     pinned only by invariants of the stand-in definition.
   candidates_*: pinned by planted cubes and an independent FFT cross-check.
+  *_adjoint, point_source_gradient: pinned by the adjoint identity
+    <A x, y> = <x, A^T y> against the forward routines, central finite
+    differences of the forward, and the brute-force DFT adjoint.
 """
 from __future__ import annotations
 
@@ -393,6 +401,135 @@ def image_snapshot(uvw_m, freq_hz, vis, flag, weight, N: int, cell_arcsec: float
     if keep_grid:
         out["grid"] = grid
     return out
+
+
+# ==========================================================================
+# Adjoint of S2..S6: reverse-mode derivative of one snapshot's image
+# (the "adjoint" the paper names as the route to gradients, Section 1)
+# ==========================================================================
+#
+# Convention: for a real loss L and a complex quantity z the gradient is
+# dL/dRe z + i dL/dIm z.  The plane fit of S1 (V, omega and the selection
+# w_q > 0) is piecewise constant in the weights and not differentiated with
+# respect to uvw, so it is held fixed.
+
+def bilinear_adjoint(grad: np.ndarray, j1, j2) -> np.ndarray:
+    """Transpose of bilinear(): every output cotangent is spread onto the four
+    source pixels with the interpolation weights, under the same rules (a
+    source position outside [0, N-1] contributes nothing; neighbours beyond
+    the last row/column are dropped)."""
+    N = grad.shape[0]
+    ok = (j1 >= 0) & (j1 <= N - 1) & (j2 >= 0) & (j2 <= N - 1)
+    a0 = np.floor(j1[ok]).astype(np.int64)
+    b0 = np.floor(j2[ok]).astype(np.int64)
+    fa = j1[ok] - a0
+    fb = j2[ok] - b0
+    g = grad[ok]
+    out = np.zeros((N + 1, N + 1))
+    np.add.at(out, (b0, a0), (1 - fb) * (1 - fa) * g)
+    np.add.at(out, (b0, a0 + 1), (1 - fb) * fa * g)
+    np.add.at(out, (b0 + 1, a0), fb * (1 - fa) * g)
+    np.add.at(out, (b0 + 1, a0 + 1), fb * fa * g)
+    return out[:N, :N]
+
+
+def reproject_adjoint(grad_image: np.ndarray, cell_arcsec: float, xi: float, eta: float,
+                      iters: int = 8) -> np.ndarray:
+    """Transpose of reproject(): cotangent of the tilted-plane image."""
+    N = grad_image.shape[0]
+    j1, j2 = reproject_source_pixels(N, cell_arcsec / 3600.0, xi, eta, iters)
+    return bilinear_adjoint(grad_image, j1, j2)
+
+
+def tilted_image_adjoint(grad_tilted: np.ndarray, G: int, W: int, beta: float,
+                         omega: float, sumw: float) -> np.ndarray:
+    """Transpose of tilted_image() with respect to the complex grid: the
+    tilted pixel j depends on Grid[k] through Re(Grid[k] e^{+i theta_kj}) s_j,
+    s_j = 1 / (psi_hat psi_hat omega sum w), so
+        dL/dGrid[k] = sum_j (dL/dT_j) s_j e^{-i theta_kj},
+    a forward centred DFT of the scaled cotangent zero-padded to G x G."""
+    N = grad_tilted.shape[0]
+    ph = correction_vector(N, G, W, beta)
+    U = grad_tilted / (ph[:, None] * ph[None, :]) / (omega * sumw)
+    pad = np.zeros((G, G))
+    lo = G // 2 - N // 2
+    pad[lo:lo + N, lo:lo + N] = U
+    return np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(pad)))
+
+
+def image_snapshot_adjoint(uvw_m, freq_hz, vis, flag, weight, N: int, cell_arcsec: float,
+                           grad_image: np.ndarray, W: int = 8, sigma: int = 2) -> Dict:
+    """Reverse mode of image_snapshot() for a loss L with dL/dImage =
+    grad_image.  Per (baseline, channel) sample q:
+      g[q]     = dL/dc_q, c_q = w_a V_a + w_b V_b (the gridded value): the
+                 ES degridding of the grid cotangent at the sample
+                 (degrid_es is the adjoint of grid_es); 0 outside the
+                 selection.
+      grad_vis = w_p g for the parallel hands p of selected samples, else 0.
+      grad_weight[p] = Re(conj(g) V_p) - <grad_image, image> / sum w for the
+                 unflagged parallel hands of selected samples (c_q is linear
+                 in w_p and the image carries 1 / sum w), else 0.
+    """
+    r = image_snapshot(uvw_m, freq_hz, vis, flag, weight, N, cell_arcsec, W, sigma)
+    G = sigma * N
+    beta = es_beta(W)
+    gt = reproject_adjoint(np.asarray(grad_image, dtype=np.float64), cell_arcsec,
+                           r["xi"], r["eta"])
+    H = tilted_image_adjoint(gt, G, W, beta, r["omega"], r["sumw"])
+    g_sel = degrid_es(H, r["g1"], r["g2"], W, beta)
+    vis = np.asarray(vis)
+    nbl, nch, n_pol = vis.shape
+    w_q, _ = sample_weights_and_values(vis, flag, weight)
+    sel = w_q > 0
+    g = np.zeros((nbl, nch), dtype=np.complex128)
+    g[sel] = g_sel
+    pa, pb = parallel_hands(n_pol)
+    f = np.asarray(flag).astype(bool)
+    wp = np.where(f, 0.0, 1.0 if weight is None else np.asarray(weight, dtype=np.float64))
+    dot = float((np.asarray(grad_image, dtype=np.float64) * r["image"]).sum())
+    grad_vis = np.zeros(vis.shape, dtype=np.complex128)
+    grad_weight = np.zeros(vis.shape)
+    for p in sorted({pa, pb}):
+        use = sel & ~f[:, :, p]
+        grad_vis[:, :, p] = np.where(sel, wp[:, :, p] * g, 0.0)
+        gw = (np.conj(g) * vis[:, :, p].astype(np.complex128)).real - dot / r["sumw"]
+        grad_weight[:, :, p] = np.where(use, gw, 0.0)
+    return dict(g=g, grad_vis=grad_vis, grad_weight=grad_weight, image=r["image"],
+                dot=dot, sumw=r["sumw"], omega=r["omega"])
+
+
+def point_source_vis(uvw_m, freq_hz, n_pol: int, l: float, m: float, flux: float):
+    """Measurement equation for one point source (Section 1): V = S exp(-2 pi
+    i (u l + v m + w (n - 1))), n = sqrt(1 - l^2 - m^2), in every parallel
+    hand (cross hands 0)."""
+    k = np.asarray(freq_hz, dtype=np.float64) / C_LIGHT
+    uvw = np.asarray(uvw_m, dtype=np.float64)
+    n = math.sqrt(1.0 - l * l - m * m)
+    ph = (uvw[:, 0:1] * l + uvw[:, 1:2] * m + uvw[:, 2:3] * (n - 1.0)) * k[None, :]
+    v = flux * np.exp(-2j * np.pi * ph)
+    out = np.zeros((uvw.shape[0], k.size, n_pol), dtype=np.complex128)
+    pa, pb = parallel_hands(n_pol)
+    out[:, :, pa] = v
+    out[:, :, pb] = v
+    return out
+
+
+def point_source_gradient(uvw_m, freq_hz, grad_vis, l: float, m: float, flux: float):
+    """Chain rule from grad_vis (dL/dRe V + i dL/dIm V per record) to the
+    point-source parameters of point_source_vis: dL/dtheta = sum Re(conj(
+    grad_vis) dV/dtheta), with dV/dS = V/S, dV/dl = -2 pi i k (u - w l / n) V,
+    dV/dm = -2 pi i k (v - w m / n) V."""
+    k = np.asarray(freq_hz, dtype=np.float64) / C_LIGHT
+    uvw = np.asarray(uvw_m, dtype=np.float64)
+    n = math.sqrt(1.0 - l * l - m * m)
+    ph = (uvw[:, 0:1] * l + uvw[:, 1:2] * m + uvw[:, 2:3] * (n - 1.0)) * k[None, :]
+    v = np.exp(-2j * np.pi * ph)                              # V / S
+    gsum = np.asarray(grad_vis).sum(axis=2)                   # same V in each hand
+    dl = -2j * np.pi * k[None, :] * (uvw[:, 0:1] - uvw[:, 2:3] * l / n) * flux * v
+    dm = -2j * np.pi * k[None, :] * (uvw[:, 1:2] - uvw[:, 2:3] * m / n) * flux * v
+    return dict(l=float((np.conj(gsum) * dl).real.sum()),
+                m=float((np.conj(gsum) * dm).real.sum()),
+                flux=float((np.conj(gsum) * v).real.sum()))
 
 
 def hermitian_half(grid: np.ndarray) -> np.ndarray:
