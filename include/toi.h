@@ -70,7 +70,11 @@ typedef struct {
   int32_t oversample;       /* sigma, grid = sigma N: 2 (default)               */
   int32_t tlisi_tile;       /* T, tLISI tile side: 32 (default); divides N      */
   int32_t grid_slots;       /* grid buffers held by the plan (>= 1; default 1)  */
-  int32_t reserved[6];      /* must be zero                                     */
+  int32_t grid_run;         /* channels each gridder lane walks: 0 = automatic
+                               (default), else 8..1024; a tuning knob that
+                               does not change results beyond float32
+                               summation order                                 */
+  int32_t reserved[5];      /* must be zero                                     */
 } toi_config;
 
 typedef struct toi_plan_s* toi_plan_t;
@@ -204,18 +208,34 @@ toi_status tlisi_candidates_noalloc(const float* cube, int32_t S, int32_t nty,
                                     int32_t* nboxes, int32_t max_boxes,
                                     double* scores);
 
-/* Adjoint of toi_image's linear map for grid slot `slot` (the paper's dirty
- * image is the adjoint of the measurement operator, Section 1): given
- * dL/dI for the standard-plane image (dev float32 [N][N]), writes
- *   grad_sample: dev float32 [n_bl][n_ch][2], g_q = dL/dc_q as (re, im)
- *                (c_q = w_q Vis_q, the weighted visibility), 0 for
- *                unselected samples;
- *   grad_weight: dev float32 [n_bl][n_ch] or NULL, dL/dw_q holding the
- *                visibilities fixed: (Re(conj(g_q) Vis_q) * sum_w - <I, dL/dI>) / sum_w.
- * Uses the uvw/freq/vis/weight/flag pointers of the last toi_grid call for
- * that slot, which must still be valid. */
-toi_status toi_degrid_backward(toi_plan_t plan, int32_t slot,
-                               const float* grad_image, float* grad_sample,
+/* Reverse mode of one snapshot's image (gridding, inverse FFT, correction,
+ * re-projection of toi_image) for a loss L whose gradient with respect to the
+ * standard-plane image is grad_image.  Section 1 of the paper notes that the
+ * dirty image is the adjoint of the measurement operator; this is that
+ * adjoint applied to dL/dI, followed by the chain rule to the inputs.  The
+ * plane fit (V, omega and the sample selection w_q > 0) is held fixed: it is
+ * piecewise constant in the weights.  Complex gradients are
+ * dL/dRe z + i dL/dIm z.
+ *   grad_image   dev float32 [N][N] (row = p2, col = p1, as toi_image's image).
+ *   image        dev float32 [N][N]: the image toi_image produced for this slot;
+ *                needed only for grad_weight (NULL otherwise).
+ *   grad_sample  dev complex64 [n_bl][n_ch] or NULL: g_q = dL/dc_q for the
+ *                gridded value c_q = w_a V_a + w_b V_b; 0 for unselected samples.
+ *   grad_vis     dev complex64 [n_bl][n_ch][n_pol] or NULL: w_p g_q for the
+ *                parallel hands p of selected samples, 0 elsewhere.
+ *   grad_weight  dev float32 [n_bl][n_ch][n_pol] or NULL: for unflagged
+ *                parallel hands of selected samples
+ *                Re(conj(g_q) V_p) - <grad_image, image> / sum w, else 0.
+ * At least one output must be non-NULL.  The inputs of the last toi_grid on
+ * `slot` (uvw, freq, vis, chan_scale, weight, flag) are read again and must
+ * still hold the same data; the slot's snapshot record (from toi_grid) gives
+ * V, omega and sum w.  The plan's tilted-image and FFT scratch and the slot's
+ * grid memory are used as workspace: a grid not yet imaged is discarded and
+ * the slot is left cleared for the next toi_grid.  Asynchronous on the
+ * plan's stream.  Errors: TOI_ERR_ARG (NULL or misaligned pointers, slot never
+ * gridded, grad_weight without image), TOI_ERR_CUDA. */
+toi_status toi_degrid_backward(toi_plan_t plan, int32_t slot, const float* grad_image,
+                               const float* image, void* grad_sample, void* grad_vis,
                                float* grad_weight);
 
 /* Copy of a plan-owned buffer, for checking intermediate stages:
@@ -231,10 +251,10 @@ toi_status toi_plan_buffer(toi_plan_t plan, int32_t which, int32_t slot, void* d
 
 /* Device-time accounting per stage of this plan, measured with CUDA events
  * recorded on the plan's stream around each stage's kernels.  Stages:
- * 0 plane fit (3 kernels), 1 binning (3 kernels), 2 gridding, 3 FFT rows,
+ * 0 plane fit (4 kernels), 1 reserved (always 0), 2 gridding, 3 FFT rows,
  * 4 FFT columns + correction, 5 re-projection + tLISI moments, 6 tLISI
- * finish / external-image moments.  Kernel launches are counted per stage
- * whether or not timing is enabled. */
+ * finish / external-image moments, 7 toi_degrid_backward.  Kernel launches
+ * are counted per stage whether or not timing is enabled. */
 toi_status toi_profile_enable(toi_plan_t plan, int32_t enable);
 
 /* Read and reset the accumulated milliseconds (ms[nstages], may be NULL) and

@@ -33,7 +33,7 @@ EXPORTS = ("toi_config_default", "toi_plan", "toi_plan_destroy", "toi_set_stream
            "tlisi_candidates_noalloc",
            "toi_degrid_backward", "toi_plan_buffer", "toi_profile_enable", "toi_profile_read",
            "toi_sync_status", "toi_last_error", "toi_status_string")
-PROF_STAGES = ("prep", "bin", "grid", "fft_rows", "fft_cols", "reproject", "tlisi")
+PROF_STAGES = ("prep", "bin", "grid", "fft_rows", "fft_cols", "reproject", "tlisi", "backward")
 
 
 class ToiError(RuntimeError):
@@ -47,7 +47,7 @@ class toi_config(C.Structure):
                 ("max_baselines", C.c_int32), ("max_channels", C.c_int32),
                 ("n_pol", C.c_int32), ("vis_dtype", C.c_int32), ("kernel_support", C.c_int32),
                 ("oversample", C.c_int32), ("tlisi_tile", C.c_int32), ("grid_slots", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("grid_run", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 _lib = None
@@ -74,7 +74,7 @@ def lib():
         "tlisi_reset": [P],
         "tlisi_candidates": [P, I, I, I, I, I, P, C.POINTER(D), P, C.POINTER(I), I, P],
         "tlisi_candidates_noalloc": [P, I, I, I, I, I, P, C.POINTER(D), P, C.POINTER(I), I, P],
-        "toi_degrid_backward": [P, I, P, P, P],
+        "toi_degrid_backward": [P, I, P, P, P, P, P],
         "toi_plan_buffer": [P, I, I, P, C.c_int64, C.POINTER(C.c_int64)],
         "toi_profile_enable": [P, I],
         "toi_profile_read": [P, P, P, I],
@@ -141,18 +141,20 @@ class Plan:
 
     def __init__(self, image_size: int, cell_arcsec: float, max_baselines: int,
                  max_channels: int, n_pol: int, *, vis_dtype: int = TOI_VIS_C64,
-                 tlisi_tile: int = 32, grid_slots: int = 1, stream=None):
+                 tlisi_tile: int = 32, grid_slots: int = 1, grid_run: int = 0, stream=None):
         import torch
         self.cfg = config_default(image_size, cell_arcsec, max_baselines, max_channels, n_pol)
         self.cfg.vis_dtype = vis_dtype
         self.cfg.tlisi_tile = tlisi_tile
         self.cfg.grid_slots = grid_slots
+        self.cfg.grid_run = grid_run
         self.N = image_size
         self.T = tlisi_tile
         h = C.c_void_p()
         _check(lib().toi_plan(C.byref(self.cfg), _stream(stream), C.byref(h)))
         self.handle = h.value
         self._torch = torch
+        self._generation = [0] * grid_slots
 
     # ---------------------------------------------------------------- calls
     def set_stream(self, stream):
@@ -167,6 +169,11 @@ class Plan:
                               _dev(vis, None, "vis"), _dev(chan_scale, t.float32, "chan_scale"),
                               _dev(weight, t.float32, "weight"), _dev(flag, t.uint8, "flag"),
                               nbl, nch, slot), self.handle)
+        self._generation[slot] += 1
+
+    def slot_generation(self, slot: int = 0) -> int:
+        """Number of toi_grid calls made on `slot` through this object."""
+        return self._generation[slot]
 
     def image(self, slot: int = 0, out=None, snap_info=None):
         t = self._torch
@@ -183,9 +190,18 @@ class Plan:
     def tlisi_reset(self):
         _check(lib().tlisi_reset(self.handle), self.handle)
 
-    def degrid_backward(self, grad_image, grad_sample, grad_weight=None, slot: int = 0):
-        _check(lib().toi_degrid_backward(self.handle, slot, _dev(grad_image), _dev(grad_sample),
-                                         _dev(grad_weight)), self.handle)
+    def degrid_backward(self, grad_image, image=None, grad_sample=None, grad_vis=None,
+                        grad_weight=None, slot: int = 0):
+        """toi_degrid_backward: fills the given output tensors (complex64
+        grad_sample [n_bl, n_ch], complex64 grad_vis [n_bl, n_ch, n_pol],
+        float32 grad_weight [n_bl, n_ch, n_pol]; image is toi_image's float32
+        output, needed for grad_weight)."""
+        t = self._torch
+        _check(lib().toi_degrid_backward(
+            self.handle, slot, _dev(grad_image, t.float32, "grad_image"),
+            _dev(image, t.float32, "image"), _dev(grad_sample, t.complex64, "grad_sample"),
+            _dev(grad_vis, t.complex64, "grad_vis"), _dev(grad_weight, t.float32, "grad_weight")),
+            self.handle)
 
     def buffer(self, which: int, slot: int = 0):
         """Copy of a plan-owned buffer as a new CUDA tensor (see toi_plan_buffer)."""

@@ -14,8 +14,6 @@ size_t candidates_scratch_bytes(int S, int nt);
 cudaError_t candidates_run(const float* cube, int S, int nty, int ntx, int T, int mode,
                            cudaStream_t st, void* scratch, double* scores_out, int max_boxes,
                            int* boxes_dev, double** thr_dev, int** nbox_dev);
-cudaError_t launch_degrid_backward(toi_plan_s* p, Slot& s, const float* grad_image,
-                                   float* grad_sample, float* grad_weight);
 
 // psi_hat(f) = integral over |x| <= W/2 of psi(x) cos(2 pi x f) dx for the
 // exponential of semicircle psi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)).
@@ -116,6 +114,7 @@ void free_plan(toi_plan_s* p) {
   cudaFree(p->tilted);
   for (int i = 0; i < 3; ++i) cudaFree(p->ring[i]);
   cudaFree(p->ring_max); cudaFree(p->tile_mom); cudaFree(p->d_status);
+  cudaFree(p->adj_scratch);
   for (cudaEvent_t ev : p->prof.ev) cudaEventDestroy(ev);
   delete p;
 }
@@ -187,7 +186,9 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     return fail(nullptr, TOI_ERR_ARG, "tlisi_tile must divide image_size");
   if (c.grid_slots < 1 || c.grid_slots > 16)
     return fail(nullptr, TOI_ERR_ARG, "grid_slots must be in [1, 16]");
-  for (int i = 0; i < 6; ++i)
+  if (c.grid_run != 0 && (c.grid_run < 8 || c.grid_run > 1024))
+    return fail(nullptr, TOI_ERR_ARG, "grid_run must be 0 (automatic) or in [8, 1024]");
+  for (int i = 0; i < 5; ++i)
     if (c.reserved[i] != 0) return fail(nullptr, TOI_ERR_ARG, "reserved fields must be zero");
   if ((long long)c.max_baselines * c.max_channels * c.n_pol > (1LL << 40))
     return fail(nullptr, TOI_ERR_ARG, "max_baselines x max_channels too large");
@@ -229,6 +230,7 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   TOI_ALLOC(p->ring_max, 3, "ring maxima");
   TOI_ALLOC(p->tile_mom, (size_t)ntl * 5, "tile moments");
   TOI_ALLOC(p->d_status, 1, "status word");
+  TOI_ALLOC(p->adj_scratch, toi::degrid_scratch_doubles(), "adjoint scratch");
 #undef TOI_ALLOC
   // constant tables, computed in float64 on the host
   float2* tw = new float2[G];
@@ -386,15 +388,28 @@ toi_status tlisi_candidates(const float* cube, int32_t S, int32_t nty, int32_t n
   return TOI_OK;
 }
 
+// NULL counts as aligned
+static bool aligned(const void* ptr, uintptr_t a) { return ((uintptr_t)ptr & (a - 1)) == 0; }
+
 toi_status toi_degrid_backward(toi_plan_t p, int32_t slot, const float* grad_image,
-                               float* grad_sample, float* grad_weight) {
+                               const float* image, void* grad_sample, void* grad_vis,
+                               float* grad_weight) {
   if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
   if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
-  if (!grad_image || !grad_sample) return fail(p, TOI_ERR_ARG, "grad_image and grad_sample must be non-NULL");
+  if (!grad_image) return fail(p, TOI_ERR_ARG, "grad_image must be non-NULL");
+  if (!grad_sample && !grad_vis && !grad_weight)
+    return fail(p, TOI_ERR_ARG, "at least one of grad_sample, grad_vis, grad_weight is needed");
+  if (grad_weight && !image) return fail(p, TOI_ERR_ARG, "grad_weight needs the image of toi_image");
   Slot& s = p->slots[slot];
   if (!s.uvw) return fail(p, TOI_ERR_ARG, "slot has not been gridded");
-  cudaError_t e = toi::launch_degrid_backward(p, s, grad_image, grad_sample, grad_weight);
-  if (e == cudaErrorNotSupported) return fail(p, TOI_ERR_UNSUPPORTED, "toi_degrid_backward not available");
+  if (!aligned(grad_image, 4) || !aligned(image, 4) || !aligned(grad_sample, 8) ||
+      !aligned(grad_vis, 8) || !aligned(grad_weight, 4))
+    return fail(p, TOI_ERR_ARG, "misaligned pointer (element alignment)");
+  cudaError_t e = toi::launch_degrid_backward(p, s, grad_image, image,
+                                              reinterpret_cast<float2*>(grad_sample),
+                                              reinterpret_cast<float2*>(grad_vis), grad_weight);
+  // the adjoint used the slot's grid memory (and left it cleared)
+  s.valid = false;
   if (e != cudaSuccess) return cuda_fail(p, e, "toi_degrid_backward");
   return TOI_OK;
 }

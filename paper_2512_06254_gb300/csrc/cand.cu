@@ -120,6 +120,37 @@ __device__ double pairwise_sum(const double* a, int lo, int hi) {
   return __dadd_rn(pairwise_sum(a, lo, mid), pairwise_sum(a, mid, hi));
 }
 
+// The pairwise tree of pairwise_sum(a, 0, n), evaluated by a whole block.
+// Cut the tree at the depth D with 2^D <= min(n, blockDim.x): while 2^D <= n
+// every node above that depth has at least two elements and splits in two, so
+// the top of the tree is a perfect binary tree over the 2^D depth-D subtrees.
+// Thread j sums subtree j (its interval follows from the bits of j, high bit
+// first: 0 takes the left half [lo, lo + m/2), 1 the right), then the 2^D
+// partial sums are combined level by level (node i adds children 2i, 2i + 1).
+// Additions and their order are exactly those of the recursion.  `sh` holds
+// blockDim.x doubles; every thread of the block must call this.
+__device__ double block_pairwise_sum(const double* a, int n, double* sh) {
+  int D = 0;
+  while ((2 << D) <= n && (2 << D) <= (int)blockDim.x) ++D;
+  const int L = 1 << D;
+  for (int j = threadIdx.x; j < L; j += blockDim.x) {
+    int lo = 0, m = n;
+    for (int b = D - 1; b >= 0; --b) {
+      const int h = m / 2;
+      if ((j >> b) & 1) { lo += h; m -= h; } else { m = h; }
+    }
+    sh[j] = pairwise_sum(a, lo, lo + m);
+  }
+  __syncthreads();
+  for (int half = L >> 1; half >= 1; half >>= 1) {
+    for (int i = threadIdx.x; i < half; i += blockDim.x) sh[i] = __dadd_rn(sh[2 * i], sh[2 * i + 1]);
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
 // One block: threshold, candidate mask, 8-connected labelling (label = first
 // tile of the component in raster order), boxes sorted by (y0, x0, label).
 __global__ void __launch_bounds__(1024)
@@ -130,16 +161,16 @@ label_kernel(const double* __restrict__ score, int nty, int ntx, int T, double k
   const int nt = nty * ntx;
   __shared__ double s_thr;
   __shared__ int s_nroot;
+  __shared__ double s_sum[1024];
+  const double mu = __ddiv_rn(block_pairwise_sum(score, nt, s_sum), (double)nt);
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    const double d = __dsub_rn(score[k], mu);
+    work[k] = __dmul_rn(d, d);
+  }
+  __syncthreads();
+  const double var = __ddiv_rn(block_pairwise_sum(work, nt, s_sum), (double)nt);
   if (threadIdx.x == 0) {
-    const double n = (double)nt;
-    const double mu = __ddiv_rn(pairwise_sum(score, 0, nt), n);
-    for (int k = 0; k < nt; ++k) {
-      const double d = __dsub_rn(score[k], mu);
-      work[k] = __dmul_rn(d, d);
-    }
-    const double var = __ddiv_rn(pairwise_sum(work, 0, nt), n);
-    const double sd = __dsqrt_rn(var);
-    s_thr = __dadd_rn(mu, __dmul_rn(ksig, sd));
+    s_thr = __dadd_rn(mu, __dmul_rn(ksig, __dsqrt_rn(var)));
     *thr_out = s_thr;
     s_nroot = 0;
   }

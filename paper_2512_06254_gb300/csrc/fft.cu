@@ -259,13 +259,96 @@ fft_cols_kernel(const float2* __restrict__ T, int N, const float2* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint passes (toi_degrid_backward).  The sample cotangents need
+//   Hbar[k'] = sum_j' U[j'] e^{-2 pi i (k1' j1' + k2' j2') / G}
+// for rows k2' = 0..R, U the real N x N cotangent (already scaled by the grid
+// correction and 1/(omega sum w)); rows k2' < 0 are conj(Hbar[-k']).  Both
+// passes run the same e^{+} transform core and use that U is real:
+//   pass A (columns, along j2'): Y[k2', j1'] = sum_j2' U e^{+2 pi i k2' j2' / G},
+//       two real columns per complex transform (Z = U_a + i U_b, then
+//       Y_a[k] = (Z[k] + conj Z[-k]) / 2, Y_b[k] = (Z[k] - conj Z[-k]) / 2i);
+//   pass B (rows, along j1'): K[k2', n] = sum_j1' (-1)^j1' Y[k2', j1'] e^{+2 pi i n j1' / G},
+//       n = k1' + G/2, so that Hbar[k2', n] = conj(K[k2', n]).
+// They are the adjoints of pass 2 and pass 1 of the image, with the same row
+// pruning.
+
+template <int G>
+__global__ void __launch_bounds__(ColCfg<G>::NT)
+fft_adj_cols_kernel(const float* __restrict__ U, int N, const float2* __restrict__ tw,
+                    const double* __restrict__ snap, float2* __restrict__ Y) {
+  constexpr int CW = ColCfg<G>::CW, LEN = ColCfg<G>::LEN;
+  extern __shared__ float2 x[];
+  const int col0 = blockIdx.x * CW;
+  const int rmax = row_limit(snap, G);
+  for (int e = threadIdx.x; e < 2 * LEN; e += blockDim.x) x[e] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int j2 = threadIdx.x; j2 < N; j2 += blockDim.x) {
+    const float4 u = *reinterpret_cast<const float4*>(U + (size_t)j2 * N + col0);
+    const int jp = j2 - N / 2;
+    const int m = pad(jp < 0 ? jp + G : jp);
+    x[m] = make_float2(u.x, u.y);          // columns col0, col0 + 1
+    x[LEN + m] = make_float2(u.z, u.w);    // columns col0 + 2, col0 + 3
+  }
+  __syncthreads();
+  fft_smem<G, 2, ColCfg<G>::NT>(x, tw);
+  for (int e = threadIdx.x; e < (rmax + 1) * 2; e += blockDim.x) {
+    const int r = e >> 1, pr = e & 1;
+    const float2* xs = x + (size_t)pr * LEN;
+    const float2 z = xs[pad(r)], zm = xs[pad((G - r) & (G - 1))];
+    const float4 o = make_float4(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y),
+                                 0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+    *reinterpret_cast<float4*>(Y + (size_t)r * N + col0 + 2 * pr) = o;
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(RowCfg<G>::NT)
+fft_adj_rows_kernel(const float2* __restrict__ Y, int N, const float2* __restrict__ tw,
+                    const double* __restrict__ snap, float2* __restrict__ K) {
+  extern __shared__ float2 x[];
+  const int row = blockIdx.x;
+  if (row > row_limit(snap, G)) return;
+  for (int n = threadIdx.x; n < G; n += blockDim.x) x[pad(n)] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const float2* src = Y + (size_t)row * N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const int jp = j - N / 2;
+    float2 v = src[j];
+    if (jp & 1) { v.x = -v.x; v.y = -v.y; }
+    x[pad(jp < 0 ? jp + G : jp)] = v;
+  }
+  __syncthreads();
+  fft_smem<G, 1, RowCfg<G>::NT>(x, tw);
+  float2* dst = K + (size_t)row * G;
+  for (int n = threadIdx.x; n < G; n += blockDim.x) dst[n] = x[pad(n)];
+}
+
 template <int G>
 cudaError_t configure_g() {
+  const int row_smem = (G + G / 8) * (int)sizeof(float2);
+  const int col_smem = 2 * ColCfg<G>::LEN * (int)sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (G + G / 8) * (int)sizeof(float2));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fft_cols_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              2 * ColCfg<G>::LEN * (int)sizeof(float2));
+                                       row_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_cols_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_adj_rows_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             row_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_adj_cols_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             col_smem);
+  return e;
+}
+
+template <int G>
+void launch_adj_g(toi_plan_s* p, Slot& s) {
+  const int N = p->N;
+  constexpr int CW = ColCfg<G>::CW;
+  fft_adj_cols_kernel<G><<<N / CW, ColCfg<G>::NT, 2 * ColCfg<G>::LEN * sizeof(float2), p->stream>>>(
+      p->tilted, N, p->twiddle, s.snap, p->fft_tmp);
+  fft_adj_rows_kernel<G><<<G / 2, RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
+      p->fft_tmp, N, p->twiddle, s.snap, s.grid);
 }
 
 template <int G>
@@ -304,6 +387,20 @@ cudaError_t launch_fft(toi_plan_s* p, Slot& s) {
     case 2048: launch_g<2048>(p, s); break;
     case 4096: launch_g<4096>(p, s); break;
     case 8192: launch_g<8192>(p, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_adjoint(toi_plan_s* p, Slot& s) {
+  switch (p->G) {
+    case 128: launch_adj_g<128>(p, s); break;
+    case 256: launch_adj_g<256>(p, s); break;
+    case 512: launch_adj_g<512>(p, s); break;
+    case 1024: launch_adj_g<1024>(p, s); break;
+    case 2048: launch_adj_g<2048>(p, s); break;
+    case 4096: launch_adj_g<4096>(p, s); break;
+    case 8192: launch_adj_g<8192>(p, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

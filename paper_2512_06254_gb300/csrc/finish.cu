@@ -46,6 +46,42 @@ __device__ void block_reduce_d(float (&v)[NV], double (*sh)[NV], double (&out)[N
     }
 }
 
+// Source of output pixel (o1, o2) in the tilted image: integer corner
+// (i1, i2), bilinear fractions (f1, f2) and whether it lies on the image.
+// K1 = -xi / beta, K2 = eta / beta, b2 = beta^2 (float32, from the snapshot
+// record).  Shared by the re-projection and its adjoint, so that both use
+// bit-identical positions and weights.
+struct Source {
+  int i1, i2;
+  float f1, f2;
+  bool ok;
+};
+
+__device__ __forceinline__ Source reproject_source(int o1, int o2, int N, float K1, float K2,
+                                                   float b2) {
+  const float D1 = (float)(o1 - N / 2), D2 = (float)(o2 - N / 2);
+  float e1 = 0.f, e2 = 0.f;
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    const float u1 = D1 + e1, u2 = D2 + e2;
+    const float q = b2 * (u1 * u1 + u2 * u2);
+    float rt;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(rt) : "f"(1.0f - q));
+    const float z = __fdividef(q, 1.0f + rt);
+    e1 = -K1 * z;
+    e2 = -K2 * z;
+  }
+  const float fl1 = floorf(e1), fl2 = floorf(e2);
+  Source r;
+  r.i1 = o1 + (int)fl1;
+  r.i2 = o2 + (int)fl2;
+  r.f1 = e1 - fl1;
+  r.f2 = e2 - fl2;
+  r.ok = r.i1 >= 0 && r.i2 >= 0 && (r.i1 < N - 1 || (r.i1 == N - 1 && r.f1 == 0.f)) &&
+         (r.i2 < N - 1 || (r.i2 == N - 1 && r.f2 == 0.f));
+  return r;
+}
+
 template <bool REPRO>
 __global__ void __launch_bounds__(kFinThreads)
 image_tile_kernel(const float* __restrict__ src, int N, int T, const double* __restrict__ snap,
@@ -68,56 +104,60 @@ image_tile_kernel(const float* __restrict__ src, int N, int T, const double* __r
   }
   __syncthreads();
   float sa = 0.f, sb = 0.f, saa = 0.f, sbb = 0.f, sab = 0.f, mx = 0.f;
-  for (int e = threadIdx.x; e < T * T; e += kFinThreads) {
-    const int o1 = tx * T + (e % T), o2 = ty * T + (e / T);
-    const size_t pix = (size_t)o2 * N + o1;
-    float v;
-    if (REPRO) {
-      const float K1 = kk[0], K2 = kk[1], b2 = kk[2];
-      const float D1 = (float)(o1 - N / 2), D2 = (float)(o2 - N / 2);
-      float e1 = 0.f, e2 = 0.f;
+  // kBatch pixels per thread at a time: all their sources first, then every
+  // load (clamped to valid addresses, so they issue back to back), then the
+  // arithmetic and the stores
+  constexpr int kBatch = 4;
+  for (int e0 = threadIdx.x; e0 < T * T; e0 += kBatch * kFinThreads) {
+    float v[kBatch], i1v[kBatch], i0v[kBatch];
+    size_t pixv[kBatch];
+    bool live[kBatch];
 #pragma unroll
-      for (int it = 0; it < 3; ++it) {
-        const float u1 = D1 + e1, u2 = D2 + e2;
-        const float q = b2 * (u1 * u1 + u2 * u2);
-        float rt;
-        asm("sqrt.approx.f32 %0, %1;" : "=f"(rt) : "f"(1.0f - q));
-        const float z = __fdividef(q, 1.0f + rt);
-        e1 = -K1 * z;
-        e2 = -K2 * z;
-      }
-      const float fl1 = floorf(e1), fl2 = floorf(e2);
-      const int i1 = o1 + (int)fl1, i2 = o2 + (int)fl2;
-      const float f1 = e1 - fl1, f2 = e2 - fl2;
-      const bool ok = i1 >= 0 && i2 >= 0 && (i1 < N - 1 || (i1 == N - 1 && f1 == 0.f)) &&
-                      (i2 < N - 1 || (i2 == N - 1 && f2 == 0.f));
-      v = 0.f;
-      if (ok) {
+    for (int b = 0; b < kBatch; ++b) {
+      const int e = e0 + b * kFinThreads;
+      live[b] = e < T * T;
+      const int ee = live[b] ? e : 0;
+      const int o1 = tx * T + (ee % T), o2 = ty * T + (ee / T);
+      const size_t pix = (size_t)o2 * N + o1;
+      pixv[b] = pix;
+      if (REPRO) {
+        const Source sr = reproject_source(o1, o2, N, kk[0], kk[1], kk[2]);
+        const bool ok = live[b] && sr.ok;
+        const int i1 = ok ? sr.i1 : 0, i2 = ok ? sr.i2 : 0;
+        const bool has1 = i1 + 1 < N, has2 = i2 + 1 < N;
         const float* r0 = src + (size_t)i2 * N;
-        const float a00 = r0[i1];
-        const float a01 = (i1 + 1 < N) ? r0[i1 + 1] : 0.f;
-        float a10 = 0.f, a11 = 0.f;
-        if (i2 + 1 < N) {
-          const float* r1 = r0 + N;
-          a10 = r1[i1];
-          a11 = (i1 + 1 < N) ? r1[i1 + 1] : 0.f;
-        }
-        v = (1.f - f2) * ((1.f - f1) * a00 + f1 * a01) + f2 * ((1.f - f1) * a10 + f1 * a11);
+        const float* r1 = has2 ? r0 + N : r0;
+        const int i1n = has1 ? i1 + 1 : i1;
+        const float a00 = r0[i1], a01r = r0[i1n], a10r = r1[i1], a11r = r1[i1n];
+        const float a01 = has1 ? a01r : 0.f;
+        const float a10 = has2 ? a10r : 0.f;
+        const float a11 = (has1 && has2) ? a11r : 0.f;
+        const float f1 = sr.f1, f2 = sr.f2;
+        const float val = (1.f - f2) * ((1.f - f1) * a00 + f1 * a01) + f2 * ((1.f - f1) * a10 + f1 * a11);
+        v[b] = ok ? val : 0.f;
+      } else {
+        v[b] = src[pix];
       }
-    } else {
-      v = src[pix];
+      if (with_moments) {
+        i1v[b] = ring_p1[pix];
+        i0v[b] = ring_p2[pix];
+      }
     }
-    ring_cur[pix] = v;
-    if (image_out) image_out[pix] = v;
-    mx = fmaxf(mx, fabsf(v));
-    if (with_moments) {
-      const float i1v = ring_p1[pix], i0v = ring_p2[pix];
-      const float a = i1v - i0v, b = v - i1v;
-      sa += a; sb += b; saa += a * a; sbb += b * b; sab += a * b;
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      if (!live[b]) continue;
+      ring_cur[pixv[b]] = v[b];
+      if (image_out) image_out[pixv[b]] = v[b];
+      mx = fmaxf(mx, fabsf(v[b]));
+      if (with_moments) {
+        const float a = i1v[b] - i0v[b], bd = v[b] - i1v[b];
+        sa += a; sb += bd; saa += a * a; sbb += bd * bd; sab += a * bd;
+      }
     }
   }
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, off));
   // order-free max of |I| (float bits of non-negative floats order like ints)
-  atomicMax(&smax, __float_as_uint(mx));
+  if ((threadIdx.x & 31) == 0) atomicMax(&smax, __float_as_uint(mx));
   if (with_moments) {
     float f5[5] = {sa, sb, saa, sbb, sab};
     double v5[5];
@@ -148,6 +188,54 @@ __global__ void tlisi_finish_kernel(const double* __restrict__ tile_mom, int ntl
   const double S = ((2.0 * mua * mub + C1) * (2.0 * cab + C2)) /
                    ((mua * mua + mub * mub + C1) * (va + vb + C2));
   out[t] = (float)((1.0 + S) * 0.5);
+}
+
+// Adjoint of the re-projection, as a gather (deterministic, no atomics):
+// tilted pixel j receives dL/dI(o) w(o, j) from every output pixel o whose
+// bilinear stencil covers j.  Those o lie within one pixel (plus the tiny
+// variation of the displacement over a pixel) of j + d(j), the forward map of
+// j, so a 4 x 4 window from floor(j + d(j)) - 1 covers them; each candidate's
+// source is recomputed with reproject_source and kept if j is one of its
+// corners.  The result is scaled by the grid correction and 1/(omega sum w),
+// giving the cotangent U that the adjoint FFT transforms.
+__global__ void __launch_bounds__(kFinThreads)
+reproject_adjoint_kernel(const float* __restrict__ gimg, int N, const double* __restrict__ snap,
+                         double beta_rad, const float* __restrict__ corr,
+                         float* __restrict__ ubar) {
+  const int j1 = blockIdx.x * 16 + (threadIdx.x & 15);
+  const int j2 = blockIdx.y * 16 + (threadIdx.x >> 4);
+  if (j1 >= N || j2 >= N) return;
+  const float K1 = (float)(-snap[SNAP_XI] / beta_rad);
+  const float K2 = (float)(snap[SNAP_ETA] / beta_rad);
+  const float b2 = (float)(beta_rad * beta_rad);
+  const double omega = snap[SNAP_OMEGA], sumw = snap[SNAP_SUMW];
+  const float norm = sumw > 0.0 ? (float)(1.0 / (omega * sumw)) : 0.f;
+  const float D1 = (float)(j1 - N / 2), D2 = (float)(j2 - N / 2);
+  const float q = b2 * (D1 * D1 + D2 * D2);
+  float rt;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(rt) : "f"(1.0f - q));
+  const float z = __fdividef(q, 1.0f + rt);
+  const int b1 = (int)floorf((float)j1 + K1 * z) - 1;
+  const int bb2 = (int)floorf((float)j2 + K2 * z) - 1;
+  float acc = 0.f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int o2 = bb2 + b;
+    if (o2 < 0 || o2 >= N) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int o1 = b1 + a;
+      if (o1 < 0 || o1 >= N) continue;
+      const Source sr = reproject_source(o1, o2, N, K1, K2, b2);
+      if (!sr.ok) continue;
+      const int dx = j1 - sr.i1, dy = j2 - sr.i2;
+      if ((unsigned)dx > 1u || (unsigned)dy > 1u) continue;
+      const float wx = dx ? sr.f1 : 1.f - sr.f1;
+      const float wy = dy ? sr.f2 : 1.f - sr.f2;
+      acc += wx * wy * gimg[(size_t)o2 * N + o1];
+    }
+  }
+  ubar[(size_t)j2 * N + j1] = acc * (norm * corr[j1] * corr[j2]);
 }
 
 }  // namespace
@@ -185,6 +273,17 @@ cudaError_t launch_tlisi_finalize(toi_plan_s* p, float* tlisi, int cur, int prev
                                                                 p->ring_max, cur, prev1, prev2,
                                                                 tlisi);
   prof_end(p, tok);
+  return cudaGetLastError();
+}
+
+}  // namespace toi
+
+namespace toi {
+
+cudaError_t launch_reproject_adjoint(toi_plan_s* p, Slot& s, const float* grad_image) {
+  const dim3 grid((p->N + 15) / 16, (p->N + 15) / 16);
+  reproject_adjoint_kernel<<<grid, kFinThreads, 0, p->stream>>>(grad_image, p->N, s.snap,
+                                                                 p->beta_rad, p->corr, p->tilted);
   return cudaGetLastError();
 }
 

@@ -498,6 +498,7 @@ cudaError_t launch_grid(toi_plan_s* p, Slot& s, const double* freq, const void* 
   // that there are several warps per SM slot (runs of at least 16 channels)
   int run = (nch + 63) / 64;
   if (run < 16) run = 16;
+  if (p->cfg.grid_run > 0) run = p->cfg.grid_run;
   const int nseg = (nch + 32 * run - 1) / (32 * run);
   const long long nwarps = 2LL * nbl * nseg;
   const int blocks = (int)((nwarps + kWarps - 1) / kWarps);

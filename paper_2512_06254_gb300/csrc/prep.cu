@@ -8,6 +8,7 @@
 // sums are the all-channel sums minus the (rare) deselected ones; with unit
 // weights the sum of weights is an exact integer count.
 #include <math.h>
+#include <stdint.h>
 
 #include "toi_internal.cuh"
 
@@ -79,14 +80,20 @@ prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict_
   __shared__ double sk_all[2];
   __shared__ double contrib[kMomWarps][11];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
+  if (wib == 0) {   // lanes take the channel-block partials in a fixed stride, then a tree
     double a = 0.0, b = 0.0;
-    for (int i = 0; i < nkblk; ++i) {
+    for (int i = lane; i < nkblk; i += 32) {
       a = __dadd_rn(a, kpart[2 * i]);
       b = __dadd_rn(b, kpart[2 * i + 1]);
     }
-    sk_all[0] = a;
-    sk_all[1] = b;
+    for (int off = 16; off > 0; off >>= 1) {
+      a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, off));
+      b = __dadd_rn(b, __shfl_down_sync(0xffffffffu, b, off));
+    }
+    if (lane == 0) {
+      sk_all[0] = a;
+      sk_all[1] = b;
+    }
   }
   __syncthreads();
   const int bl = blockIdx.x * kMomWarps + wib;
@@ -98,19 +105,9 @@ prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict_
     const size_t base = (size_t)bl * nch * npol;
     double sk = 0.0, sk2 = 0.0, sw = 0.0;
     long long nd = 0, cnt = 0;
-    for (int c = lane; c < nch; c += 32) {
+    // One channel: weights of the two parallel hands from its flags.
+    auto account = [&](int c, bool fa, bool fb) {
       const size_t o = base + (size_t)c * npol;
-      bool fa = false, fb = false;
-      if (flag) {
-        if (npol == 4) {
-          const unsigned int f4 = __ldcs(reinterpret_cast<const unsigned int*>(flag + o));
-          fa = (f4 & 0xffu) != 0;
-          fb = (f4 >> 24) != 0;
-        } else {
-          fa = flag[o + pa] != 0;
-          fb = flag[o + pb] != 0;
-        }
-      }
       float wa, wb;
       if (weight) {
         wa = fa ? 0.f : weight[o + pa];
@@ -128,6 +125,51 @@ prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict_
         sk += k;
         sk2 += k * k;
         nd += 1;
+      }
+    };
+    constexpr int U = 8;   // independent loads in flight per lane
+    if (npol == 4 && flag && (nch & 3) == 0 &&
+        (reinterpret_cast<uintptr_t>(flag) & 15) == 0) {
+      // 16 bytes = the 4 pols of 4 consecutive channels; 32 KB per warp in flight
+      const uint4* f16 = reinterpret_cast<const uint4*>(flag + base);
+      const int ngrp = nch >> 2;
+      for (int g0 = lane; g0 < ngrp; g0 += 32 * U) {
+        uint4 fv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int g = g0 + 32 * u;
+          fv[u] = g < ngrp ? __ldcs(f16 + g) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int g = g0 + 32 * u;
+          if (g >= ngrp) continue;
+          const unsigned int w4[4] = {fv[u].x, fv[u].y, fv[u].z, fv[u].w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            account(4 * g + i, (w4[i] & 0xffu) != 0, (w4[i] >> 24) != 0);
+        }
+      }
+    } else {
+      for (int c0 = lane; c0 < nch; c0 += 32 * U) {
+        unsigned int f4[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int c = c0 + 32 * u;
+          f4[u] = 0u;
+          if (c < nch && flag) {
+            const size_t o = base + (size_t)c * npol;
+            if (npol == 4)
+              f4[u] = __ldcs(reinterpret_cast<const unsigned int*>(flag + o));
+            else
+              f4[u] = (unsigned int)(flag[o + pa] != 0) | ((unsigned int)(flag[o + pb] != 0) << 24);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int c = c0 + 32 * u;
+          if (c < nch) account(c, (f4[u] & 0xffu) != 0, (f4[u] >> 24) != 0);
+        }
       }
     }
     // fixed-order warp reduction
@@ -174,26 +216,33 @@ __device__ bool smallest_eigvec(const double Cd[3][3], double v3[3]) {
       a[i][j] = (float)(Cd[i][j] / tr);
       e[i][j] = (i == j) ? 1.f : 0.f;
     }
+  // every index below is a compile-time constant after unrolling, so a and e
+  // stay in registers
   for (int sweep = 0; sweep < 12; ++sweep) {
     const float off = fabsf(a[0][1]) + fabsf(a[0][2]) + fabsf(a[1][2]);
     if (off < 1e-30f) break;
+#pragma unroll
     for (int p = 0; p < 2; ++p)
+#pragma unroll
       for (int q = p + 1; q < 3; ++q) {
         const float apq = a[p][q];
         if (apq == 0.f) continue;
         const float theta = (a[q][q] - a[p][p]) / (2.f * apq);
         const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
         const float c = rsqrtf(t * t + 1.f), s = t * c;
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
           const float akp = a[k][p], akq = a[k][q];
           a[k][p] = c * akp - s * akq;
           a[k][q] = s * akp + c * akq;
         }
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
           const float apk = a[p][k], aqk = a[q][k];
           a[p][k] = c * apk - s * aqk;
           a[q][k] = s * apk + c * aqk;
         }
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
           const float ekp = e[k][p], ekq = e[k][q];
           e[k][p] = c * ekp - s * ekq;
@@ -201,16 +250,20 @@ __device__ bool smallest_eigvec(const double Cd[3][3], double v3[3]) {
         }
       }
   }
+  const float d[3] = {a[0][0], a[1][1], a[2][2]};
   int imin = 0, imax = 0;
-  for (int i = 1; i < 3; ++i) {
-    if (a[i][i] < a[imin][imin]) imin = i;
-    if (a[i][i] > a[imax][imax]) imax = i;
-  }
+  if (d[1] < d[0]) imin = 1;
+  if (d[2] < (imin == 0 ? d[0] : d[1])) imin = 2;
+  if (d[1] > d[0]) imax = 1;
+  if (d[2] > (imax == 0 ? d[0] : d[1])) imax = 2;
   const int imid = (imin == imax) ? (imin + 1) % 3 : 3 - imin - imax;
-  const double lmax = fmax((double)a[imax][imax], 0.0), lmid = fmax((double)a[imid][imid], 0.0);
+  auto pick = [&](int i) { return i == 0 ? d[0] : (i == 1 ? d[1] : d[2]); };
+  const double lmax = fmax((double)pick(imax), 0.0), lmid = fmax((double)pick(imid), 0.0);
   // rank <= 1: the float32 estimate is ample for this 1e-6 test
   if (!(sqrt(lmid) > 1e-6 * sqrt(lmax))) return false;
-  const double u[3] = {e[0][imin], e[1][imin], e[2][imin]};
+  double u[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) u[r] = imin == 0 ? e[r][0] : (imin == 1 ? e[r][1] : e[r][2]);
   double Cu[3];
   for (int i = 0; i < 3; ++i) Cu[i] = Cd[i][0] * u[0] + Cd[i][1] * u[1] + Cd[i][2] * u[2];
   const double l = (u[0] * Cu[0] + u[1] * Cu[1] + u[2] * Cu[2]) / (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
@@ -218,6 +271,7 @@ __device__ bool smallest_eigvec(const double Cd[3][3], double v3[3]) {
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) M[i][j] = Cd[i][j] - (i == j ? l : 0.0);
   double best[3] = {0.0, 0.0, 0.0}, bn = -1.0;
+#pragma unroll
   for (int r = 0; r < 3; ++r) {
     const double* m1 = M[r];
     const double* m2 = M[(r + 1) % 3];
@@ -239,11 +293,14 @@ __device__ bool smallest_eigvec(const double Cd[3][3], double v3[3]) {
 
 __global__ void prep_finalize_kernel(const double* __restrict__ bpart, int nbpart,
                                      double* __restrict__ snap, int* status) {
+  // one warp per sum: lanes take partials in a fixed stride, then a fixed tree
   __shared__ double v[11];
-  if (threadIdx.x < 11) {
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = wib; i < 11; i += blockDim.x >> 5) {
     double a = 0.0;
-    for (int b = 0; b < nbpart; ++b) a += bpart[(size_t)b * 11 + threadIdx.x];
-    v[threadIdx.x] = a;
+    for (int b = lane; b < nbpart; b += 32) a += bpart[(size_t)b * 11 + i];
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) v[i] = a;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -330,7 +387,7 @@ cudaError_t launch_prep(toi_plan_s* p, Slot& s, const double* uvw, const double*
                                                      p->d_status);
   prep_baselines_kernel<<<nbblk, kMomWarps * 32, 0, p->stream>>>(
       flag, weight, p->kch, p->kch_sum, nkblk, uvw, nbl, nch, p->cfg.n_pol, p->bpart);
-  prep_finalize_kernel<<<1, 32, 0, p->stream>>>(p->bpart, nbblk, s.snap, p->d_status);
+  prep_finalize_kernel<<<1, 352, 0, p->stream>>>(p->bpart, nbblk, s.snap, p->d_status);
   prep_coef_kernel<<<(nbl + 127) / 128, 128, 0, p->stream>>>(uvw, nbl, nch, p->kch, s.snap,
                                                              p->beta_rad, p->G, p->W, s.coef,
                                                              p->d_status);

@@ -52,7 +52,7 @@ struct Slot {
 enum ProfStage {
   // PROF_BIN is reserved (the gridder needs no binning pass)
   PROF_PREP = 0, PROF_BIN, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_REPROJECT,
-  PROF_TLISI, PROF_NSTAGE
+  PROF_TLISI, PROF_BACKWARD, PROF_NSTAGE
 };
 
 struct ProfState {
@@ -88,6 +88,7 @@ struct toi_plan_s {
   unsigned int* ring_max = nullptr;      // [3] float bits of max |I|
   double* tile_mom = nullptr;            // [ntl][6]
   int* d_status = nullptr;               // device status word
+  double* adj_scratch = nullptr;         // partial sums and <dL/dI, I> of the adjoint
   long long nimg = 0;                    // images in the ring since reset
   const float* last_image = nullptr;     // output pointer of the last toi_image
   bool fused_pending = false;
@@ -112,6 +113,12 @@ cudaError_t launch_reproject_moments(toi_plan_s* p, Slot& s, float* image_out,
 cudaError_t launch_ring_moments(toi_plan_s* p, const float* image, int cur, int prev1,
                                 int prev2, bool with_moments);
 cudaError_t launch_tlisi_finalize(toi_plan_s* p, float* tlisi, int cur, int prev1, int prev2);
+
+// degrid.cu
+size_t degrid_scratch_doubles();
+cudaError_t launch_degrid_backward(toi_plan_s* p, Slot& s, const float* grad_image,
+                                   const float* image, float2* grad_sample, float2* grad_vis,
+                                   float* grad_weight);
 
 // host-side constant tables (api.cu)
 void es_fourier_table(int N, int G, int W, double beta_es, float* out);
