@@ -52,6 +52,7 @@ ALG_BYTES = {
 }
 
 
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):

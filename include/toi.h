@@ -74,7 +74,11 @@ typedef struct {
                                (default), else 8..1024; a tuning knob that
                                does not change results beyond float32
                                summation order                                 */
-  int32_t reserved[5];      /* must be zero                                     */
+  int32_t batch_max;        /* largest batch of toi_batch (0 = no batched path,
+                               default); each entry gets its own grid, FFT and
+                               tilted-image workspace, and the image ring
+                               holds batch_max + 2 images                       */
+  int32_t reserved[4];      /* must be zero                                     */
 } toi_config;
 
 typedef struct toi_plan_s* toi_plan_t;
@@ -208,6 +212,68 @@ toi_status tlisi_candidates_noalloc(const float* cube, int32_t S, int32_t nty,
                                     int32_t* nboxes, int32_t max_boxes,
                                     double* scores);
 
+/* One snapshot of a batch: the arguments of toi_grid (device pointers with
+ * the same layouts and rules) plus where toi_image would write its image
+ * (dev float32 [N][N] or NULL: the image then stays in the plan's ring). */
+typedef struct {
+  const double* uvw;
+  const double* freq;
+  const void* vis;
+  const float* chan_scale;
+  const float* weight;
+  const uint8_t* flag;
+  float* image;
+  int32_t n_bl;
+  int32_t n_ch;
+} toi_snapshot;
+
+/* Batched S1-S7 over n <= batch_max snapshots of the stream, in stream
+ * order, with one launch per stage for the whole batch (Section 4.3: the
+ * pipelined, stream-parallel execution of many snapshots; the batch may mix
+ * channel counts and flag fractions).  The gridder is persistent: its warps
+ * take (snapshot, track, segment) work items from a counter, so uneven
+ * snapshots share the GPU without a partial last wave per snapshot.
+ * Results equal n calls of toi_grid + toi_image + tlisi_update up to the
+ * float32 summation order of the gridder.
+ *
+ * toi_batch_prepare validates the snapshots on the host and fills the
+ * plan's pinned batch table; toi_batch_run enqueues the batch on the plan's
+ * stream (two table copies, then 10 kernels).  toi_batch_run makes no host
+ * call that a CUDA graph capture forbids, and its launch shapes do not
+ * depend on the batch, so one captured toi_batch_run can be replayed for
+ * every later batch: call toi_batch_prepare before each replay, after the
+ * previous replay's table copies have run (for instance after synchronising
+ * the stream).  Without capture, toi_batch_prepare waits for the previous
+ * batch's table copies itself.
+ *   tlisi        dev float32 [n][N/T][N/T] or NULL: row i receives the tLISI
+ *                of the three-image window ending with snapshot i.
+ *   first_valid  host, may be NULL: rows [first_valid, n) are written (the
+ *                first two images of a stream have no window).
+ * The batch uses its own grid slots (not those of toi_grid) and advances
+ * the same image stream as toi_image / tlisi_update.  Errors: TOI_ERR_ARG
+ * (batch_max = 0, n outside [1, batch_max], a snapshot failing toi_grid's
+ * checks, run without prepare), TOI_ERR_CUDA; data errors as for toi_grid,
+ * via toi_sync_status. */
+toi_status toi_batch_prepare(toi_plan_t plan, const toi_snapshot* snaps, int32_t n,
+                             float* tlisi, int32_t* first_valid);
+toi_status toi_batch_run(toi_plan_t plan);
+/* toi_batch_prepare followed by toi_batch_run. */
+toi_status toi_batch(toi_plan_t plan, const toi_snapshot* snaps, int32_t n, float* tlisi,
+                     int32_t* first_valid);
+
+/* Choose the gridder's channels per lane for each channel-count bucket
+ * (n_ch <= 1024, <= 2048, <= 4096, larger) present among the n sample
+ * snapshots, by timing the batched gridder for 16, 24, 32, 48 and 64
+ * channels per lane (best of three launches each, CUDA events).  The choice
+ * is cached in the plan and used by toi_grid and the batch when
+ * config.grid_run is 0.  runs_out[4] and us_out[4] (host, may be NULL)
+ * receive the chosen run and its gridding time per snapshot in
+ * microseconds for the buckets that were tuned.  Synchronous; needs
+ * batch_max >= n; leaves the stream position and the batch grids as they
+ * were.  Errors as toi_batch_prepare. */
+toi_status toi_autotune(toi_plan_t plan, const toi_snapshot* snaps, int32_t n, int32_t* runs_out,
+                        double* us_out);
+
 /* Reverse mode of one snapshot's image (gridding, inverse FFT, correction,
  * re-projection of toi_image) for a loss L whose gradient with respect to the
  * standard-plane image is grad_image.  Section 1 of the paper notes that the
@@ -253,8 +319,9 @@ toi_status toi_plan_buffer(toi_plan_t plan, int32_t which, int32_t slot, void* d
  * recorded on the plan's stream around each stage's kernels.  Stages:
  * 0 plane fit (4 kernels), 1 reserved (always 0), 2 gridding, 3 FFT rows,
  * 4 FFT columns + correction, 5 re-projection + tLISI moments, 6 tLISI
- * finish / external-image moments, 7 toi_degrid_backward.  Kernel launches
- * are counted per stage whether or not timing is enabled. */
+ * finish / external-image moments, 7 toi_degrid_backward.  toi_batch_run's
+ * kernels count under the same stages (one launch per stage per batch).
+ * Kernel launches are counted per stage whether or not timing is enabled. */
 toi_status toi_profile_enable(toi_plan_t plan, int32_t enable);
 
 /* Read and reset the accumulated milliseconds (ms[nstages], may be NULL) and

@@ -31,7 +31,8 @@ BUF_GRID, BUF_TILTED, BUF_SNAP, BUF_RING = 0, 1, 2, 3
 EXPORTS = ("toi_config_default", "toi_plan", "toi_plan_destroy", "toi_set_stream", "toi_grid",
            "toi_image", "tlisi_update", "tlisi_reset", "tlisi_candidates",
            "tlisi_candidates_noalloc",
-           "toi_degrid_backward", "toi_plan_buffer", "toi_profile_enable", "toi_profile_read",
+           "toi_degrid_backward", "toi_batch_prepare", "toi_batch_run", "toi_batch",
+           "toi_autotune", "toi_plan_buffer", "toi_profile_enable", "toi_profile_read",
            "toi_sync_status", "toi_last_error", "toi_status_string")
 PROF_STAGES = ("prep", "bin", "grid", "fft_rows", "fft_cols", "reproject", "tlisi", "backward")
 
@@ -47,7 +48,13 @@ class toi_config(C.Structure):
                 ("max_baselines", C.c_int32), ("max_channels", C.c_int32),
                 ("n_pol", C.c_int32), ("vis_dtype", C.c_int32), ("kernel_support", C.c_int32),
                 ("oversample", C.c_int32), ("tlisi_tile", C.c_int32), ("grid_slots", C.c_int32),
-                ("grid_run", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("grid_run", C.c_int32), ("batch_max", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class toi_snapshot(C.Structure):
+    _fields_ = [("uvw", C.c_void_p), ("freq", C.c_void_p), ("vis", C.c_void_p),
+                ("chan_scale", C.c_void_p), ("weight", C.c_void_p), ("flag", C.c_void_p),
+                ("image", C.c_void_p), ("n_bl", C.c_int32), ("n_ch", C.c_int32)]
 
 
 _lib = None
@@ -75,6 +82,10 @@ def lib():
         "tlisi_candidates": [P, I, I, I, I, I, P, C.POINTER(D), P, C.POINTER(I), I, P],
         "tlisi_candidates_noalloc": [P, I, I, I, I, I, P, C.POINTER(D), P, C.POINTER(I), I, P],
         "toi_degrid_backward": [P, I, P, P, P, P, P],
+        "toi_batch_prepare": [P, P, I, P, C.POINTER(I)],
+        "toi_batch_run": [P],
+        "toi_batch": [P, P, I, P, C.POINTER(I)],
+        "toi_autotune": [P, P, I, P, P],
         "toi_plan_buffer": [P, I, I, P, C.c_int64, C.POINTER(C.c_int64)],
         "toi_profile_enable": [P, I],
         "toi_profile_read": [P, P, P, I],
@@ -141,13 +152,15 @@ class Plan:
 
     def __init__(self, image_size: int, cell_arcsec: float, max_baselines: int,
                  max_channels: int, n_pol: int, *, vis_dtype: int = TOI_VIS_C64,
-                 tlisi_tile: int = 32, grid_slots: int = 1, grid_run: int = 0, stream=None):
+                 tlisi_tile: int = 32, grid_slots: int = 1, grid_run: int = 0, batch_max: int = 0,
+                 stream=None):
         import torch
         self.cfg = config_default(image_size, cell_arcsec, max_baselines, max_channels, n_pol)
         self.cfg.vis_dtype = vis_dtype
         self.cfg.tlisi_tile = tlisi_tile
         self.cfg.grid_slots = grid_slots
         self.cfg.grid_run = grid_run
+        self.cfg.batch_max = batch_max
         self.N = image_size
         self.T = tlisi_tile
         h = C.c_void_p()
@@ -202,6 +215,54 @@ class Plan:
             _dev(image, t.float32, "image"), _dev(grad_sample, t.complex64, "grad_sample"),
             _dev(grad_vis, t.complex64, "grad_vis"), _dev(grad_weight, t.float32, "grad_weight")),
             self.handle)
+
+    # ---------------------------------------------------------------- batch
+    def _snapshots(self, snaps):
+        """toi_snapshot array for a list of dicts (uvw, freq, vis, flag,
+        weight, chan_scale, image); the tensors are kept referenced."""
+        t = self._torch
+        arr = (toi_snapshot * len(snaps))()
+        for i, d in enumerate(snaps):
+            arr[i].uvw = _dev(d["uvw"], t.float64, "uvw")
+            arr[i].freq = _dev(d["freq"], t.float64, "freq")
+            arr[i].vis = _dev(d["vis"], None, "vis")
+            arr[i].chan_scale = _dev(d.get("chan_scale"), t.float32, "chan_scale")
+            arr[i].weight = _dev(d.get("weight"), t.float32, "weight")
+            arr[i].flag = _dev(d.get("flag"), t.uint8, "flag")
+            arr[i].image = _dev(d.get("image"), t.float32, "image")
+            arr[i].n_bl = d["uvw"].shape[0]
+            arr[i].n_ch = d["freq"].shape[0]
+        self._batch_refs = list(snaps)
+        return arr
+
+    def batch_prepare(self, snaps, tlisi=None) -> int:
+        """toi_batch_prepare; returns first_valid."""
+        arr = self._snapshots(snaps)
+        fv = C.c_int32(0)
+        _check(lib().toi_batch_prepare(self.handle, C.cast(arr, C.c_void_p), len(snaps),
+                                       _dev(tlisi, self._torch.float32, "tlisi"), C.byref(fv)),
+               self.handle)
+        return fv.value
+
+    def batch_run(self):
+        _check(lib().toi_batch_run(self.handle), self.handle)
+
+    def batch(self, snaps, tlisi=None) -> int:
+        """toi_batch (prepare + run); returns first_valid."""
+        arr = self._snapshots(snaps)
+        fv = C.c_int32(0)
+        _check(lib().toi_batch(self.handle, C.cast(arr, C.c_void_p), len(snaps),
+                               _dev(tlisi, self._torch.float32, "tlisi"), C.byref(fv)), self.handle)
+        return fv.value
+
+    def autotune(self, snaps):
+        """toi_autotune: ({bucket: run}, {bucket: microseconds per snapshot})."""
+        arr = self._snapshots(snaps)
+        runs = (C.c_int32 * 4)()
+        us = (C.c_double * 4)()
+        _check(lib().toi_autotune(self.handle, C.cast(arr, C.c_void_p), len(snaps),
+                                  C.cast(runs, C.c_void_p), C.cast(us, C.c_void_p)), self.handle)
+        return ({b: runs[b] for b in range(4) if runs[b]}, {b: us[b] for b in range(4) if runs[b]})
 
     def buffer(self, which: int, slot: int = 0):
         """Copy of a plan-owned buffer as a new CUDA tensor (see toi_plan_buffer)."""

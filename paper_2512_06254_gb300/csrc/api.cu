@@ -5,6 +5,7 @@
 
 #include <new>
 #include <string>
+#include <vector>
 
 #include "toi_internal.cuh"
 
@@ -87,6 +88,17 @@ toi_status cuda_fail(toi_plan_s* p, cudaError_t e, const char* where) {
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
+// lengths of the per-snapshot partial-sum buffers of the plane fit
+size_t kpart_len(int max_ch) { return 2 * (((size_t)max_ch + 255) / 256) + 2; }
+size_t bpart_len(int max_bl) { return 11 * (((size_t)max_bl + 7) / 8); }
+
+// ring position of stream image t (t may be negative for the images before
+// the first, which are never read)
+int ring_idx(const toi_plan_s* p, long long t) {
+  const long long R = (long long)p->ring.size();
+  return (int)(((t % R) + R) % R);
+}
+
 template <typename T>
 toi_status dev_alloc(toi_plan_s* p, T** ptr, size_t count, const char* what) {
   cudaError_t e = cudaMalloc((void**)ptr, sizeof(T) * (count ? count : 1));
@@ -112,9 +124,22 @@ void free_plan(toi_plan_s* p) {
   cudaFree(p->kch); cudaFree(p->kf); cudaFree(p->kch_sum); cudaFree(p->bpart);
   cudaFree(p->twiddle); cudaFree(p->corr); cudaFree(p->fft_tmp);
   cudaFree(p->tilted);
-  for (int i = 0; i < 3; ++i) cudaFree(p->ring[i]);
+  for (float* r : p->ring) cudaFree(r);
   cudaFree(p->ring_max); cudaFree(p->tile_mom); cudaFree(p->d_status);
   cudaFree(p->adj_scratch);
+  if (p->bslots) {
+    for (int i = 0; i < p->batch_max; ++i) {
+      cudaFree(p->bslots[i].grid);
+      cudaFree(p->bslots[i].snap);
+      cudaFree(p->bslots[i].coef);
+    }
+    delete[] p->bslots;
+  }
+  cudaFreeHost(p->bentry_host); cudaFreeHost(p->bheader_host);
+  cudaFree(p->bentry_dev); cudaFree(p->bheader_dev); cudaFree(p->bqueue);
+  cudaFree(p->b_kch); cudaFree(p->b_kf); cudaFree(p->b_kpart); cudaFree(p->b_bpart);
+  cudaFree(p->b_fft_tmp); cudaFree(p->b_tilted); cudaFree(p->b_tile_mom);
+  if (p->bcopied) cudaEventDestroy(p->bcopied);
   for (cudaEvent_t ev : p->prof.ev) cudaEventDestroy(ev);
   delete p;
 }
@@ -188,7 +213,9 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     return fail(nullptr, TOI_ERR_ARG, "grid_slots must be in [1, 16]");
   if (c.grid_run != 0 && (c.grid_run < 8 || c.grid_run > 1024))
     return fail(nullptr, TOI_ERR_ARG, "grid_run must be 0 (automatic) or in [8, 1024]");
-  for (int i = 0; i < 5; ++i)
+  if (c.batch_max < 0 || c.batch_max > 64)
+    return fail(nullptr, TOI_ERR_ARG, "batch_max must be in [0, 64]");
+  for (int i = 0; i < 4; ++i)
     if (c.reserved[i] != 0) return fail(nullptr, TOI_ERR_ARG, "reserved fields must be zero");
   if ((long long)c.max_baselines * c.max_channels * c.n_pol > (1LL << 40))
     return fail(nullptr, TOI_ERR_ARG, "max_baselines x max_channels too large");
@@ -220,17 +247,55 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   }
   TOI_ALLOC(p->kch, (size_t)c.max_channels, "channel table");
   TOI_ALLOC(p->kf, (size_t)c.max_channels, "channel table (float pairs)");
-  TOI_ALLOC(p->kch_sum, 2 * ((size_t)c.max_channels + 255) / 256 + 2, "channel sums");
-  TOI_ALLOC(p->bpart, 11 * (((size_t)c.max_baselines + 7) / 8), "plane-fit partial sums");
+  TOI_ALLOC(p->kch_sum, kpart_len(c.max_channels), "channel sums");
+  TOI_ALLOC(p->bpart, bpart_len(c.max_baselines), "plane-fit partial sums");
   TOI_ALLOC(p->twiddle, (size_t)G, "FFT twiddles");
   TOI_ALLOC(p->corr, (size_t)N, "grid correction");
   TOI_ALLOC(p->fft_tmp, (size_t)(G / 2) * N, "FFT intermediate");
   TOI_ALLOC(p->tilted, (size_t)N * N, "tilted image");
-  for (int i = 0; i < 3; ++i) TOI_ALLOC(p->ring[i], (size_t)N * N, "image ring");
-  TOI_ALLOC(p->ring_max, 3, "ring maxima");
+  const int R = c.batch_max + 2 > 3 ? c.batch_max + 2 : 3;
+  p->ring.assign(R, nullptr);
+  for (int i = 0; i < R; ++i) TOI_ALLOC(p->ring[i], (size_t)N * N, "image ring");
+  TOI_ALLOC(p->ring_max, (size_t)R, "ring maxima");
   TOI_ALLOC(p->tile_mom, (size_t)ntl * 5, "tile moments");
   TOI_ALLOC(p->d_status, 1, "status word");
   TOI_ALLOC(p->adj_scratch, toi::degrid_scratch_doubles(), "adjoint scratch");
+  p->batch_max = c.batch_max;
+  if (p->batch_max > 0) {
+    const int B = p->batch_max;
+    p->bslots = new (std::nothrow) Slot[B];
+    if (!p->bslots) { free_plan(p); return fail(nullptr, TOI_ERR_OOM, "host allocation failed"); }
+    for (int i = 0; i < B; ++i) {
+      TOI_ALLOC(p->bslots[i].grid, (size_t)(G / 2) * G, "batch grid");
+      TOI_ALLOC(p->bslots[i].snap, toi::SNAP_LEN, "batch snapshot record");
+      TOI_ALLOC(p->bslots[i].coef, (size_t)c.max_baselines, "batch baseline coefficients");
+    }
+    TOI_ALLOC(p->b_kch, (size_t)B * c.max_channels, "batch channel tables");
+    TOI_ALLOC(p->b_kf, (size_t)B * c.max_channels, "batch channel tables (float pairs)");
+    TOI_ALLOC(p->b_kpart, (size_t)B * kpart_len(c.max_channels), "batch channel sums");
+    TOI_ALLOC(p->b_bpart, (size_t)B * bpart_len(c.max_baselines), "batch plane-fit sums");
+    TOI_ALLOC(p->b_fft_tmp, (size_t)B * (G / 2) * N, "batch FFT intermediates");
+    TOI_ALLOC(p->b_tilted, (size_t)B * N * N, "batch tilted images");
+    TOI_ALLOC(p->b_tile_mom, (size_t)B * ntl * 5, "batch tile moments");
+    TOI_ALLOC(p->bentry_dev, (size_t)B, "batch table");
+    TOI_ALLOC(p->bheader_dev, 1, "batch header");
+    TOI_ALLOC(p->bqueue, 1, "gridder work counter");
+    e = cudaMallocHost((void**)&p->bentry_host, sizeof(toi::BatchEntry) * B);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->bheader_host, sizeof(toi::BatchHeader));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->bcopied, cudaEventDisableTiming);
+    if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "batch tables"); free_plan(p); return r; }
+    int dev = 0, nsm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = toi::grid_resident_blocks();
+    if (e != cudaSuccess || per_sm < 1) {
+      toi_status r = cuda_fail(nullptr, e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
+                               "persistent gridder occupancy");
+      free_plan(p);
+      return r;
+    }
+    p->grid_blocks = nsm * per_sm;
+  }
 #undef TOI_ALLOC
   // constant tables, computed in float64 on the host
   float2* tw = new float2[G];
@@ -246,10 +311,13 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   delete[] tw;
   delete[] corr;
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(p->ring_max, 0, 3 * sizeof(unsigned int));
-  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemset(p->ring[i], 0, sizeof(float) * N * N);
+  if (e == cudaSuccess) e = cudaMemset(p->ring_max, 0, p->ring.size() * sizeof(unsigned int));
+  for (size_t i = 0; i < p->ring.size() && e == cudaSuccess; ++i)
+    e = cudaMemset(p->ring[i], 0, sizeof(float) * N * N);
   for (int i = 0; i < p->nslot && e == cudaSuccess; ++i)
     e = cudaMemset(p->slots[i].grid, 0, sizeof(float2) * (size_t)(G / 2) * G);
+  for (int i = 0; i < p->batch_max && e == cudaSuccess; ++i)
+    e = cudaMemset(p->bslots[i].grid, 0, sizeof(float2) * (size_t)(G / 2) * G);
   if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "initialising plan tables"); free_plan(p); return r; }
   *out = p;
   return TOI_OK;
@@ -268,16 +336,15 @@ toi_status toi_set_stream(toi_plan_t plan, void* cuda_stream) {
   return TOI_OK;
 }
 
-toi_status toi_grid(toi_plan_t p, const double* uvw_m, const double* freq_hz, const void* vis,
-                    const float* chan_scale, const float* weight, const uint8_t* flag,
-                    int32_t n_bl, int32_t n_ch, int32_t slot) {
-  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+// Host checks of one snapshot's arguments (toi_grid and the batch).
+static toi_status check_snapshot(toi_plan_t p, const double* uvw_m, const double* freq_hz,
+                                 const void* vis, const float* chan_scale, const float* weight,
+                                 const uint8_t* flag, int32_t n_bl, int32_t n_ch) {
   if (!uvw_m || !freq_hz || !vis) return fail(p, TOI_ERR_ARG, "uvw, freq and vis must be non-NULL");
   if (n_bl < 1 || n_bl > p->cfg.max_baselines)
     return fail(p, TOI_ERR_ARG, "n_bl outside [1, max_baselines]");
   if (n_ch < 1 || n_ch > p->cfg.max_channels)
     return fail(p, TOI_ERR_ARG, "n_ch outside [1, max_channels]");
-  if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
   const bool half = p->cfg.vis_dtype == TOI_VIS_C16_CHANSCALE;
   if (half && !chan_scale) return fail(p, TOI_ERR_ARG, "chan_scale required for float16 visibilities");
   if (!half && chan_scale) return fail(p, TOI_ERR_ARG, "chan_scale given for float32 visibilities");
@@ -285,6 +352,16 @@ toi_status toi_grid(toi_plan_t p, const double* uvw_m, const double* freq_hz, co
       ((uintptr_t)weight & 3) || ((uintptr_t)chan_scale & 3) ||
       (p->cfg.n_pol == 4 && ((uintptr_t)flag & 3)))
     return fail(p, TOI_ERR_ARG, "misaligned input pointer (element alignment; flags of 4 pols: 4 bytes)");
+  return TOI_OK;
+}
+
+toi_status toi_grid(toi_plan_t p, const double* uvw_m, const double* freq_hz, const void* vis,
+                    const float* chan_scale, const float* weight, const uint8_t* flag,
+                    int32_t n_bl, int32_t n_ch, int32_t slot) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  const toi_status st = check_snapshot(p, uvw_m, freq_hz, vis, chan_scale, weight, flag, n_bl, n_ch);
+  if (st != TOI_OK) return st;
+  if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
   Slot& s = p->slots[slot];
   cudaError_t e;
   if (s.valid) {   // re-gridded before being imaged: start from zero again
@@ -308,8 +385,8 @@ toi_status toi_image(toi_plan_t p, int32_t slot, float* image, double* snap_info
   cudaError_t e = toi::launch_fft(p, s);
   if (e != cudaSuccess) return cuda_fail(p, e, "toi_image/fft");
   s.valid = false;   // the row pass consumed (and cleared) the grid
-  const int cur = (int)(p->nimg % 3);
-  const int prev1 = (int)((p->nimg + 2) % 3), prev2 = (int)((p->nimg + 1) % 3);
+  const int cur = ring_idx(p, p->nimg);
+  const int prev1 = ring_idx(p, p->nimg - 1), prev2 = ring_idx(p, p->nimg - 2);
   e = toi::launch_reproject_moments(p, s, image, p->nimg >= 2, cur, prev1, prev2);
   if (e != cudaSuccess) return cuda_fail(p, e, "toi_image/reproject");
   if (snap_info) {
@@ -323,14 +400,203 @@ toi_status toi_image(toi_plan_t p, int32_t slot, float* image, double* snap_info
   return TOI_OK;
 }
 
+
+// ---------------------------------------------------------------- batch --
+
+// Fill the host table for n snapshots: workspace of entry i, ring positions
+// of stream images nimg + i, outputs, and the gridder's work split (runs[i]
+// channels per lane).  Does not touch the plan's stream counters.
+static void fill_batch_table(toi_plan_t p, const toi_snapshot* snaps, int n, float* tlisi,
+                             const int* runs) {
+  const int N = p->N, G = p->G;
+  const int ntl = (N / p->T) * (N / p->T);
+  long long up = 0;
+  for (int i = 0; i < n; ++i) {
+    const toi_snapshot& sn = snaps[i];
+    toi::BatchEntry& e = p->bentry_host[i];
+    Slot& sl = p->bslots[i];
+    e.uvw = sn.uvw; e.freq = sn.freq; e.vis = sn.vis; e.chan_scale = sn.chan_scale;
+    e.weight = sn.weight; e.flag = sn.flag; e.nbl = sn.n_bl; e.nch = sn.n_ch;
+    e.grid = sl.grid; e.snap = sl.snap; e.coef = sl.coef;
+    e.kch = p->b_kch + (size_t)i * p->cfg.max_channels;
+    e.kf = p->b_kf + (size_t)i * p->cfg.max_channels;
+    e.kpart = p->b_kpart + (size_t)i * kpart_len(p->cfg.max_channels);
+    e.bpart = p->b_bpart + (size_t)i * bpart_len(p->cfg.max_baselines);
+    e.fft_tmp = p->b_fft_tmp + (size_t)i * (G / 2) * N;
+    e.tilted = p->b_tilted + (size_t)i * N * N;
+    e.tile_mom = p->b_tile_mom + (size_t)i * ntl * 5;
+    const long long t = p->nimg + i;
+    const int cur = ring_idx(p, t), p1 = ring_idx(p, t - 1), p2 = ring_idx(p, t - 2);
+    e.ring_cur = p->ring[cur]; e.ring_p1 = p->ring[p1]; e.ring_p2 = p->ring[p2];
+    e.max_cur = p->ring_max + cur; e.max_p1 = p->ring_max + p1; e.max_p2 = p->ring_max + p2;
+    e.image_out = sn.image;
+    e.with_moments = t >= 2 ? 1 : 0;
+    e.tlisi_out = (tlisi && t >= 2) ? tlisi + (size_t)i * ntl : nullptr;
+    e.run = runs[i];
+    e.nseg = (sn.n_ch + 32 * e.run - 1) / (32 * e.run);
+    e.up_begin = up;
+    up += (long long)sn.n_bl * e.nseg;
+  }
+  long long mi = up;
+  for (int i = 0; i < n; ++i) {
+    toi::BatchEntry& e = p->bentry_host[i];
+    e.mi_begin = mi;
+    mi += (long long)e.nbl * e.nseg;
+  }
+  p->bheader_host->n = n;
+  p->bheader_host->pad = 0;
+  p->bheader_host->total_items = mi;
+}
+
+static int lane_run(toi_plan_t p, int nch) {
+  if (p->cfg.grid_run > 0) return p->cfg.grid_run;
+  const int t = p->tuned_run[toi::channel_bucket(nch)];
+  return t > 0 ? t : toi::grid_default_run(nch);
+}
+
+static toi_status check_batch(toi_plan_t p, const toi_snapshot* snaps, int32_t n) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  if (p->batch_max < 1) return fail(p, TOI_ERR_ARG, "the plan was made with batch_max = 0");
+  if (!snaps || n < 1 || n > p->batch_max)
+    return fail(p, TOI_ERR_ARG, "need 1 <= n <= batch_max snapshots");
+  for (int i = 0; i < n; ++i) {
+    const toi_snapshot& sn = snaps[i];
+    const toi_status st = check_snapshot(p, sn.uvw, sn.freq, sn.vis, sn.chan_scale, sn.weight,
+                                         sn.flag, sn.n_bl, sn.n_ch);
+    if (st != TOI_OK) return fail(p, st, "snapshot " + std::to_string(i) + ": " + p->err);
+    if ((uintptr_t)sn.image & 3) return fail(p, TOI_ERR_ARG, "misaligned image pointer");
+  }
+  return TOI_OK;
+}
+
+toi_status toi_batch_prepare(toi_plan_t p, const toi_snapshot* snaps, int32_t n, float* tlisi,
+                             int32_t* first_valid) {
+  const toi_status st = check_batch(p, snaps, n);
+  if (st != TOI_OK) return st;
+  if ((uintptr_t)tlisi & 3) return fail(p, TOI_ERR_ARG, "misaligned tlisi pointer");
+  // the previous batch's table must have been copied before it is rewritten
+  if (p->bcopied_pending) {
+    cudaError_t e = cudaEventSynchronize(p->bcopied);
+    if (e != cudaSuccess) return cuda_fail(p, e, "toi_batch_prepare");
+    p->bcopied_pending = false;
+  }
+  std::vector<int> runs(n);
+  for (int i = 0; i < n; ++i) runs[i] = lane_run(p, snaps[i].n_ch);
+  fill_batch_table(p, snaps, n, tlisi, runs.data());
+  const long long t0 = p->nimg;
+  if (first_valid) {
+    const long long fv = 2 - t0;
+    *first_valid = (int32_t)(fv < 0 ? 0 : (fv > n ? n : fv));
+  }
+  p->nimg += n;
+  p->last_image = snaps[n - 1].image ? snaps[n - 1].image : p->ring[ring_idx(p, p->nimg - 1)];
+  p->fused_pending = false;
+  p->bn = n;
+  return TOI_OK;
+}
+
+toi_status toi_batch_run(toi_plan_t p) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  if (p->batch_max < 1) return fail(p, TOI_ERR_ARG, "the plan was made with batch_max = 0");
+  if (p->bn < 1) return fail(p, TOI_ERR_ARG, "no batch prepared since the last toi_batch_run");
+  cudaError_t e = cudaMemcpyAsync(p->bentry_dev, p->bentry_host,
+                                  sizeof(toi::BatchEntry) * p->batch_max, cudaMemcpyHostToDevice,
+                                  p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->bheader_dev, p->bheader_host, sizeof(toi::BatchHeader),
+                        cudaMemcpyHostToDevice, p->stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (e == cudaSuccess) e = cudaStreamIsCapturing(p->stream, &cap);
+  if (e == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+    e = cudaEventRecord(p->bcopied, p->stream);
+    p->bcopied_pending = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = toi::launch_prep_batch(p);
+  if (e == cudaSuccess) e = toi::launch_grid_batch(p, p->cfg.vis_dtype == TOI_VIS_C16_CHANSCALE);
+  if (e == cudaSuccess) e = toi::launch_fft_batch(p);
+  if (e == cudaSuccess) e = toi::launch_finish_batch(p);
+  p->bn = 0;
+  if (e != cudaSuccess) return cuda_fail(p, e, "toi_batch_run");
+  return TOI_OK;
+}
+
+toi_status toi_batch(toi_plan_t p, const toi_snapshot* snaps, int32_t n, float* tlisi,
+                     int32_t* first_valid) {
+  const toi_status st = toi_batch_prepare(p, snaps, n, tlisi, first_valid);
+  if (st != TOI_OK) return st;
+  return toi_batch_run(p);
+}
+
+toi_status toi_autotune(toi_plan_t p, const toi_snapshot* snaps, int32_t n, int32_t* runs_out,
+                        double* us_out) {
+  const toi_status st = check_batch(p, snaps, n);
+  if (st != TOI_OK) return st;
+  static const int kCand[] = {16, 24, 32, 48, 64};
+  constexpr int kNc = (int)(sizeof(kCand) / sizeof(kCand[0]));
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (p->bcopied_pending && e == cudaSuccess) e = cudaEventSynchronize(p->bcopied);
+  p->bcopied_pending = false;
+  const long long nimg0 = p->nimg;
+  for (int bucket = 0; bucket < 4 && e == cudaSuccess; ++bucket) {
+    // the sample snapshots of this channel bucket
+    std::vector<toi_snapshot> sub;
+    for (int i = 0; i < n; ++i)
+      if (toi::channel_bucket(snaps[i].n_ch) == bucket) sub.push_back(snaps[i]);
+    if (sub.empty()) continue;
+    for (auto& sn : sub) sn.image = nullptr;
+    double best = 1e300;
+    int best_run = 0;
+    for (int c = 0; c < kNc && e == cudaSuccess; ++c) {
+      std::vector<int> runs(sub.size(), kCand[c]);
+      fill_batch_table(p, sub.data(), (int)sub.size(), nullptr, runs.data());
+      e = cudaMemcpyAsync(p->bentry_dev, p->bentry_host, sizeof(toi::BatchEntry) * p->batch_max,
+                          cudaMemcpyHostToDevice, p->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->bheader_dev, p->bheader_host, sizeof(toi::BatchHeader),
+                            cudaMemcpyHostToDevice, p->stream);
+      if (e == cudaSuccess) e = toi::launch_prep_batch(p);
+      double t_min = 1e300;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        for (size_t i = 0; i < sub.size() && e == cudaSuccess; ++i)
+          e = cudaMemsetAsync(p->bslots[i].grid, 0, sizeof(float2) * (size_t)(p->G / 2) * p->G,
+                              p->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(a, p->stream);
+        if (e == cudaSuccess) e = toi::launch_grid_batch(p, p->cfg.vis_dtype == TOI_VIS_C16_CHANSCALE);
+        if (e == cudaSuccess) e = cudaEventRecord(b, p->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && ms < t_min) t_min = ms;
+      }
+      if (e == cudaSuccess && t_min < best) { best = t_min; best_run = kCand[c]; }
+    }
+    if (e == cudaSuccess) {
+      p->tuned_run[bucket] = best_run;
+      if (runs_out) runs_out[bucket] = best_run;
+      if (us_out) us_out[bucket] = best * 1e3 / (double)sub.size();
+    }
+  }
+  // leave the batch grids zero and the stream position untouched
+  for (int i = 0; i < p->batch_max && e == cudaSuccess; ++i)
+    e = cudaMemsetAsync(p->bslots[i].grid, 0, sizeof(float2) * (size_t)(p->G / 2) * p->G, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  p->nimg = nimg0;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(p, e, "toi_autotune");
+  return TOI_OK;
+}
+
 toi_status tlisi_update(toi_plan_t p, const float* image, float* tlisi, int32_t* valid) {
   if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
   if (!valid) return fail(p, TOI_ERR_ARG, "valid must be non-NULL");
   const bool fused = p->fused_pending && (image == nullptr || image == p->last_image);
   if (!fused) {
     if (!image) return fail(p, TOI_ERR_ARG, "no image given and none pending from toi_image");
-    const int cur = (int)(p->nimg % 3);
-    const int prev1 = (int)((p->nimg + 2) % 3), prev2 = (int)((p->nimg + 1) % 3);
+    const int cur = ring_idx(p, p->nimg);
+    const int prev1 = ring_idx(p, p->nimg - 1), prev2 = ring_idx(p, p->nimg - 2);
     cudaError_t e = toi::launch_ring_moments(p, image, cur, prev1, prev2, p->nimg >= 2);
     if (e != cudaSuccess) return cuda_fail(p, e, "tlisi_update/moments");
     p->nimg += 1;
@@ -338,8 +604,8 @@ toi_status tlisi_update(toi_plan_t p, const float* image, float* tlisi, int32_t*
   p->fused_pending = false;
   if (p->nimg < 3) { *valid = 0; return TOI_OK; }
   if (!tlisi) return fail(p, TOI_ERR_ARG, "tlisi must be non-NULL");
-  const int cur = (int)((p->nimg - 1) % 3);
-  const int prev1 = (int)((p->nimg + 1) % 3), prev2 = (int)(p->nimg % 3);
+  const int cur = ring_idx(p, p->nimg - 1);
+  const int prev1 = ring_idx(p, p->nimg - 2), prev2 = ring_idx(p, p->nimg - 3);
   cudaError_t e = toi::launch_tlisi_finalize(p, tlisi, cur, prev1, prev2);
   if (e != cudaSuccess) return cuda_fail(p, e, "tlisi_update/finish");
   *valid = 1;
@@ -424,7 +690,7 @@ toi_status toi_plan_buffer(toi_plan_t p, int32_t which, int32_t slot, void* dst,
     case 0: src = p->slots[slot].grid; *nbytes = (int64_t)(p->G / 2) * p->G * 8; break;
     case 1: src = p->tilted; *nbytes = NN * 4; break;
     case 2: src = p->slots[slot].snap; *nbytes = toi::SNAP_LEN * 8; break;
-    case 3: src = p->ring[(p->nimg + 2) % 3]; *nbytes = NN * 4; break;
+    case 3: src = p->ring[ring_idx(p, p->nimg - 1)]; *nbytes = NN * 4; break;
     default: return fail(p, TOI_ERR_ARG, "unknown buffer");
   }
   if (dst) {

@@ -177,11 +177,11 @@ struct RowCfg {
 };
 
 template <int G>
-__global__ void __launch_bounds__(RowCfg<G>::NT)
-fft_rows_kernel(float2* __restrict__ H, int N, const float2* __restrict__ tw,
-                const double* __restrict__ snap, float2* __restrict__ T) {
+__device__ __forceinline__ void fft_rows_body(float2* __restrict__ H, int N,
+                                              const float2* __restrict__ tw,
+                                              const double* __restrict__ snap,
+                                              float2* __restrict__ T, int row) {
   extern __shared__ float2 x[];
-  const int row = blockIdx.x;
   if (row > row_limit(snap, G)) return;
   float2* src = H + (size_t)row * G;
   constexpr int PER = (G + RowCfg<G>::NT - 1) / RowCfg<G>::NT;
@@ -210,6 +210,22 @@ fft_rows_kernel(float2* __restrict__ H, int N, const float2* __restrict__ tw,
 }
 
 template <int G>
+__global__ void __launch_bounds__(RowCfg<G>::NT)
+fft_rows_kernel(float2* __restrict__ H, int N, const float2* __restrict__ tw,
+                const double* __restrict__ snap, float2* __restrict__ T) {
+  fft_rows_body<G>(H, N, tw, snap, T, blockIdx.x);
+}
+
+template <int G>
+__global__ void __launch_bounds__(RowCfg<G>::NT)
+fft_rows_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
+               const float2* __restrict__ tw) {
+  if ((int)blockIdx.y >= hdr->n) return;
+  const BatchEntry& e = E[blockIdx.y];
+  fft_rows_body<G>(e.grid, N, tw, e.snap, e.fft_tmp, blockIdx.x);
+}
+
+template <int G>
 struct ColCfg {
   static constexpr int CW = 4;            // columns per block: two complex transforms
   static constexpr int NT = 512;
@@ -217,13 +233,14 @@ struct ColCfg {
 };
 
 template <int G>
-__global__ void __launch_bounds__(ColCfg<G>::NT)
-fft_cols_kernel(const float2* __restrict__ T, int N, const float2* __restrict__ tw,
-                const float* __restrict__ corr, const double* __restrict__ snap,
-                float* __restrict__ out) {
+__device__ __forceinline__ void fft_cols_body(const float2* __restrict__ T, int N,
+                                              const float2* __restrict__ tw,
+                                              const float* __restrict__ corr,
+                                              const double* __restrict__ snap,
+                                              float* __restrict__ out, int blk) {
   constexpr int CW = ColCfg<G>::CW, LEN = ColCfg<G>::LEN;
   extern __shared__ float2 x[];
-  const int col0 = blockIdx.x * CW;
+  const int col0 = blk * CW;
   constexpr int half = G / 2;
   const int rmax = row_limit(snap, G);
   for (int e = threadIdx.x; e < half * 2; e += blockDim.x) {
@@ -257,6 +274,23 @@ fft_cols_kernel(const float2* __restrict__ T, int N, const float2* __restrict__ 
     o.w = z1.y * (s * cd);
     *reinterpret_cast<float4*>(out + (size_t)j2 * N + col0) = o;
   }
+}
+
+template <int G>
+__global__ void __launch_bounds__(ColCfg<G>::NT)
+fft_cols_kernel(const float2* __restrict__ T, int N, const float2* __restrict__ tw,
+                const float* __restrict__ corr, const double* __restrict__ snap,
+                float* __restrict__ out) {
+  fft_cols_body<G>(T, N, tw, corr, snap, out, blockIdx.x);
+}
+
+template <int G>
+__global__ void __launch_bounds__(ColCfg<G>::NT)
+fft_cols_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
+               const float2* __restrict__ tw, const float* __restrict__ corr) {
+  if ((int)blockIdx.y >= hdr->n) return;
+  const BatchEntry& e = E[blockIdx.y];
+  fft_cols_body<G>(e.fft_tmp, N, tw, corr, e.snap, e.tilted, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -338,7 +372,25 @@ cudaError_t configure_g() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fft_adj_cols_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              col_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_rows_batch<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_cols_batch<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
   return e;
+}
+
+template <int G>
+void launch_batch_g(toi_plan_s* p) {
+  const int N = p->N, B = p->batch_max;
+  constexpr int CW = ColCfg<G>::CW;
+  int tok = prof_begin(p, PROF_FFT_ROWS, 1);
+  fft_rows_batch<G><<<dim3(G / 2, B), RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
+      p->bentry_dev, p->bheader_dev, N, p->twiddle);
+  prof_end(p, tok);
+  tok = prof_begin(p, PROF_FFT_COLS, 1);
+  fft_cols_batch<G><<<dim3(N / CW, B), ColCfg<G>::NT, 2 * ColCfg<G>::LEN * sizeof(float2),
+                      p->stream>>>(p->bentry_dev, p->bheader_dev, N, p->twiddle, p->corr);
+  prof_end(p, tok);
 }
 
 template <int G>
@@ -387,6 +439,20 @@ cudaError_t launch_fft(toi_plan_s* p, Slot& s) {
     case 2048: launch_g<2048>(p, s); break;
     case 4096: launch_g<4096>(p, s); break;
     case 8192: launch_g<8192>(p, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_batch(toi_plan_s* p) {
+  switch (p->G) {
+    case 128: launch_batch_g<128>(p); break;
+    case 256: launch_batch_g<256>(p); break;
+    case 512: launch_batch_g<512>(p); break;
+    case 1024: launch_batch_g<1024>(p); break;
+    case 2048: launch_batch_g<2048>(p); break;
+    case 4096: launch_batch_g<4096>(p); break;
+    case 8192: launch_batch_g<8192>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -83,17 +83,19 @@ __device__ __forceinline__ Source reproject_source(int o1, int o2, int N, float 
 }
 
 template <bool REPRO>
-__global__ void __launch_bounds__(kFinThreads)
-image_tile_kernel(const float* __restrict__ src, int N, int T, const double* __restrict__ snap,
-                  double beta_rad, float* __restrict__ ring_cur,
-                  const float* __restrict__ ring_p1, const float* __restrict__ ring_p2,
-                  float* __restrict__ image_out, int with_moments,
-                  double* __restrict__ tile_mom, unsigned int* __restrict__ max_cur) {
+__device__ __forceinline__ void image_tile_body(const float* __restrict__ src, int N, int T,
+                                                const double* __restrict__ snap, double beta_rad,
+                                                float* __restrict__ ring_cur,
+                                                const float* __restrict__ ring_p1,
+                                                const float* __restrict__ ring_p2,
+                                                float* __restrict__ image_out, int with_moments,
+                                                double* __restrict__ tile_mom,
+                                                unsigned int* __restrict__ max_cur, int tile) {
   __shared__ double sh[kFinThreads / 32][5];
   __shared__ float kk[3];
   __shared__ unsigned int smax;
   const int ntx = N / T;
-  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
+  const int tx = tile % ntx, ty = tile / ntx;
   if (threadIdx.x == 0) {
     smax = 0u;
     if (REPRO) {
@@ -163,20 +165,91 @@ image_tile_kernel(const float* __restrict__ src, int N, int T, const double* __r
     double v5[5];
     block_reduce_d<5>(f5, sh, v5);
     if (threadIdx.x == 0)
-      for (int i = 0; i < 5; ++i) tile_mom[(size_t)blockIdx.x * 5 + i] = v5[i];
+      for (int i = 0; i < 5; ++i) tile_mom[(size_t)tile * 5 + i] = v5[i];
   } else {
     __syncthreads();
   }
   if (threadIdx.x == 0) atomicMax(max_cur, smax);
 }
 
-__global__ void tlisi_finish_kernel(const double* __restrict__ tile_mom, int ntl, int T,
-                                    const unsigned int* __restrict__ ring_max, int cur, int p1,
-                                    int p2, float* __restrict__ out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+template <bool REPRO>
+__global__ void __launch_bounds__(kFinThreads)
+image_tile_kernel(const float* __restrict__ src, int N, int T, const double* __restrict__ snap,
+                  double beta_rad, float* __restrict__ ring_cur,
+                  const float* __restrict__ ring_p1, const float* __restrict__ ring_p2,
+                  float* __restrict__ image_out, int with_moments,
+                  double* __restrict__ tile_mom, unsigned int* __restrict__ max_cur) {
+  image_tile_body<REPRO>(src, N, T, snap, beta_rad, ring_cur, ring_p1, ring_p2, image_out,
+                         with_moments, tile_mom, max_cur, blockIdx.x);
+}
+
+// Batch: the images of one batch are made by one launch, and entry i's
+// window includes entries i-1 and i-2 of the same batch, so the images are
+// written first (no moments) and the tile moments follow in a second launch.
+__global__ void __launch_bounds__(kFinThreads)
+image_tile_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
+                 int T, double beta_rad) {
+  if ((int)blockIdx.y >= hdr->n) return;
+  const BatchEntry& e = E[blockIdx.y];
+  image_tile_body<true>(e.tilted, N, T, e.snap, beta_rad, e.ring_cur, e.ring_p1, e.ring_p2,
+                        e.image_out, 0, e.tile_mom, e.max_cur, blockIdx.x);
+}
+
+// Tile moments of the window (p2, p1, cur) of stored images, with the pixel
+// order and sums of image_tile_body (so they equal the fused ones bit for bit).
+__device__ __forceinline__ void tile_moments_body(const float* __restrict__ cur,
+                                                  const float* __restrict__ p1,
+                                                  const float* __restrict__ p2, int N, int T,
+                                                  double* __restrict__ tile_mom, int tile) {
+  __shared__ double sh[kFinThreads / 32][5];
+  const int ntx = N / T;
+  const int tx = tile % ntx, ty = tile / ntx;
+  float sa = 0.f, sb = 0.f, saa = 0.f, sbb = 0.f, sab = 0.f;
+  constexpr int kBatch = 4;
+  for (int e0 = threadIdx.x; e0 < T * T; e0 += kBatch * kFinThreads) {
+    float v[kBatch], i1v[kBatch], i0v[kBatch];
+    bool live[kBatch];
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      const int e = e0 + b * kFinThreads;
+      live[b] = e < T * T;
+      const int ee = live[b] ? e : 0;
+      const size_t pix = (size_t)(ty * T + ee / T) * N + tx * T + (ee % T);
+      v[b] = cur[pix];
+      i1v[b] = p1[pix];
+      i0v[b] = p2[pix];
+    }
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      if (!live[b]) continue;
+      const float a = i1v[b] - i0v[b], bd = v[b] - i1v[b];
+      sa += a; sb += bd; saa += a * a; sbb += bd * bd; sab += a * bd;
+    }
+  }
+  float f5[5] = {sa, sb, saa, sbb, sab};
+  double v5[5];
+  block_reduce_d<5>(f5, sh, v5);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 5; ++i) tile_mom[(size_t)tile * 5 + i] = v5[i];
+}
+
+__global__ void __launch_bounds__(kFinThreads)
+tile_moments_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
+                   int T) {
+  if ((int)blockIdx.y >= hdr->n) return;
+  const BatchEntry& e = E[blockIdx.y];
+  if (!e.with_moments) return;
+  tile_moments_body(e.ring_cur, e.ring_p1, e.ring_p2, N, T, e.tile_mom, blockIdx.x);
+}
+
+__device__ __forceinline__ void tlisi_finish_body(const double* __restrict__ tile_mom, int ntl,
+                                                  int T, const unsigned int* __restrict__ m_cur,
+                                                  const unsigned int* __restrict__ m_p1,
+                                                  const unsigned int* __restrict__ m_p2,
+                                                  float* __restrict__ out, int t) {
   if (t >= ntl) return;
-  const double L = (double)fmaxf(__uint_as_float(ring_max[cur]),
-                                 fmaxf(__uint_as_float(ring_max[p1]), __uint_as_float(ring_max[p2])));
+  const double L = (double)fmaxf(__uint_as_float(*m_cur),
+                                 fmaxf(__uint_as_float(*m_p1), __uint_as_float(*m_p2)));
   if (L == 0.0) { out[t] = 1.0f; return; }
   const double n = (double)T * (double)T;
   const double* m = tile_mom + (size_t)t * 5;
@@ -188,6 +261,22 @@ __global__ void tlisi_finish_kernel(const double* __restrict__ tile_mom, int ntl
   const double S = ((2.0 * mua * mub + C1) * (2.0 * cab + C2)) /
                    ((mua * mua + mub * mub + C1) * (va + vb + C2));
   out[t] = (float)((1.0 + S) * 0.5);
+}
+
+__global__ void tlisi_finish_kernel(const double* __restrict__ tile_mom, int ntl, int T,
+                                    const unsigned int* __restrict__ ring_max, int cur, int p1,
+                                    int p2, float* __restrict__ out) {
+  tlisi_finish_body(tile_mom, ntl, T, ring_max + cur, ring_max + p1, ring_max + p2, out,
+                    blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void tlisi_finish_batch(const BatchEntry* __restrict__ E,
+                                   const BatchHeader* __restrict__ hdr, int ntl, int T) {
+  if ((int)blockIdx.y >= hdr->n) return;
+  const BatchEntry& e = E[blockIdx.y];
+  if (!e.tlisi_out) return;
+  tlisi_finish_body(e.tile_mom, ntl, T, e.max_cur, e.max_p1, e.max_p2, e.tlisi_out,
+                    blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Adjoint of the re-projection, as a gather (deterministic, no atomics):
@@ -262,6 +351,22 @@ cudaError_t launch_ring_moments(toi_plan_s* p, const float* image, int cur, int 
   image_tile_kernel<false><<<ntl, kFinThreads, 0, p->stream>>>(
       image, p->N, p->T, nullptr, p->beta_rad, p->ring[cur], p->ring[prev1], p->ring[prev2],
       nullptr, with_moments ? 1 : 0, p->tile_mom, p->ring_max + cur);
+  prof_end(p, tok);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_batch(toi_plan_s* p) {
+  const int ntl = (p->N / p->T) * (p->N / p->T);
+  const int B = p->batch_max;
+  int tok = prof_begin(p, PROF_REPROJECT, 1);
+  image_tile_batch<<<dim3(ntl, B), kFinThreads, 0, p->stream>>>(p->bentry_dev, p->bheader_dev,
+                                                                p->N, p->T, p->beta_rad);
+  prof_end(p, tok);
+  tok = prof_begin(p, PROF_TLISI, 2);
+  tile_moments_batch<<<dim3(ntl, B), kFinThreads, 0, p->stream>>>(p->bentry_dev, p->bheader_dev,
+                                                                  p->N, p->T);
+  tlisi_finish_batch<<<dim3((ntl + 255) / 256, B), 256, 0, p->stream>>>(p->bentry_dev,
+                                                                         p->bheader_dev, ntl, p->T);
   prof_end(p, tok);
   return cudaGetLastError();
 }

@@ -314,22 +314,18 @@ __device__ __forceinline__ Sample read_staged(const StageBuf& sb, int sidx, int 
   return s;
 }
 
+// One warp's work: segment `seg` of track `track` (tracks [0, nbl) are the
+// upper-half tracks of the baselines, [nbl, 2 nbl) their mirrors).
 template <bool HALF>
-__global__ void __launch_bounds__(kWarps * 32)
-grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restrict__ kf,
-                   const void* __restrict__ vis, const float* __restrict__ chan_scale,
-                   const float* __restrict__ weight, const uint8_t* __restrict__ flag, int nbl,
-                   int nch, int npol, int G, float bl2, int run, int nseg,
-                   float2* __restrict__ H) {
-  __shared__ StageBuf stage_all[kWarps];
-  const int wib = threadIdx.x >> 5;
-  const int warp = blockIdx.x * kWarps + wib;
+__device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef,
+                                           const float2* __restrict__ kf,
+                                           const void* __restrict__ vis,
+                                           const float* __restrict__ chan_scale,
+                                           const float* __restrict__ weight,
+                                           const uint8_t* __restrict__ flag, int nbl, int nch,
+                                           int npol, int G, float bl2, int run, int track,
+                                           int seg, StageBuf& sb, float2* __restrict__ H) {
   const int lane = threadIdx.x & 31;
-  if (warp >= 2 * nbl * nseg) return;
-  // warps [0, nbl * nseg) walk the upper-half tracks, the rest their mirrors
-  // (most mirror warps exit at once, so they are kept out of the busy blocks)
-  const int seg = warp % nseg;
-  const int track = warp / nseg;
   const int mirror = track >= nbl ? 1 : 0;
   const int bl = track - mirror * nbl;
   const TrackGeom t = track_geom(coef[bl], mirror);
@@ -355,7 +351,6 @@ grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restri
   const int sx = (t.s1 * dk >= 0.0) ? 1 : -1;
   const int sy = (t.s2 * dk >= 0.0) ? 1 : -1;
   const size_t obase = (size_t)bl * nch * npol;
-  StageBuf& sb = stage_all[wib];
 
   // lane-private staging: lane l only ever touches st[stage][u][l]
 
@@ -484,7 +479,102 @@ grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restri
   flush_all(w, H, G, ox, oy, sx, sy, rx, ry);
 }
 
+template <bool HALF>
+__global__ void __launch_bounds__(kWarps * 32)
+grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restrict__ kf,
+                   const void* __restrict__ vis, const float* __restrict__ chan_scale,
+                   const float* __restrict__ weight, const uint8_t* __restrict__ flag, int nbl,
+                   int nch, int npol, int G, float bl2, int run, int nseg,
+                   float2* __restrict__ H) {
+  __shared__ StageBuf stage_all[kWarps];
+  const int wib = threadIdx.x >> 5;
+  const int warp = blockIdx.x * kWarps + wib;
+  if (warp >= 2 * nbl * nseg) return;
+  // warps [0, nbl * nseg) walk the upper-half tracks, the rest their mirrors
+  // (most mirror warps exit at once, so they are kept out of the busy blocks)
+  grid_track<HALF>(coef, kf, vis, chan_scale, weight, flag, nbl, nch, npol, G, bl2, run,
+                   warp / nseg, warp % nseg, stage_all[wib], H);
+}
+
+// Persistent gridder over a batch: each warp takes work items from a
+// counter until none is left.  Items are numbered upper tracks of every
+// entry first (the heavy ones, entries in table order), then the mirror
+// tracks, most of which store nothing and leave at once.  Uneven entries
+// (different channel counts and flag fractions) thus share the GPU without
+// a partial last wave per entry.
+template <bool HALF>
+__global__ void __launch_bounds__(kWarps * 32)
+grid_batch_kernel(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr,
+                  int* __restrict__ queue, int npol, int G, float bl2) {
+  __shared__ StageBuf stage_all[kWarps];
+  const int wib = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n = hdr->n;
+  const long long total = hdr->total_items;
+  for (;;) {
+    __syncwarp();   // lanes past their track's last channel rejoin here
+    long long item = 0;
+    if (lane == 0) item = (long long)atomicAdd(queue, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    // find the entry: upper items first, then mirror items
+    int ent = -1;
+    bool mir = false;
+    long long local = 0;
+    for (int i = 0; i < n; ++i) {
+      const long long cnt = (long long)E[i].nbl * E[i].nseg;
+      if (item >= E[i].up_begin && item < E[i].up_begin + cnt) { ent = i; local = item - E[i].up_begin; break; }
+      if (item >= E[i].mi_begin && item < E[i].mi_begin + cnt) { ent = i; mir = true; local = item - E[i].mi_begin; break; }
+    }
+    if (ent < 0) continue;
+    const BatchEntry& e = E[ent];
+    const int seg = (int)(local % e.nseg);
+    const int track = (int)(local / e.nseg) + (mir ? e.nbl : 0);
+    grid_track<HALF>(e.coef, e.kf, e.vis, e.chan_scale, e.weight, e.flag, e.nbl, e.nch, npol, G,
+                     bl2, e.run, track, seg, stage_all[wib], e.grid);
+  }
+}
+
 }  // namespace
+
+// Channels per lane: each track is split into segments of 32 lanes so that
+// there are several warps per SM slot (runs of at least 16 channels);
+// nch / 128 measured best at 4096 channels (finer runs pay more window
+// flushes, coarser ones leave a partial last wave of warps).
+int grid_default_run(int nch) {
+  const int run = (nch + 127) / 128;
+  return run < 16 ? 16 : run;
+}
+
+int channel_bucket(int nch) {
+  return nch <= 1024 ? 0 : (nch <= 2048 ? 1 : (nch <= 4096 ? 2 : 3));
+}
+
+int grid_resident_blocks() {
+  int b0 = 0, b1 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, grid_batch_kernel<false>, kWarps * 32, 0) !=
+      cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, grid_batch_kernel<true>, kWarps * 32, 0) !=
+      cudaSuccess)
+    return 0;
+  return b0 < b1 ? b0 : b1;
+}
+
+cudaError_t launch_grid_batch(toi_plan_s* p, bool half) {
+  const float bl2 = (float)(p->beta_es * 1.4426950408889634);
+  cudaError_t e = cudaMemsetAsync(p->bqueue, 0, sizeof(int), p->stream);
+  if (e != cudaSuccess) return e;
+  const int tok = prof_begin(p, PROF_GRID, 1);
+  if (half)
+    grid_batch_kernel<true><<<p->grid_blocks, kWarps * 32, 0, p->stream>>>(
+        p->bentry_dev, p->bheader_dev, p->bqueue, p->cfg.n_pol, p->G, bl2);
+  else
+    grid_batch_kernel<false><<<p->grid_blocks, kWarps * 32, 0, p->stream>>>(
+        p->bentry_dev, p->bheader_dev, p->bqueue, p->cfg.n_pol, p->G, bl2);
+  prof_end(p, tok);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_grid(toi_plan_s* p, Slot& s, const double* freq, const void* vis,
                         const float* chan_scale, const float* weight, const uint8_t* flag,
@@ -494,11 +584,8 @@ cudaError_t launch_grid(toi_plan_s* p, Slot& s, const double* freq, const void* 
   const int tok = prof_begin(p, PROF_GRID, 1);
   // the slot is zero: cleared at plan creation, by the row pass of the
   // previous toi_image, or by toi_grid when a gridded slot is re-gridded
-  // channel runs per lane: each track is split into segments of 32 lanes so
-  // that there are several warps per SM slot (runs of at least 16 channels)
-  int run = (nch + 63) / 64;
-  if (run < 16) run = 16;
-  if (p->cfg.grid_run > 0) run = p->cfg.grid_run;
+  int run = p->cfg.grid_run > 0 ? p->cfg.grid_run : p->tuned_run[channel_bucket(nch)];
+  if (run <= 0) run = grid_default_run(nch);
   const int nseg = (nch + 32 * run - 1) / (32 * run);
   const long long nwarps = 2LL * nbl * nseg;
   const int blocks = (int)((nwarps + kWarps - 1) / kWarps);

@@ -39,11 +39,11 @@ __device__ void block_reduce(double (&v)[NV], double* sh) {
 }
 
 // k = nu / c per channel, per-block sums of k and k^2, monotonicity.
-__global__ void prep_channels_kernel(const double* __restrict__ freq, int nch,
-                                     double* __restrict__ kch, float2* __restrict__ kf,
-                                     double* __restrict__ kpart, int* status) {
+__device__ __forceinline__ void prep_channels_body(const double* __restrict__ freq, int nch,
+                                                   double* __restrict__ kch, float2* __restrict__ kf,
+                                                   double* __restrict__ kpart, int* status, int blk) {
   __shared__ double sh[2 * 256];
-  const int c = blockIdx.x * 256 + threadIdx.x;
+  const int c = blk * 256 + threadIdx.x;
   double v[2] = {0.0, 0.0};
   bool bad = false;
   if (c < nch) {
@@ -61,9 +61,15 @@ __global__ void prep_channels_kernel(const double* __restrict__ freq, int nch,
   if (bad) set_status(status, TOI_DEV_RANGE);
   block_reduce<256, 2>(v, sh);
   if (threadIdx.x == 0) {
-    kpart[2 * blockIdx.x] = v[0];
-    kpart[2 * blockIdx.x + 1] = v[1];
+    kpart[2 * blk] = v[0];
+    kpart[2 * blk + 1] = v[1];
   }
+}
+
+__global__ void prep_channels_kernel(const double* __restrict__ freq, int nch,
+                                     double* __restrict__ kch, float2* __restrict__ kf,
+                                     double* __restrict__ kpart, int* status) {
+  prep_channels_body(freq, nch, kch, kf, kpart, status, blockIdx.x);
 }
 
 // Per baseline (one warp): deselected channels (both parallel hands flagged
@@ -72,11 +78,11 @@ __global__ void prep_channels_kernel(const double* __restrict__ freq, int nch,
 // moments, sum of weights) into one partial record, in a fixed order.
 constexpr int kMomWarps = 8;
 
-__global__ void __launch_bounds__(kMomWarps * 32)
-prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict__ weight,
-                      const double* __restrict__ kch, const double* __restrict__ kpart, int nkblk,
-                      const double* __restrict__ uvw, int nbl, int nch, int npol,
-                      double* __restrict__ bpart) {
+__device__ __forceinline__ void
+prep_baselines_body(const uint8_t* __restrict__ flag, const float* __restrict__ weight,
+                    const double* __restrict__ kch, const double* __restrict__ kpart, int nkblk,
+                    const double* __restrict__ uvw, int nbl, int nch, int npol,
+                    double* __restrict__ bpart, int blk) {
   __shared__ double sk_all[2];
   __shared__ double contrib[kMomWarps][11];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -96,7 +102,7 @@ prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict_
     }
   }
   __syncthreads();
-  const int bl = blockIdx.x * kMomWarps + wib;
+  const int bl = blk * kMomWarps + wib;
   double out[11];
   for (int i = 0; i < 11; ++i) out[i] = 0.0;
   if (bl < nbl) {
@@ -105,8 +111,21 @@ prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict_
     const size_t base = (size_t)bl * nch * npol;
     double sk = 0.0, sk2 = 0.0, sw = 0.0;
     long long nd = 0, cnt = 0;
-    // One channel: weights of the two parallel hands from its flags.
-    auto account = [&](int c, bool fa, bool fb) {
+    // Per channel only float32 and integer work: a deselected channel sets a
+    // bit of `dmask` (its float64 k sums are added afterwards in a
+    // data-dependent loop, so they are never issued for the ~all selected
+    // channels: float64 issue is scarce on this GPU), and weights are summed
+    // with an error-free float32 two-sum, folded into float64 once per
+    // iteration.
+    float swh = 0.f, swl = 0.f;
+    auto add_w = [&](float x) {
+      const float t = swh + x;
+      const float bp = t - swh;
+      swl += (swh - (t - bp)) + (x - bp);
+      swh = t;
+    };
+    // returns whether channel c (flags fa, fb) is deselected
+    auto account = [&](int c, bool fa, bool fb) -> bool {
       const size_t o = base + (size_t)c * npol;
       float wa, wb;
       if (weight) {
@@ -118,10 +137,26 @@ prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict_
       }
       const float wq = (pa == pb) ? wa : wa + wb;
       if (wq > 0.f) {
-        if (weight) sw += (pa == pb) ? (double)wa : (double)wa + (double)wb;
-        else cnt += (pa == pb) ? 1 : (int)(!fa) + (int)(!fb);
-      } else {
-        const double k = kch[c];
+        if (weight) {
+          add_w(wa);
+          if (pa != pb) add_w(wb);
+        } else {
+          cnt += (pa == pb) ? 1 : (int)(!fa) + (int)(!fb);
+        }
+        return false;
+      }
+      return true;
+    };
+    auto fold = [&](unsigned int dmask, auto chan_of_bit) {
+      if (weight) {
+        sw += (double)swh + (double)swl;
+        swh = 0.f;
+        swl = 0.f;
+      }
+      while (dmask) {
+        const int bit = __ffs(dmask) - 1;
+        dmask &= dmask - 1;
+        const double k = kch[chan_of_bit(bit)];
         sk += k;
         sk2 += k * k;
         nd += 1;
@@ -140,6 +175,7 @@ prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict_
           const int g = g0 + 32 * u;
           fv[u] = g < ngrp ? __ldcs(f16 + g) : make_uint4(0u, 0u, 0u, 0u);
         }
+        unsigned int dmask = 0u;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int g = g0 + 32 * u;
@@ -147,8 +183,10 @@ prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict_
           const unsigned int w4[4] = {fv[u].x, fv[u].y, fv[u].z, fv[u].w};
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            account(4 * g + i, (w4[i] & 0xffu) != 0, (w4[i] >> 24) != 0);
+            if (account(4 * g + i, (w4[i] & 0xffu) != 0, (w4[i] >> 24) != 0))
+              dmask |= 1u << (4 * u + i);
         }
+        fold(dmask, [&](int bit) { return 4 * (g0 + 32 * (bit >> 2)) + (bit & 3); });
       }
     } else {
       for (int c0 = lane; c0 < nch; c0 += 32 * U) {
@@ -165,11 +203,13 @@ prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict_
               f4[u] = (unsigned int)(flag[o + pa] != 0) | ((unsigned int)(flag[o + pb] != 0) << 24);
           }
         }
+        unsigned int dmask = 0u;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int c = c0 + 32 * u;
-          if (c < nch) account(c, (f4[u] & 0xffu) != 0, (f4[u] >> 24) != 0);
+          if (c < nch && account(c, (f4[u] & 0xffu) != 0, (f4[u] >> 24) != 0)) dmask |= 1u << u;
         }
+        fold(dmask, [&](int bit) { return c0 + 32 * bit; });
       }
     }
     // fixed-order warp reduction
@@ -197,8 +237,49 @@ prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict_
   if (threadIdx.x < 11) {
     double a = 0.0;
     for (int wdx = 0; wdx < kMomWarps; ++wdx) a += contrib[wdx][threadIdx.x];
-    bpart[(size_t)blockIdx.x * 11 + threadIdx.x] = a;
+    bpart[(size_t)blk * 11 + threadIdx.x] = a;
   }
+}
+
+__global__ void __launch_bounds__(kMomWarps * 32)
+prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict__ weight,
+                      const double* __restrict__ kch, const double* __restrict__ kpart, int nkblk,
+                      const double* __restrict__ uvw, int nbl, int nch, int npol,
+                      double* __restrict__ bpart) {
+  prep_baselines_body(flag, weight, kch, kpart, nkblk, uvw, nbl, nch, npol, bpart, blockIdx.x);
+}
+
+// 1/x and 1/sqrt(x) for normal x (x > 0 for the square root) to float64
+// accuracy with few dependent float64 operations: x = m 2^e with m in
+// [1, 2) is split off through the IEEE-754 bit fields (so the float32 seed
+// cannot overflow whatever the magnitude of x), a float32 seed is refined by
+// two Newton steps in float64 (each squares the relative error: 2^-24 ->
+// 2^-48 -> below one ulp), and 2^-e (2^(-e/2)) is applied exactly.
+__device__ __forceinline__ double pow2_exact(int e) {   // 2^e, -1022 <= e <= 1023
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+__device__ __forceinline__ double split_exp(double x, int& e) {
+  const long long b = __double_as_longlong(x);
+  e = (int)((b >> 52) & 0x7ff) - 1023;
+  return __longlong_as_double((b & (long long)0x800fffffffffffffULL) | (1023LL << 52));
+}
+__device__ __forceinline__ double rcp64(double x) {
+  int e;
+  const double m = split_exp(x, e);
+  double r = (double)(1.0f / (float)m);
+  r = __fma_rn(r, __fma_rn(-m, r, 1.0), r);
+  r = __fma_rn(r, __fma_rn(-m, r, 1.0), r);
+  return r * pow2_exact(-e);
+}
+__device__ __forceinline__ double rsqrt64(double x) {
+  int e;
+  double m = split_exp(x, e);
+  if (e & 1) { m *= 2.0; e -= 1; }        // m in [1, 4), e even
+  double r = (double)rsqrtf((float)m);
+  const double h = 0.5 * m;
+  r = __fma_rn(r, __fma_rn(-h * r, r, 0.5), r);
+  r = __fma_rn(r, __fma_rn(-h * r, r, 0.5), r);
+  return r * pow2_exact(-e / 2);
 }
 
 // Eigenvector of the smallest eigenvalue of the symmetric 3x3 C (float64
@@ -210,10 +291,11 @@ prep_baselines_kernel(const uint8_t* __restrict__ flag, const float* __restrict_
 __device__ bool smallest_eigvec(const double Cd[3][3], double v3[3]) {
   double tr = fabs(Cd[0][0]) + fabs(Cd[1][1]) + fabs(Cd[2][2]);
   if (!(tr > 0.0)) return false;
+  const double itr = rcp64(tr);
   float a[3][3], e[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      a[i][j] = (float)(Cd[i][j] / tr);
+      a[i][j] = (float)(Cd[i][j] * itr);
       e[i][j] = (i == j) ? 1.f : 0.f;
     }
   // every index below is a compile-time constant after unrolling, so a and e
@@ -266,7 +348,8 @@ __device__ bool smallest_eigvec(const double Cd[3][3], double v3[3]) {
   for (int r = 0; r < 3; ++r) u[r] = imin == 0 ? e[r][0] : (imin == 1 ? e[r][1] : e[r][2]);
   double Cu[3];
   for (int i = 0; i < 3; ++i) Cu[i] = Cd[i][0] * u[0] + Cd[i][1] * u[1] + Cd[i][2] * u[2];
-  const double l = (u[0] * Cu[0] + u[1] * Cu[1] + u[2] * Cu[2]) / (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const double l = (u[0] * Cu[0] + u[1] * Cu[1] + u[2] * Cu[2]) *
+                   rcp64(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   double M[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) M[i][j] = Cd[i][j] - (i == j ? l : 0.0);
@@ -286,13 +369,13 @@ __device__ bool smallest_eigvec(const double Cd[3][3], double v3[3]) {
   } else {
     for (int i = 0; i < 3; ++i) v3[i] = best[i];
   }
-  const double inv = 1.0 / sqrt(v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2]);
+  const double inv = rsqrt64(v3[0] * v3[0] + v3[1] * v3[1] + v3[2] * v3[2]);
   for (int i = 0; i < 3; ++i) v3[i] *= inv;
   return true;
 }
 
-__global__ void prep_finalize_kernel(const double* __restrict__ bpart, int nbpart,
-                                     double* __restrict__ snap, int* status) {
+__device__ __forceinline__ void prep_finalize_body(const double* __restrict__ bpart, int nbpart,
+                                                   double* __restrict__ snap, int* status) {
   // one warp per sum: lanes take partials in a fixed stride, then a fixed tree
   __shared__ double v[11];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -309,13 +392,14 @@ __global__ void prep_finalize_kernel(const double* __restrict__ bpart, int nbpar
   double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
   if (!empty) {
     const double m1[3] = {v[1], v[2], v[3]};
+    const double iN = rcp64(N);
     double C[3][3];
-    C[0][0] = v[4] - m1[0] * m1[0] / N;
-    C[0][1] = v[5] - m1[0] * m1[1] / N;
-    C[0][2] = v[6] - m1[0] * m1[2] / N;
-    C[1][1] = v[7] - m1[1] * m1[1] / N;
-    C[1][2] = v[8] - m1[1] * m1[2] / N;
-    C[2][2] = v[9] - m1[2] * m1[2] / N;
+    C[0][0] = v[4] - m1[0] * m1[0] * iN;
+    C[0][1] = v[5] - m1[0] * m1[1] * iN;
+    C[0][2] = v[6] - m1[0] * m1[2] * iN;
+    C[1][1] = v[7] - m1[1] * m1[1] * iN;
+    C[1][2] = v[8] - m1[1] * m1[2] * iN;
+    C[2][2] = v[9] - m1[2] * m1[2] * iN;
     C[1][0] = C[0][1]; C[2][0] = C[0][2]; C[2][1] = C[1][2];
     double v3[3];
     if (smallest_eigvec(C, v3)) {
@@ -325,7 +409,7 @@ __global__ void prep_finalize_kernel(const double* __restrict__ bpart, int nbpar
       if (fabs(v3[0]) > 0.999) { e[0] = 0.0; e[1] = 1.0; }
       const double d = e[0] * v3[0] + e[1] * v3[1] + e[2] * v3[2];
       double v1[3] = {e[0] - d * v3[0], e[1] - d * v3[1], e[2] - d * v3[2]};
-      const double nn = 1.0 / sqrt(v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]);
+      const double nn = rsqrt64(v1[0] * v1[0] + v1[1] * v1[1] + v1[2] * v1[2]);
       for (int i = 0; i < 3; ++i) v1[i] *= nn;
       const double v2[3] = {v3[1] * v1[2] - v3[2] * v1[1], v3[2] * v1[0] - v3[0] * v1[2],
                             v3[0] * v1[1] - v3[1] * v1[0]};
@@ -345,13 +429,18 @@ __global__ void prep_finalize_kernel(const double* __restrict__ bpart, int nbpar
   snap[15] = 0.0;
 }
 
+__global__ void prep_finalize_kernel(const double* __restrict__ bpart, int nbpart,
+                                     double* __restrict__ snap, int* status) {
+  prep_finalize_body(bpart, nbpart, snap, status);
+}
+
 // Per baseline: R = V uvw (float64), grid coefficients a1 = -r1 beta G,
 // a2 = r2 beta G, and the check that every footprint stays on the grid.
-__global__ void prep_coef_kernel(const double* __restrict__ uvw, int nbl, int nch,
-                                 const double* __restrict__ kch, double* __restrict__ snap,
-                                 double beta_rad, int G, int W, BaselineCoef* __restrict__ coef,
-                                 int* status) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void prep_coef_body(const double* __restrict__ uvw, int nbl, int nch,
+                                               const double* __restrict__ kch,
+                                               double* __restrict__ snap, double beta_rad, int G,
+                                               int W, BaselineCoef* __restrict__ coef, int* status,
+                                               int b) {
   if (b >= nbl) return;
   double Vs[9];
   for (int i = 0; i < 9; ++i) Vs[i] = snap[SNAP_V + i];
@@ -376,6 +465,50 @@ __global__ void prep_coef_kernel(const double* __restrict__ uvw, int nbl, int nc
             (unsigned long long)__double_as_longlong(rowmax));
 }
 
+__global__ void prep_coef_kernel(const double* __restrict__ uvw, int nbl, int nch,
+                                 const double* __restrict__ kch, double* __restrict__ snap,
+                                 double beta_rad, int G, int W, BaselineCoef* __restrict__ coef,
+                                 int* status) {
+  prep_coef_body(uvw, nbl, nch, kch, snap, beta_rad, G, W, coef, status,
+                 blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---- batched wrappers: blockIdx.y selects the entry; blocks beyond an
+// entry's extent (or entries beyond the batch) leave at once ----
+__global__ void prep_channels_batch(const BatchEntry* __restrict__ E,
+                                    const BatchHeader* __restrict__ hdr, int* status) {
+  if ((int)blockIdx.y >= hdr->n) return;
+  const BatchEntry& e = E[blockIdx.y];
+  if ((int)blockIdx.x * 256 >= e.nch) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *e.max_cur = 0u;   // this image's max |I| starts at 0
+  prep_channels_body(e.freq, e.nch, e.kch, e.kf, e.kpart, status, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kMomWarps * 32)
+prep_baselines_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr,
+                     int npol) {
+  if ((int)blockIdx.y >= hdr->n) return;
+  const BatchEntry& e = E[blockIdx.y];
+  if ((int)blockIdx.x * kMomWarps >= e.nbl) return;
+  prep_baselines_body(e.flag, e.weight, e.kch, e.kpart, (e.nch + 255) / 256, e.uvw, e.nbl, e.nch,
+                      npol, e.bpart, blockIdx.x);
+}
+
+__global__ void prep_finalize_batch(const BatchEntry* __restrict__ E,
+                                    const BatchHeader* __restrict__ hdr, int* status) {
+  if ((int)blockIdx.y >= hdr->n) return;
+  const BatchEntry& e = E[blockIdx.y];
+  prep_finalize_body(e.bpart, (e.nbl + kMomWarps - 1) / kMomWarps, e.snap, status);
+}
+
+__global__ void prep_coef_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr,
+                                double beta_rad, int G, int W, int* status) {
+  if ((int)blockIdx.y >= hdr->n) return;
+  const BatchEntry& e = E[blockIdx.y];
+  prep_coef_body(e.uvw, e.nbl, e.nch, e.kch, e.snap, beta_rad, G, W, e.coef, status,
+                 blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 }  // namespace
 
 cudaError_t launch_prep(toi_plan_s* p, Slot& s, const double* uvw, const double* freq,
@@ -391,6 +524,22 @@ cudaError_t launch_prep(toi_plan_s* p, Slot& s, const double* uvw, const double*
   prep_coef_kernel<<<(nbl + 127) / 128, 128, 0, p->stream>>>(uvw, nbl, nch, p->kch, s.snap,
                                                              p->beta_rad, p->G, p->W, s.coef,
                                                              p->d_status);
+  prof_end(p, tok);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_batch(toi_plan_s* p) {
+  const int B = p->batch_max;
+  const int maxch = p->cfg.max_channels, maxbl = p->cfg.max_baselines;
+  const int tok = prof_begin(p, PROF_PREP, 4);
+  prep_channels_batch<<<dim3((maxch + 255) / 256, B), 256, 0, p->stream>>>(
+      p->bentry_dev, p->bheader_dev, p->d_status);
+  prep_baselines_batch<<<dim3((maxbl + kMomWarps - 1) / kMomWarps, B), kMomWarps * 32, 0,
+                         p->stream>>>(p->bentry_dev, p->bheader_dev, p->cfg.n_pol);
+  prep_finalize_batch<<<dim3(1, B), 352, 0, p->stream>>>(p->bentry_dev, p->bheader_dev,
+                                                         p->d_status);
+  prep_coef_batch<<<dim3((maxbl + 127) / 128, B), 128, 0, p->stream>>>(
+      p->bentry_dev, p->bheader_dev, p->beta_rad, p->G, p->W, p->d_status);
   prof_end(p, tok);
   return cudaGetLastError();
 }

@@ -48,6 +48,51 @@ struct Slot {
   bool valid = false;   // holds a grid from toi_grid that toi_image has not consumed
 };
 
+// One snapshot of a batch as the batched kernels see it (device copy of a
+// host-built table; see toi_batch_prepare).
+struct BatchEntry {
+  // inputs (caller-owned)
+  const double* uvw;
+  const double* freq;
+  const void* vis;
+  const float* chan_scale;
+  const float* weight;
+  const uint8_t* flag;
+  int nbl, nch;
+  // per-entry workspace (plan-owned)
+  float2* grid;
+  double* snap;
+  BaselineCoef* coef;
+  double* kch;
+  float2* kf;
+  double* kpart;
+  double* bpart;
+  float2* fft_tmp;
+  float* tilted;
+  double* tile_mom;
+  // image ring and outputs
+  float* ring_cur;
+  const float* ring_p1;
+  const float* ring_p2;
+  unsigned int* max_cur;
+  const unsigned int* max_p1;
+  const unsigned int* max_p2;
+  float* image_out;     // caller's image or NULL
+  float* tlisi_out;     // caller's tLISI row or NULL (no three-image window yet)
+  int with_moments;
+  // gridder work split: lanes walk `run` channels, a track has nseg
+  // segments; upper-track items [up_begin, up_begin + nbl * nseg), mirror
+  // items [mi_begin, mi_begin + nbl * nseg)
+  int run, nseg;
+  long long up_begin, mi_begin;
+};
+
+struct BatchHeader {
+  int n;                 // entries in this batch
+  int pad;
+  long long total_items; // gridder work items over all entries
+};
+
 // Per-stage device-time accounting with CUDA events on the plan's stream.
 enum ProfStage {
   // PROF_BIN is reserved (the gridder needs no binning pass)
@@ -84,8 +129,8 @@ struct toi_plan_s {
   float* corr = nullptr;                 // [N] 1 / psi_hat((j - N/2) / G)
   float2* fft_tmp = nullptr;             // [G/2][N] rows after pass 1
   float* tilted = nullptr;               // [N][N]
-  float* ring[3] = {nullptr, nullptr, nullptr};
-  unsigned int* ring_max = nullptr;      // [3] float bits of max |I|
+  std::vector<float*> ring;              // [R][N][N] image ring, R = max(3, batch_max + 2)
+  unsigned int* ring_max = nullptr;      // [R] float bits of max |I|
   double* tile_mom = nullptr;            // [ntl][6]
   int* d_status = nullptr;               // device status word
   double* adj_scratch = nullptr;         // partial sums and <dL/dI, I> of the adjoint
@@ -93,6 +138,27 @@ struct toi_plan_s {
   const float* last_image = nullptr;     // output pointer of the last toi_image
   bool fused_pending = false;
   toi::ProfState prof;
+
+  // batched path (toi_batch_*): batch_max entries with their own workspace
+  int batch_max = 0;
+  toi::BatchEntry* bentry_host = nullptr;   // pinned [batch_max]
+  toi::BatchHeader* bheader_host = nullptr; // pinned
+  toi::BatchEntry* bentry_dev = nullptr;
+  toi::BatchHeader* bheader_dev = nullptr;
+  int* bqueue = nullptr;                    // gridder work counter
+  int bn = 0;                               // entries of the prepared batch (0: none)
+  cudaEvent_t bcopied = nullptr;            // the table of the last toi_batch_run was copied
+  bool bcopied_pending = false;
+  toi::Slot* bslots = nullptr;              // [batch_max] grid, snap, coef of each entry
+  double* b_kch = nullptr;                  // [batch_max][max_ch]
+  float2* b_kf = nullptr;
+  double* b_kpart = nullptr;                // [batch_max][2 ceil(max_ch / 256) + 2]
+  double* b_bpart = nullptr;                // [batch_max][11 ceil(max_bl / 8)]
+  float2* b_fft_tmp = nullptr;              // [batch_max][G/2][N]
+  float* b_tilted = nullptr;                // [batch_max][N][N]
+  double* b_tile_mom = nullptr;             // [batch_max][ntl][5]
+  int grid_blocks = 0;                      // persistent gridder: resident blocks
+  int tuned_run[4] = {0, 0, 0, 0};          // autotuned lane runs per channel bucket
 };
 
 namespace toi {
@@ -113,6 +179,15 @@ cudaError_t launch_reproject_moments(toi_plan_s* p, Slot& s, float* image_out,
 cudaError_t launch_ring_moments(toi_plan_s* p, const float* image, int cur, int prev1,
                                 int prev2, bool with_moments);
 cudaError_t launch_tlisi_finalize(toi_plan_s* p, float* tlisi, int cur, int prev1, int prev2);
+
+// batched path (one launch per stage over all entries of a batch)
+cudaError_t launch_prep_batch(toi_plan_s* p);
+cudaError_t launch_grid_batch(toi_plan_s* p, bool half);
+cudaError_t launch_fft_batch(toi_plan_s* p);
+cudaError_t launch_finish_batch(toi_plan_s* p);
+int grid_resident_blocks();                 // persistent gridder blocks per SM
+int grid_default_run(int nch);
+int channel_bucket(int nch);
 
 // degrid.cu
 size_t degrid_scratch_doubles();

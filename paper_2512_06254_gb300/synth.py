@@ -236,6 +236,30 @@ def faint_transient_workload(n_snap: int = 300) -> Workload:
     return replace(base, name="meerkat-faint-transients", sources=tuple(src))
 
 
+def uneven_stream(base: Workload, n_snap: int, seed: int = 5,
+                  channel_choices=(1024, 2048, 4096), flag_max: float = 0.6,
+                  image_sizes=(1024, 2048)) -> List[Workload]:
+    """Per-snapshot workloads of an uneven stream (the batched case): each
+    snapshot s keeps the array, sky and noise of `base` but takes a channel
+    count from `channel_choices` (a contiguous sub-band of base's channel
+    grid at a random offset), a flag fraction uniform in [0, flag_max] and an
+    image size from `image_sizes`, all drawn from a seeded generator."""
+    g = torch.Generator().manual_seed(seed)
+    step = (base.f_hi_hz - base.f_lo_hz) / base.n_chan
+    out = []
+    for _ in range(n_snap):
+        nc = channel_choices[int(torch.randint(len(channel_choices), (1,), generator=g))]
+        nc = min(nc, base.n_chan)
+        off = int(torch.randint(base.n_chan - nc + 1, (1,), generator=g))
+        ff = float(torch.rand(1, generator=g)) * flag_max
+        N = image_sizes[int(torch.randint(len(image_sizes), (1,), generator=g))]
+        f_lo = base.f_lo_hz + off * step
+        out.append(replace(base, n_chan=nc, f_lo_hz=f_lo, f_hi_hz=f_lo + nc * step,
+                           flag_frac=ff, image_size=N,
+                           name=f"{base.name}-uneven-{nc}ch-{N}px"))
+    return out
+
+
 # --------------------------------------------------------------------------
 # Snapshot synthesis
 # --------------------------------------------------------------------------
