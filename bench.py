@@ -29,28 +29,33 @@ sys.path.insert(0, ROOT)
 METRIC = "snapshots/s end-to-end (grid+iFFT+tLISI) at MeerKAT shape; % HBM roofline"
 WORKLOAD = "meerkat-64ant-2016bl-4096ch-4pol-2048px-1500snap"
 
-# Algorithmic HBM bytes per launch of each stage at this workload (minimum
-# traffic: every input byte read once, every output byte written once).
+# Algorithmic HBM bytes of each stage per snapshot (minimum traffic: every
+# input byte read once, every output byte written once).
 N_BL, N_CH, N_POL, N_IMG = 2016, 4096, 4, 2048
 G = 2 * N_IMG
-VIS_B = N_BL * N_CH * N_POL * 8
-FLAG_B = N_BL * N_CH * N_POL
-HALF_GRID_B = (G // 2) * G * 8
-ALG_BYTES = {
-    "prep": FLAG_B,
-    "bin": 0,
-    "grid": VIS_B + FLAG_B + HALF_GRID_B,
-    "fft_rows": HALF_GRID_B + (G // 2) * N_IMG * 8,
-    "fft_cols": (G // 2) * N_IMG * 8 + N_IMG * N_IMG * 4,
-    "reproject": N_IMG * N_IMG * 4 * 4,
-    "tlisi": 64 * 64 * 4,
-    # adjoint (not part of the timed step): dL/dI read, U and the column
-    # pass written and read once, the half grid written and read, flags
-    # read, grad_vis written
-    "backward": (N_IMG * N_IMG * 4 * 3 + 2 * (G // 2) * N_IMG * 8 + 2 * HALF_GRID_B
-                 + FLAG_B + VIS_B),
-}
 
+
+def alg_bytes(nbl=N_BL, nch=N_CH, npol=N_POL, N=N_IMG, T=32):
+    g = 2 * N
+    vis_b = nbl * nch * npol * 8
+    flag_b = nbl * nch * npol
+    half_grid_b = (g // 2) * g * 8
+    return {
+        "prep": flag_b,
+        "bin": 0,
+        "grid": vis_b + flag_b + half_grid_b,
+        "fft_rows": half_grid_b + (g // 2) * N * 8,
+        "fft_cols": (g // 2) * N * 8 + N * N * 4,
+        "reproject": N * N * 4 * 4,
+        "tlisi": (N // T) ** 2 * 4,
+        # adjoint (not part of the timed step): dL/dI read, U and the column
+        # pass written and read once, the half grid written and read, flags
+        # read, grad_vis written
+        "backward": N * N * 4 * 3 + 2 * (g // 2) * N * 8 + 2 * half_grid_b + flag_b + vis_b,
+    }
+
+
+ALG_BYTES = alg_bytes()
 
 
 def load_peaks():
@@ -146,8 +151,11 @@ def run_ours(args):
     T = 32
     nt = w.image_size // T
     pool = make_pool(w, args.pool, dev)
-    plan = toi.Plan(w.image_size, w.cell_arcsec, w.n_bl, w.n_chan, w.n_pol, tlisi_tile=T)
+    B = args.batch if args.engine == "batch" else 0
+    plan = toi.Plan(w.image_size, w.cell_arcsec, w.n_bl, w.n_chan, w.n_pol, tlisi_tile=T,
+                    batch_max=B)
     cube = torch.empty(S - 2, nt, nt, dtype=torch.float32, device=dev)
+    row_bytes = nt * nt * 4
 
     sharded = args.shard_observation and world > 1
     if sharded:
@@ -160,8 +168,19 @@ def run_ours(args):
         plan.image(0, None)
         return plan.tlisi_update(None, dst)
 
+    def image_batched(first, last, out_base):
+        """Snapshots [first, last) in batches of B; the tLISI of image t goes
+        to row t - 2 of the cube whose first row is at out_base."""
+        for lo in range(first, last, B):
+            hi = min(lo + B, last)
+            snaps = [pool[s % len(pool)] for s in range(lo, hi)]
+            plan.batch(snaps, out_base + (lo - first - 2) * row_bytes)
+
     def step():
         plan.tlisi_reset()
+        if B and not sharded:
+            image_batched(0, S, cube.data_ptr())
+            return toi.tlisi_candidates(cube, T, toi.TOI_CAND_PERIODIC)
         if sharded:
             shard.run_shard(S, world, rank, image_and_tlisi, local)
             full = shard.gather_cube(local, S, world, rank)
@@ -206,14 +225,21 @@ def run_ours(args):
     # roofline of the dominant stage (CUDA events on the plan's stream)
     peak, peak_kind = load_peaks()
     dom = max(prof, key=lambda k: prof[k][0])
-    dom_ms, dom_n = prof[dom]
-    achieved = ALG_BYTES[dom] * dom_n / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
-    total_alg = sum(ALG_BYTES[k] * prof[k][1] for k in prof)
+    dom_ms = prof[dom][0]
+    if sharded:
+        first, last = shard.image_range(S, world, rank)
+        imaged = (last - first) * args.steps
+    else:
+        imaged = S * args.steps
+    achieved = ALG_BYTES[dom] * imaged / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    total_alg = sum(ALG_BYTES[k] for k in ("prep", "grid", "fft_rows", "fft_cols", "reproject",
+                                           "tlisi")) * imaged
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "alg_bytes_per_launch": ALG_BYTES[dom],
+                "traffic": None, "alg_bytes_per_launch": ALG_BYTES[dom] * (
+                    args.batch if args.engine == "batch" else 1),
                 "share": round(dom_ms / sum(v[0] for v in prof.values()), 3),
-                "path_alg_gbs": round(total_alg / (ms / 1e3) / 1e9 * world / world, 1)}
+                "path_alg_gbs": round(total_alg / (ms / 1e3) / 1e9, 1)}
     stages = {k: {"ms_per_launch": round(v[0] / max(v[1], 1), 4), "launches": v[1]}
               for k, v in prof.items()}
 
@@ -224,7 +250,8 @@ def run_ours(args):
         for p in pool[:args.host_pool]:
             hpool.append({k: v.cpu().pin_memory() for k, v in p.items()})
         cube_host = torch.empty(S - 2, nt, nt, dtype=torch.float32).pin_memory()
-        si = StreamingImager(plan, w.n_bl, w.n_chan, w.n_pol)
+        si = StreamingImager(plan, w.n_bl, w.n_chan, w.n_pol, batch=B,
+                             copy_streams=args.copy_streams)
         for _ in range(args.e2e_warmup):
             si.run(hpool, S, cube, cube_host, T)
         si.h2d_bytes = si.d2h_bytes = 0
@@ -241,7 +268,8 @@ def run_ours(args):
         e2e = {"value": round(S * args.e2e_steps * world / es, 2), "unit": "snapshots/s",
                "h2d_bytes_per_step": si.h2d_bytes // args.e2e_steps,
                "d2h_bytes_per_step": si.d2h_bytes // args.e2e_steps,
-               "host_pool_snapshots": args.host_pool}
+               "host_pool_snapshots": args.host_pool, "copy_streams": args.copy_streams,
+               "engine": args.engine + (f"{B}" if B else "")}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -254,6 +282,7 @@ def run_ours(args):
                "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (seeded MeerKAT-shaped snapshots, resident pool)",
                "config": {"workload": WORKLOAD, "snapshots_per_step": S,
+                          "engine": args.engine + (f"{B}" if B else ""),
                           "resident_pool": args.pool, "image": N_IMG, "grid": G,
                           "tlisi_tile": T, "candidate_mode": "periodic",
                           "l2": "inputs larger than L2 (297 MB per snapshot, 40 distinct = one pulsar period)",
@@ -265,6 +294,134 @@ def run_ours(args):
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_uneven(args):
+    """The batched uneven stream: 512 snapshots of the MeerKAT-shaped array
+    with per-snapshot channel counts in {1024, 2048, 4096} (contiguous
+    sub-bands), flag fractions uniform in [0, 0.6] and 1024^2 or 2048^2
+    images, imaged in batches of --batch per image size (one plan per size,
+    autotuned), optionally by replaying one captured batch launch."""
+    import torch
+
+    import paper_2512_06254_gb300 as toi
+    from paper_2512_06254_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    S, B, P, T = 512, args.batch, args.pool, 32
+    base = synth.meerkat_workload(n_snap=S)
+    specs = synth.uneven_stream(base, S, seed=23, channel_choices=(1024, 2048, 4096),
+                                flag_max=0.6, image_sizes=(1024, 2048))
+    pool = []
+    for i in range(P):
+        sn = synth.make_snapshot(specs[i], i, device=dev, uvw_index=i)
+        sn.pop("weight")
+        pool.append(sn)
+    sizes = sorted({specs[i].image_size for i in range(P)})
+    stream = torch.cuda.Stream()
+    plans, cubes, tuned = {}, {}, {}
+    for N in sizes:
+        plans[N] = toi.Plan(N, base.cell_arcsec, base.n_bl, base.n_chan, base.n_pol,
+                            tlisi_tile=T, batch_max=B, stream=stream)
+        count = sum(1 for s in range(S) if specs[s % P].image_size == N)
+        cubes[N] = torch.empty(max(count - 2, 1), N // T, N // T, dtype=torch.float32, device=dev)
+        sample = [pool[i] for i in range(P) if specs[i].image_size == N][:B]
+        tuned[N] = plans[N].autotune(sample)
+    graphs = {}
+
+    def run_batch(N, idx, t0):
+        plan = plans[N]
+        snaps = [pool[s % P] for s in idx]
+        row = (N // T) ** 2 * 4
+        out = cubes[N].data_ptr() + (t0 - 2) * row
+        if not args.graph:
+            plan.batch(snaps, out)
+            return
+        stream.synchronize()
+        plan.batch_prepare(snaps, out)
+        if N not in graphs:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                plan.batch_run()
+            graphs[N] = g
+        with torch.cuda.stream(stream):
+            graphs[N].replay()
+
+    def step():
+        pending = {N: [] for N in sizes}
+        done = {N: 0 for N in sizes}
+        for p in plans.values():
+            p.tlisi_reset()
+        for s in range(S):
+            N = specs[s % P].image_size
+            pending[N].append(s)
+            if len(pending[N]) == B:
+                run_batch(N, pending[N], done[N])
+                done[N] += B
+                pending[N] = []
+        for N in sizes:
+            if pending[N]:
+                run_batch(N, pending[N], done[N])
+                done[N] += len(pending[N])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for p in plans.values():
+        if p.sync_status() != toi.TOI_OK:
+            raise RuntimeError(p.last_error())
+        p.profile_read()
+        p.profile_enable(not args.graph)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    prof = {}
+    for p in plans.values():
+        for k, v in p.profile_read().items():
+            a = prof.setdefault(k, [0.0, 0])
+            a[0] += v[0]
+            a[1] += v[1]
+        p.profile_enable(False)
+        if p.sync_status() != toi.TOI_OK:
+            raise RuntimeError(p.last_error())
+    alg = {k: 0 for k in ALG_BYTES}
+    for s in range(S):
+        w = specs[s % P]
+        for k, v in alg_bytes(base.n_bl, w.n_chan, base.n_pol, w.image_size).items():
+            alg[k] += v * args.steps
+    peak, peak_kind = load_peaks()
+    roofline = None
+    if prof and prof.get("grid", [0])[0] > 0:
+        g_ms = prof["grid"][0]
+        achieved = alg["grid"] / (g_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "grid", "achieved": round(achieved, 1),
+                    "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "share": round(g_ms / sum(v[0] for v in prof.values()), 3)}
+    value = S * args.steps / (ms / 1e3)
+    print(json.dumps({
+        "metric": METRIC, "value": round(value, 2), "unit": "snapshots/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded uneven MeerKAT-array snapshots, resident pool)",
+        "config": {"workload": "meerkat-uneven-512snap-1024to4096ch-0to60pctflags-1024or2048px",
+                   "batch": B, "graph": bool(args.graph), "resident_pool": P,
+                   "autotuned_runs": {str(N): tuned[N][0] for N in sizes},
+                   "l2": "inputs larger than L2"},
+        "roofline": roofline,
+        "stages": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]},
+        "clocks": ck}))
+    for p in plans.values():
+        p.close()
 
 
 CPU_SNIPPET = r"""
@@ -344,19 +501,27 @@ def run_reference(args):
 
 def profile_case(args):
     """Small case for ncu captures: one MeerKAT-shaped snapshot resident on the
-    device, `--profile-case` passes of toi_grid + toi_image + tlisi_update."""
+    device, `--profile-case` passes of toi_grid + toi_image + tlisi_update
+    (--engine single) or of toi_batch over --batch references to it
+    (--engine batch)."""
     import torch
 
     import paper_2512_06254_gb300 as toi
     from paper_2512_06254_gb300 import synth
     w = synth.meerkat_workload()
     p = synth.make_snapshot(w, 3, device="cuda", uvw_index=3)
-    plan = toi.Plan(w.image_size, w.cell_arcsec, w.n_bl, w.n_chan, w.n_pol)
-    out = torch.empty(w.image_size // 32, w.image_size // 32, device="cuda")
+    batch = args.engine == "batch"
+    B = args.batch if batch else 0
+    plan = toi.Plan(w.image_size, w.cell_arcsec, w.n_bl, w.n_chan, w.n_pol, batch_max=B)
+    nt = w.image_size // 32
+    out = torch.empty(max(B, 1), nt, nt, device="cuda")
     for _ in range(args.profile_case):
-        plan.grid(p["uvw"], p["freq"], p["vis"], flag=p["flag"])
-        plan.image(0, None)
-        plan.tlisi_update(None, out)
+        if batch:   # one resident snapshot referenced B times: B launches' worth of work
+            plan.batch([p] * B, out)
+        else:
+            plan.grid(p["uvw"], p["freq"], p["vis"], flag=p["flag"])
+            plan.image(0, None)
+            plan.tlisi_update(None, out[0])
     torch.cuda.synchronize()
     st = plan.sync_status()
     print("profile case done, status", st)
@@ -377,6 +542,17 @@ def main():
     ap.add_argument("--e2e-warmup", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--engine", default="batch", choices=["single", "batch"],
+                    help="single: toi_grid + toi_image + tlisi_update per snapshot; batch: "
+                         "toi_batch over --batch snapshots per launch")
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--copy-streams", type=int, default=4,
+                    help="e2e: copy streams each snapshot's host-to-device copy is split over")
+    ap.add_argument("--workload", default="meerkat", choices=["meerkat", "uneven"],
+                    help="meerkat: the headline stream; uneven: the batched uneven stream "
+                         "(512 snapshots, 1024-4096 channels, 0-60%% flags, 1024/2048 px)")
+    ap.add_argument("--graph", action="store_true",
+                    help="uneven workload: replay one captured toi_batch_run per batch")
     ap.add_argument("--shard-observation", action="store_true",
                     help="with N > 1 ranks, split one observation across them (strong scaling) "
                          "instead of one observation per rank")
@@ -388,6 +564,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven":
+        run_uneven(args)
     else:
         run_ours(args)
 

@@ -238,7 +238,7 @@ typedef struct {
  *
  * toi_batch_prepare validates the snapshots on the host and fills the
  * plan's pinned batch table; toi_batch_run enqueues the batch on the plan's
- * stream (two table copies, then 10 kernels).  toi_batch_run makes no host
+ * stream (two table copies, a counter reset, then 10 kernels).  toi_batch_run makes no host
  * call that a CUDA graph capture forbids, and its launch shapes do not
  * depend on the batch, so one captured toi_batch_run can be replayed for
  * every later batch: call toi_batch_prepare before each replay, after the
@@ -252,8 +252,8 @@ typedef struct {
  * The batch uses its own grid slots (not those of toi_grid) and advances
  * the same image stream as toi_image / tlisi_update.  Errors: TOI_ERR_ARG
  * (batch_max = 0, n outside [1, batch_max], a snapshot failing toi_grid's
- * checks, run without prepare), TOI_ERR_CUDA; data errors as for toi_grid,
- * via toi_sync_status. */
+ * checks, run without prepare), TOI_ERR_UNSUPPORTED (tlisi_tile > 32),
+ * TOI_ERR_CUDA; data errors as for toi_grid, via toi_sync_status. */
 toi_status toi_batch_prepare(toi_plan_t plan, const toi_snapshot* snaps, int32_t n,
                              float* tlisi, int32_t* first_valid);
 toi_status toi_batch_run(toi_plan_t plan);

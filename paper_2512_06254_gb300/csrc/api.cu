@@ -459,6 +459,7 @@ static toi_status check_batch(toi_plan_t p, const toi_snapshot* snaps, int32_t n
   if (p->batch_max < 1) return fail(p, TOI_ERR_ARG, "the plan was made with batch_max = 0");
   if (!snaps || n < 1 || n > p->batch_max)
     return fail(p, TOI_ERR_ARG, "need 1 <= n <= batch_max snapshots");
+  if (p->T > 32) return fail(p, TOI_ERR_UNSUPPORTED, "the batched path needs tlisi_tile <= 32");
   for (int i = 0; i < n; ++i) {
     const toi_snapshot& sn = snaps[i];
     const toi_status st = check_snapshot(p, sn.uvw, sn.freq, sn.vis, sn.chan_scale, sn.weight,

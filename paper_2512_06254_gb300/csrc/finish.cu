@@ -93,11 +93,9 @@ __device__ __forceinline__ void image_tile_body(const float* __restrict__ src, i
                                                 unsigned int* __restrict__ max_cur, int tile) {
   __shared__ double sh[kFinThreads / 32][5];
   __shared__ float kk[3];
-  __shared__ unsigned int smax;
   const int ntx = N / T;
   const int tx = tile % ntx, ty = tile / ntx;
   if (threadIdx.x == 0) {
-    smax = 0u;
     if (REPRO) {
       kk[0] = (float)(-snap[SNAP_XI] / beta_rad);
       kk[1] = (float)(snap[SNAP_ETA] / beta_rad);
@@ -158,18 +156,16 @@ __device__ __forceinline__ void image_tile_body(const float* __restrict__ src, i
     }
   }
   for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, off));
-  // order-free max of |I| (float bits of non-negative floats order like ints)
-  if ((threadIdx.x & 31) == 0) atomicMax(&smax, __float_as_uint(mx));
+  // order-free max of |I| (float bits of non-negative floats order like
+  // ints): one global atomic per warp, so no block barrier is needed for it
+  if ((threadIdx.x & 31) == 0) atomicMax(max_cur, __float_as_uint(mx));
   if (with_moments) {
     float f5[5] = {sa, sb, saa, sbb, sab};
     double v5[5];
     block_reduce_d<5>(f5, sh, v5);
     if (threadIdx.x == 0)
       for (int i = 0; i < 5; ++i) tile_mom[(size_t)tile * 5 + i] = v5[i];
-  } else {
-    __syncthreads();
   }
-  if (threadIdx.x == 0) atomicMax(max_cur, smax);
 }
 
 template <bool REPRO>
@@ -183,9 +179,13 @@ image_tile_kernel(const float* __restrict__ src, int N, int T, const double* __r
                          with_moments, tile_mom, max_cur, blockIdx.x);
 }
 
-// Batch: the images of one batch are made by one launch, and entry i's
-// window includes entries i-1 and i-2 of the same batch, so the images are
-// written first (no moments) and the tile moments follow in a second launch.
+// Batch, in two launches.  Entry i's window holds entries i-1 and i-2 of
+// the same batch, so the images are made first, all entries in parallel
+// (image_tile_body without moments: ring, caller's image, max |I|); then one
+// block per tile walks the entries in stream order and forms the window
+// moments, keeping each pixel's two previous images in registers so that
+// every stored image is read once.  Pixel order and sums are those of
+// image_tile_body: the moments equal the unbatched ones bit for bit.
 __global__ void __launch_bounds__(kFinThreads)
 image_tile_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
                  int T, double beta_rad) {
@@ -195,51 +195,69 @@ image_tile_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict
                         e.image_out, 0, e.tile_mom, e.max_cur, blockIdx.x);
 }
 
-// Tile moments of the window (p2, p1, cur) of stored images, with the pixel
-// order and sums of image_tile_body (so they equal the fused ones bit for bit).
-__device__ __forceinline__ void tile_moments_body(const float* __restrict__ cur,
-                                                  const float* __restrict__ p1,
-                                                  const float* __restrict__ p2, int N, int T,
-                                                  double* __restrict__ tile_mom, int tile) {
-  __shared__ double sh[kFinThreads / 32][5];
-  const int ntx = N / T;
-  const int tx = tile % ntx, ty = tile / ntx;
-  float sa = 0.f, sb = 0.f, saa = 0.f, sbb = 0.f, sab = 0.f;
-  constexpr int kBatch = 4;
-  for (int e0 = threadIdx.x; e0 < T * T; e0 += kBatch * kFinThreads) {
-    float v[kBatch], i1v[kBatch], i0v[kBatch];
-    bool live[kBatch];
-#pragma unroll
-    for (int b = 0; b < kBatch; ++b) {
-      const int e = e0 + b * kFinThreads;
-      live[b] = e < T * T;
-      const int ee = live[b] ? e : 0;
-      const size_t pix = (size_t)(ty * T + ee / T) * N + tx * T + (ee % T);
-      v[b] = cur[pix];
-      i1v[b] = p1[pix];
-      i0v[b] = p2[pix];
-    }
-#pragma unroll
-    for (int b = 0; b < kBatch; ++b) {
-      if (!live[b]) continue;
-      const float a = i1v[b] - i0v[b], bd = v[b] - i1v[b];
-      sa += a; sb += bd; saa += a * a; sbb += bd * bd; sab += a * bd;
-    }
-  }
-  float f5[5] = {sa, sb, saa, sbb, sab};
-  double v5[5];
-  block_reduce_d<5>(f5, sh, v5);
-  if (threadIdx.x == 0)
-    for (int i = 0; i < 5; ++i) tile_mom[(size_t)tile * 5 + i] = v5[i];
-}
+constexpr int kBatchPix = 4;   // pixels per thread of a tile of up to 32 x 32
+
+constexpr int kMaxBatch = 64;   // toi_config.batch_max limit
 
 __global__ void __launch_bounds__(kFinThreads)
-tile_moments_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
-                   int T) {
-  if ((int)blockIdx.y >= hdr->n) return;
-  const BatchEntry& e = E[blockIdx.y];
-  if (!e.with_moments) return;
-  tile_moments_body(e.ring_cur, e.ring_p1, e.ring_p2, N, T, e.tile_mom, blockIdx.x);
+window_moments_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
+                     int T) {
+  // per entry and warp, the five float32 warp sums (as in block_reduce_d)
+  __shared__ float part[kMaxBatch][kFinThreads / 32][5];
+  const int n = hdr->n;
+  const int tile = blockIdx.x;
+  const int ntx = N / T;
+  const int tx = tile % ntx, ty = tile / ntx;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  size_t pixv[kBatchPix];
+  bool live[kBatchPix];
+  float prev1[kBatchPix], prev2[kBatchPix], cur[kBatchPix];
+#pragma unroll
+  for (int b = 0; b < kBatchPix; ++b) {
+    const int e = threadIdx.x + b * kFinThreads;
+    live[b] = e < T * T;
+    const int ee = live[b] ? e : 0;
+    pixv[b] = (size_t)(ty * T + ee / T) * N + tx * T + (ee % T);
+    prev1[b] = E[0].ring_p1[pixv[b]];
+    prev2[b] = E[0].ring_p2[pixv[b]];
+    cur[b] = E[0].ring_cur[pixv[b]];
+  }
+  for (int i = 0; i < n; ++i) {
+    // prefetch the next entry's pixels while this one is summed
+    float nxt[kBatchPix];
+    const float* nsrc = (i + 1 < n) ? E[i + 1].ring_cur : nullptr;
+#pragma unroll
+    for (int b = 0; b < kBatchPix; ++b) nxt[b] = nsrc ? nsrc[pixv[b]] : 0.f;
+    float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < kBatchPix; ++b) {
+      if (!live[b]) continue;
+      const float a = prev1[b] - prev2[b], bd = cur[b] - prev1[b];
+      v[0] += a; v[1] += bd; v[2] += a * a; v[3] += bd * bd; v[4] += a * bd;
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) part[i][wib][k] = v[k];
+#pragma unroll
+    for (int b = 0; b < kBatchPix; ++b) {
+      prev2[b] = prev1[b];
+      prev1[b] = cur[b];
+      cur[b] = nxt[b];
+    }
+  }
+  __syncthreads();
+  // the warp totals of each entry summed in float64 in warp order
+  for (int q = threadIdx.x; q < n * 5; q += blockDim.x) {
+    const int i = q / 5, k = q - 5 * (q / 5);
+    const BatchEntry& e = E[i];
+    if (!e.with_moments) continue;
+    double a = 0.0;
+    for (int wdx = 0; wdx < kFinThreads / 32; ++wdx) a += (double)part[i][wdx][k];
+    e.tile_mom[(size_t)tile * 5 + k] = a;
+  }
 }
 
 __device__ __forceinline__ void tlisi_finish_body(const double* __restrict__ tile_mom, int ntl,
@@ -358,13 +376,14 @@ cudaError_t launch_ring_moments(toi_plan_s* p, const float* image, int cur, int 
 cudaError_t launch_finish_batch(toi_plan_s* p) {
   const int ntl = (p->N / p->T) * (p->N / p->T);
   const int B = p->batch_max;
+  if (p->T * p->T > kBatchPix * kFinThreads) return cudaErrorInvalidConfiguration;
   int tok = prof_begin(p, PROF_REPROJECT, 1);
   image_tile_batch<<<dim3(ntl, B), kFinThreads, 0, p->stream>>>(p->bentry_dev, p->bheader_dev,
                                                                 p->N, p->T, p->beta_rad);
   prof_end(p, tok);
   tok = prof_begin(p, PROF_TLISI, 2);
-  tile_moments_batch<<<dim3(ntl, B), kFinThreads, 0, p->stream>>>(p->bentry_dev, p->bheader_dev,
-                                                                  p->N, p->T);
+  window_moments_batch<<<ntl, kFinThreads, 0, p->stream>>>(p->bentry_dev, p->bheader_dev, p->N,
+                                                           p->T);
   tlisi_finish_batch<<<dim3((ntl + 255) / 256, B), 256, 0, p->stream>>>(p->bentry_dev,
                                                                          p->bheader_dev, ntl, p->T);
   prof_end(p, tok);
