@@ -22,6 +22,8 @@ It is a plain, slow, step-by-step restatement of the method in float64:
                              connected tiles -> bounding boxes, in a fixed FP64
                              evaluation order so that another implementation
                              of the same order reproduces it bit for bit.
+  3-D mode  Section 3.4, App. B, Table 2: t3 on the sphere, slabs,
+                             Chebyshev moments (Jacobi-Anger), the order rule
   adjoint                   reverse mode of S2..S6 (Section 1 names the
                              adjoint route to gradients): bilinear transpose,
                              correction, forward DFT, ES degridding (the
@@ -39,6 +41,9 @@ Parity status per function (pins live in tests/):
   tlisi: parity unpinned against the paper (its formula is not printed);
     pinned only by invariants of the stand-in definition.
   candidates_*: pinned by planted cubes and an independent FFT cross-check.
+  t3_of, slab_plan, chebyshev_*, tilted_image_3d: pinned by Table 2's
+    (Phi_max, N_slab, alpha_slab, K) rows, the sphere constraint of App. B.1,
+    the Jacobi-Anger series, the brute-force I_D^(3) and the coplanar limit.
   *_adjoint, point_source_gradient: pinned by the adjoint identity
     <A x, y> = <x, A^T y> against the forward routines, central finite
     differences of the forward, and the brute-force DFT adjoint.
@@ -530,6 +535,179 @@ def point_source_gradient(uvw_m, freq_hz, grad_vis, l: float, m: float, flux: fl
     return dict(l=float((np.conj(gsum) * dl).real.sum()),
                 m=float((np.conj(gsum) * dm).real.sum()),
                 flux=float((np.conj(gsum) * v).real.sum()))
+
+
+# ==========================================================================
+# Near-coplanar (3-D) mode (Section 3.4, Appendix B, Table 2)
+# ==========================================================================
+
+def t3_of(t1, t2, V):
+    """Section 3.4 (derived in Appendix B.1): the t3 on the celestial sphere
+    for image coordinates (t1, t2), the root that is 0 at t1 = t2 = 0,
+        t3 = -V33 + sgn(V33) sqrt(1 - (t1 + V13)^2 - (t2 + V23)^2).
+    Written without cancellation: with a = t1^2 + 2 t1 V13 + t2^2 + 2 t2 V23
+    (using V13^2 + V23^2 + V33^2 = 1), t3 = -sgn(V33) a / (sqrt(V33^2 - a) + |V33|)."""
+    t1 = np.asarray(t1, dtype=np.float64)
+    t2 = np.asarray(t2, dtype=np.float64)
+    a = t1 * t1 + 2.0 * t1 * V[0, 2] + t2 * t2 + 2.0 * t2 * V[1, 2]
+    v33 = V[2, 2]
+    return -np.sign(v33) * a / (np.sqrt(v33 * v33 - a) + abs(v33))
+
+
+def pixel_t(N: int, cell_arcsec: float):
+    """t1 (columns) and t2 (rows) of the N x N pixel centres (reading c6)."""
+    beta = cell_arcsec * ARCSEC
+    j = np.arange(N) - N // 2
+    return -beta * j, beta * j
+
+
+def t3_max(N: int, cell_arcsec: float, V) -> float:
+    """max |t3| over the image's pixel centres (the valid region D)."""
+    t1, t2 = pixel_t(N, cell_arcsec)
+    return float(np.abs(t3_of(t1[None, :], t2[:, None], V)).max())
+
+
+def chebyshev_coeffs(alpha, K: int) -> np.ndarray:
+    """Jacobi-Anger coefficients of exp(i alpha s) in Chebyshev polynomials
+    (Appendix B.2): c_0 = J_0(alpha), c_k = 2 i^k J_k(alpha); shape
+    alpha.shape + (K,).  scipy's Bessel J is the library step."""
+    from scipy.special import jv
+    alpha = np.asarray(alpha, dtype=np.float64)
+    k = np.arange(K)
+    J = jv(k, alpha[..., None])
+    c = 2.0 * (1j ** k) * J
+    c[..., 0] = J[..., 0]
+    return c
+
+
+def chebyshev_T(s, K: int) -> np.ndarray:
+    """T_k(s) for k < K (shape s.shape + (K,)) by the three-term recurrence."""
+    s = np.asarray(s, dtype=np.float64)
+    T = np.empty(s.shape + (K,))
+    T[..., 0] = 1.0
+    if K > 1:
+        T[..., 1] = s
+    for k in range(2, K):
+        T[..., k] = 2.0 * s * T[..., k - 1] - T[..., k - 2]
+    return T
+
+
+CHEB_ORDERS = (8, 16, 24, 32)
+CHEB_GAMMA = 1e-2
+ALPHA_TARGET = 10.0
+
+
+def chebyshev_order(alpha_slab: float, n_alpha: int = 256, n_s: int = 257):
+    """Section 3.4: the smallest K in {8, 16, 24, 32} whose maximum sampled
+    error |exp(i alpha s) - sum_k c_k(alpha) T_k(s)| over 0 <= alpha <=
+    alpha_slab, -1 <= s <= 1 is below 1e-2, else 32.  Reading: the samples
+    are n_alpha uniform alphas and n_s uniform s, both ends included.
+    Returns (K, error)."""
+    a = np.linspace(0.0, alpha_slab, n_alpha)
+    sv = np.linspace(-1.0, 1.0, n_s)
+    exact = np.exp(1j * a[:, None] * sv[None, :])
+    err = np.inf
+    for K in CHEB_ORDERS:
+        approx = np.einsum("ak,sk->as", chebyshev_coeffs(a, K), chebyshev_T(sv, K))
+        err = float(np.abs(exact - approx).max())
+        if err < CHEB_GAMMA:
+            return K, err
+    return CHEB_ORDERS[-1], err
+
+
+def slab_plan(r3min: float, r3max: float, t3max: float, K=None) -> Dict:
+    """Section 3.4, Eqs. (26)-(27): Phi_max = 2 pi t3max (r3max - r3min)/2,
+    N_slab = max(1, ceil(Phi_max / alpha_target)), slabs of equal width
+    2 dr3 over [r3min, r3max], alpha_slab = 2 pi t3max dr3 and K from
+    chebyshev_order (or as given)."""
+    phi = 2.0 * math.pi * t3max * (r3max - r3min) / 2.0
+    n_slab = max(1, int(math.ceil(phi / ALPHA_TARGET)))
+    dr3 = (r3max - r3min) / (2.0 * n_slab)
+    centres = r3min + (2.0 * np.arange(n_slab) + 1.0) * dr3
+    alpha_slab = 2.0 * math.pi * t3max * dr3
+    if K is None:
+        K, err = chebyshev_order(alpha_slab)
+    else:
+        err = None
+    return dict(phi_max=phi, n_slab=n_slab, dr3=dr3, centres=centres, alpha_slab=alpha_slab,
+                K=K, err=err, r3min=r3min)
+
+
+def slab_of(r3, plan) -> Tuple[np.ndarray, np.ndarray]:
+    """Slab index p and s_q = (r3_q - r3_p) / dr3 of every sample (the last
+    slab is closed; a zero-width range gives s = 0)."""
+    r3 = np.asarray(r3, dtype=np.float64)
+    if plan["dr3"] <= 0.0:
+        return np.zeros(r3.shape, dtype=np.int64), np.zeros(r3.shape)
+    p = np.floor((r3 - plan["r3min"]) / (2.0 * plan["dr3"])).astype(np.int64)
+    p = np.clip(p, 0, plan["n_slab"] - 1)
+    s = (r3 - plan["centres"][p]) / plan["dr3"]
+    return p, s
+
+
+def tilted_image_3d(r, c, N: int, cell_arcsec: float, V, omega: float, sumw: float,
+                    W: int = 8, sigma: int = 2, K=None) -> Dict:
+    """Near-coplanar tilted image (Section 3.4): for every slab p and order
+    k the Chebyshev moment M_pk (ES gridding of T_k(s_q) c_q, full complex
+    centred inverse FFT, grid correction and 1/(omega sum w)), combined per
+    pixel as Re sum_p exp(i 2 pi r3_p t3) sum_k c_k(2 pi dr3 t3) M_pk."""
+    G = sigma * N
+    beta_es = es_beta(W)
+    r = np.asarray(r, dtype=np.float64)
+    c = np.asarray(c, dtype=np.complex128)
+    t1, t2 = pixel_t(N, cell_arcsec)
+    T3 = t3_of(t1[None, :], t2[:, None], V)
+    t3m = float(np.abs(T3).max())
+    plan = slab_plan(float(r[:, 2].min()), float(r[:, 2].max()), t3m, K)
+    p_of, s_of = slab_of(r[:, 2], plan)
+    g1, g2 = grid_coords(r[:, 0], r[:, 1], N, cell_arcsec, sigma)
+    ph = correction_vector(N, G, W, beta_es)
+    corr = 1.0 / (ph[:, None] * ph[None, :]) / (omega * sumw)
+    coef = chebyshev_coeffs(2.0 * math.pi * plan["dr3"] * T3, plan["K"])   # [N, N, K]
+    out = np.zeros((N, N))
+    for p in range(plan["n_slab"]):
+        m = p_of == p
+        if not m.any():
+            continue
+        Tk = chebyshev_T(s_of[m], plan["K"])
+        slab_phase = np.exp(2j * math.pi * plan["centres"][p] * T3)
+        acc = np.zeros((N, N), dtype=np.complex128)
+        for k in range(plan["K"]):
+            grid = grid_es(g1[m], g2[m], c[m] * Tk[:, k], G, W, beta_es)
+            M = ifft_centred(grid, N) * corr
+            acc += coef[:, :, k] * M
+        out += (slab_phase * acc).real
+    return dict(tilted=out, plan=plan, t3=T3, t3max=t3m)
+
+
+def dirty_image_3d_dft(r, c, N: int, cell_arcsec: float, V, omega: float, sumw: float,
+                       rows=None, cols=None) -> np.ndarray:
+    """Exact near-coplanar dirty image I_D^(3) of Section 3.4 by brute force:
+    1/(omega sum w) Re sum_q c_q exp(i 2 pi (r1 t1 + r2 t2 + r3 t3(t1, t2)))."""
+    t1, t2 = pixel_t(N, cell_arcsec)
+    rows = np.arange(N) if rows is None else np.asarray(rows)
+    cols = np.arange(N) if cols is None else np.asarray(cols)
+    r = np.asarray(r)
+    c = np.asarray(c)
+    out = np.zeros((len(rows), len(cols)))
+    for a, j2 in enumerate(rows):
+        tt1 = t1[cols]
+        tt2 = np.full_like(tt1, t2[j2])
+        tt3 = t3_of(tt1, tt2, V)
+        phase = 2 * np.pi * (np.outer(tt1, r[:, 0]) + np.outer(tt2, r[:, 1]) + np.outer(tt3, r[:, 2]))
+        out[a] = (np.exp(1j * phase) @ c).real
+    return out / (omega * sumw)
+
+
+def image_snapshot_3d(uvw_m, freq_hz, vis, flag, weight, N: int, cell_arcsec: float,
+                      W: int = 8, sigma: int = 2, K=None) -> Dict:
+    """S1 + the near-coplanar S2-S5 + S6 for one snapshot."""
+    p = prepare(uvw_m, freq_hz, vis, flag, weight)
+    t = tilted_image_3d(p["r"], p["c"], N, cell_arcsec, p["V"], p["omega"], p["sumw"], W, sigma, K)
+    image = reproject(t["tilted"], cell_arcsec, p["xi"], p["eta"])
+    return dict(V=p["V"], omega=p["omega"], xi=p["xi"], eta=p["eta"], sumw=p["sumw"],
+                r=p["r"], c=p["c"], tilted=t["tilted"], image=image, plan=t["plan"],
+                t3max=t["t3max"])
 
 
 def hermitian_half(grid: np.ndarray) -> np.ndarray:
