@@ -27,6 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "snapshots/s end-to-end (grid+iFFT+tLISI) at MeerKAT shape; % HBM roofline"
+MODE3_HEIGHT_M = 16.4
 WORKLOAD = "meerkat-64ant-2016bl-4096ch-4pol-2048px-1500snap"
 
 # Algorithmic HBM bytes of each stage per snapshot (minimum traffic: every
@@ -147,13 +148,19 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = synth.meerkat_workload(n_snap=args.snapshots)
+    if args.mode == 3:
+        # antenna heights of ~16 m rms give this array Phi_max ~ 5 (one
+        # slab, K = 16), the MeerKAT row of the paper's Table 2
+        from dataclasses import replace as _replace
+        w = _replace(w, height_sigma_m=MODE3_HEIGHT_M)
+        args.engine = "single"
     S = args.snapshots
     T = 32
     nt = w.image_size // T
     pool = make_pool(w, args.pool, dev)
     B = args.batch if args.engine == "batch" else 0
     plan = toi.Plan(w.image_size, w.cell_arcsec, w.n_bl, w.n_chan, w.n_pol, tlisi_tile=T,
-                    batch_max=B)
+                    batch_max=B, mode=args.mode)
     cube = torch.empty(S - 2, nt, nt, dtype=torch.float32, device=dev)
     row_bytes = nt * nt * 4
 
@@ -271,6 +278,7 @@ def run_ours(args):
                "host_pool_snapshots": args.host_pool, "copy_streams": args.copy_streams,
                "engine": args.engine + (f"{B}" if B else "")}
 
+    mode3_plan = plan.mode3_info() if args.mode == 3 else None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -281,7 +289,9 @@ def run_ours(args):
                "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
                "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (seeded MeerKAT-shaped snapshots, resident pool)",
-               "config": {"workload": WORKLOAD, "snapshots_per_step": S,
+               "config": {"workload": WORKLOAD + ("-3d-heights16m" if args.mode == 3 else ""),
+                          "snapshots_per_step": S, "mode": args.mode,
+                          "mode3_plan": mode3_plan,
                           "engine": args.engine + (f"{B}" if B else ""),
                           "resident_pool": args.pool, "image": N_IMG, "grid": G,
                           "tlisi_tile": T, "candidate_mode": "periodic",
@@ -546,6 +556,9 @@ def main():
                     help="single: toi_grid + toi_image + tlisi_update per snapshot; batch: "
                          "toi_batch over --batch snapshots per launch")
     ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--mode", type=int, default=2, choices=[2, 3],
+                    help="3: near-coplanar imaging (slabs + Chebyshev moments) of the stream "
+                         "with antenna heights (single engine)")
     ap.add_argument("--copy-streams", type=int, default=4,
                     help="e2e: copy streams each snapshot's host-to-device copy is split over")
     ap.add_argument("--workload", default="meerkat", choices=["meerkat", "uneven"],

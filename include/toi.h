@@ -78,7 +78,12 @@ typedef struct {
                                default); each entry gets its own grid, FFT and
                                tilted-image workspace, and the image ring
                                holds batch_max + 2 images                       */
-  int32_t reserved[4];      /* must be zero                                     */
+  int32_t mode;             /* 2 (TOI 2-D, default; 0 means 2) or 3 (near-
+                               coplanar, Section 3.4: residual r3 t3 phase by
+                               slabs and Chebyshev moments)                    */
+  int32_t max_moments;      /* mode 3: largest N_slab K a snapshot may need
+                               (0 = 64); two N x N float32 images each          */
+  int32_t reserved[2];      /* must be zero                                     */
 } toi_config;
 
 typedef struct toi_plan_s* toi_plan_t;
@@ -273,6 +278,17 @@ toi_status toi_batch(toi_plan_t plan, const toi_snapshot* snaps, int32_t n, floa
  * were.  Errors as toi_batch_prepare. */
 toi_status toi_autotune(toi_plan_t plan, const toi_snapshot* snaps, int32_t n, int32_t* runs_out,
                         double* us_out);
+
+/* Near-coplanar plan of the snapshot gridded into `slot` (mode 3; host
+ * double[8]): N_slab, K, Phi_max, alpha_slab, dr3 (wavelengths), r3min,
+ * r3max (over the selected samples) and t3max (over the pixel centres) as
+ * chosen by Section 3.4 (Eqs. 26-27, K from {8, 16, 24, 32} by the sampled
+ * truncation error, gamma = 1e-2).  In mode 3 toi_grid does S1 and the
+ * moment gridding and transforms (2 N_slab K passes into the plan's moment
+ * images; it synchronises the stream once to read the selection), and
+ * toi_image combines the moments per pixel before S6-S7.  Errors:
+ * TOI_ERR_ARG (not mode 3, slot never gridded). */
+toi_status toi_mode3_info(toi_plan_t plan, int32_t slot, double* info);
 
 /* Reverse mode of one snapshot's image (gridding, inverse FFT, correction,
  * re-projection of toi_image) for a loss L whose gradient with respect to the

@@ -562,9 +562,12 @@ def pixel_t(N: int, cell_arcsec: float):
 
 
 def t3_max(N: int, cell_arcsec: float, V) -> float:
-    """max |t3| over the image's pixel centres (the valid region D)."""
+    """max |t3| over the image's pixel centres (the valid region D); a pixel
+    whose (t1, t2) is off the visible sphere (no real t3) is not valid."""
     t1, t2 = pixel_t(N, cell_arcsec)
-    return float(np.abs(t3_of(t1[None, :], t2[:, None], V)).max())
+    with np.errstate(invalid="ignore"):
+        t3 = np.abs(t3_of(t1[None, :], t2[:, None], V))
+    return float(np.nanmax(t3)) if np.isfinite(t3).any() else 0.0
 
 
 def chebyshev_coeffs(alpha, K: int) -> np.ndarray:
@@ -656,8 +659,11 @@ def tilted_image_3d(r, c, N: int, cell_arcsec: float, V, omega: float, sumw: flo
     r = np.asarray(r, dtype=np.float64)
     c = np.asarray(c, dtype=np.complex128)
     t1, t2 = pixel_t(N, cell_arcsec)
-    T3 = t3_of(t1[None, :], t2[:, None], V)
-    t3m = float(np.abs(T3).max())
+    with np.errstate(invalid="ignore"):
+        T3 = t3_of(t1[None, :], t2[:, None], V)
+    off = ~np.isfinite(T3)                     # pixels off the visible sphere: image 0
+    T3 = np.where(off, 0.0, T3)
+    t3m = t3_max(N, cell_arcsec, V)
     plan = slab_plan(float(r[:, 2].min()), float(r[:, 2].max()), t3m, K)
     p_of, s_of = slab_of(r[:, 2], plan)
     g1, g2 = grid_coords(r[:, 0], r[:, 1], N, cell_arcsec, sigma)
@@ -677,6 +683,7 @@ def tilted_image_3d(r, c, N: int, cell_arcsec: float, V, omega: float, sumw: flo
             M = ifft_centred(grid, N) * corr
             acc += coef[:, :, k] * M
         out += (slab_phase * acc).real
+    out[off] = 0.0
     return dict(tilted=out, plan=plan, t3=T3, t3max=t3m)
 
 

@@ -32,7 +32,7 @@ EXPORTS = ("toi_config_default", "toi_plan", "toi_plan_destroy", "toi_set_stream
            "toi_image", "tlisi_update", "tlisi_reset", "tlisi_candidates",
            "tlisi_candidates_noalloc",
            "toi_degrid_backward", "toi_batch_prepare", "toi_batch_run", "toi_batch",
-           "toi_autotune", "toi_plan_buffer", "toi_profile_enable", "toi_profile_read",
+           "toi_autotune", "toi_mode3_info", "toi_plan_buffer", "toi_profile_enable", "toi_profile_read",
            "toi_sync_status", "toi_last_error", "toi_status_string")
 PROF_STAGES = ("prep", "bin", "grid", "fft_rows", "fft_cols", "reproject", "tlisi", "backward")
 
@@ -48,7 +48,8 @@ class toi_config(C.Structure):
                 ("max_baselines", C.c_int32), ("max_channels", C.c_int32),
                 ("n_pol", C.c_int32), ("vis_dtype", C.c_int32), ("kernel_support", C.c_int32),
                 ("oversample", C.c_int32), ("tlisi_tile", C.c_int32), ("grid_slots", C.c_int32),
-                ("grid_run", C.c_int32), ("batch_max", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("grid_run", C.c_int32), ("batch_max", C.c_int32), ("mode", C.c_int32),
+                ("max_moments", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class toi_snapshot(C.Structure):
@@ -86,6 +87,7 @@ def lib():
         "toi_batch_run": [P],
         "toi_batch": [P, P, I, P, C.POINTER(I)],
         "toi_autotune": [P, P, I, P, P],
+        "toi_mode3_info": [P, I, P],
         "toi_plan_buffer": [P, I, I, P, C.c_int64, C.POINTER(C.c_int64)],
         "toi_profile_enable": [P, I],
         "toi_profile_read": [P, P, P, I],
@@ -153,7 +155,7 @@ class Plan:
     def __init__(self, image_size: int, cell_arcsec: float, max_baselines: int,
                  max_channels: int, n_pol: int, *, vis_dtype: int = TOI_VIS_C64,
                  tlisi_tile: int = 32, grid_slots: int = 1, grid_run: int = 0, batch_max: int = 0,
-                 stream=None):
+                 mode: int = 2, max_moments: int = 0, stream=None):
         import torch
         self.cfg = config_default(image_size, cell_arcsec, max_baselines, max_channels, n_pol)
         self.cfg.vis_dtype = vis_dtype
@@ -161,6 +163,8 @@ class Plan:
         self.cfg.grid_slots = grid_slots
         self.cfg.grid_run = grid_run
         self.cfg.batch_max = batch_max
+        self.cfg.mode = mode
+        self.cfg.max_moments = max_moments
         self.N = image_size
         self.T = tlisi_tile
         h = C.c_void_p()
@@ -263,6 +267,13 @@ class Plan:
         _check(lib().toi_autotune(self.handle, C.cast(arr, C.c_void_p), len(snaps),
                                   C.cast(runs, C.c_void_p), C.cast(us, C.c_void_p)), self.handle)
         return ({b: runs[b] for b in range(4) if runs[b]}, {b: us[b] for b in range(4) if runs[b]})
+
+    def mode3_info(self, slot: int = 0):
+        """toi_mode3_info as a dict."""
+        out = (C.c_double * 8)()
+        _check(lib().toi_mode3_info(self.handle, slot, C.cast(out, C.c_void_p)), self.handle)
+        keys = ("n_slab", "K", "phi_max", "alpha_slab", "dr3", "r3min", "r3max", "t3max")
+        return {k: (int(out[i]) if i < 2 else out[i]) for i, k in enumerate(keys)}
 
     def buffer(self, which: int, slot: int = 0):
         """Copy of a plan-owned buffer as a new CUDA tensor (see toi_plan_buffer)."""

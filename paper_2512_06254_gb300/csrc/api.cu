@@ -127,6 +127,7 @@ void free_plan(toi_plan_s* p) {
   for (float* r : p->ring) cudaFree(r);
   cudaFree(p->ring_max); cudaFree(p->tile_mom); cudaFree(p->d_status);
   cudaFree(p->adj_scratch);
+  cudaFree(p->moments); cudaFree(p->m3_dev); cudaFree(p->m3_slabs); cudaFreeHost(p->m3_host);
   if (p->bslots) {
     for (int i = 0; i < p->batch_max; ++i) {
       cudaFree(p->bslots[i].grid);
@@ -215,7 +216,13 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     return fail(nullptr, TOI_ERR_ARG, "grid_run must be 0 (automatic) or in [8, 1024]");
   if (c.batch_max < 0 || c.batch_max > 64)
     return fail(nullptr, TOI_ERR_ARG, "batch_max must be in [0, 64]");
-  for (int i = 0; i < 4; ++i)
+  if (!(c.mode == 0 || c.mode == 2 || c.mode == 3))
+    return fail(nullptr, TOI_ERR_ARG, "mode must be 2 (or 0) or 3");
+  if (c.max_moments < 0 || c.max_moments > 1024)
+    return fail(nullptr, TOI_ERR_ARG, "max_moments must be in [0, 1024]");
+  if (c.mode == 3 && c.batch_max > 0)
+    return fail(nullptr, TOI_ERR_UNSUPPORTED, "the batched path is 2-D only (mode 3 with batch_max > 0)");
+  for (int i = 0; i < 2; ++i)
     if (c.reserved[i] != 0) return fail(nullptr, TOI_ERR_ARG, "reserved fields must be zero");
   if ((long long)c.max_baselines * c.max_channels * c.n_pol > (1LL << 40))
     return fail(nullptr, TOI_ERR_ARG, "max_baselines x max_channels too large");
@@ -223,6 +230,8 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   toi_plan_s* p = new (std::nothrow) toi_plan_s();
   if (!p) return fail(nullptr, TOI_ERR_OOM, "host allocation failed");
   p->cfg = c;
+  if (p->cfg.mode == 0) p->cfg.mode = 2;
+  if (p->cfg.max_moments == 0) p->cfg.max_moments = 64;
   p->N = c.image_size;
   p->G = c.oversample * c.image_size;
   p->W = c.kernel_support;
@@ -260,6 +269,13 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   TOI_ALLOC(p->tile_mom, (size_t)ntl * 5, "tile moments");
   TOI_ALLOC(p->d_status, 1, "status word");
   TOI_ALLOC(p->adj_scratch, toi::degrid_scratch_doubles(), "adjoint scratch");
+  if (p->cfg.mode == 3) {
+    TOI_ALLOC(p->moments, (size_t)2 * p->cfg.max_moments * N * N, "moment images");
+    TOI_ALLOC(p->m3_dev, (size_t)16 + 256 * 32, "near-coplanar selection");
+    TOI_ALLOC(p->m3_slabs, (size_t)p->cfg.max_moments, "slab centres");
+    e = cudaMallocHost((void**)&p->m3_host, sizeof(double) * 16);
+    if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "near-coplanar host buffer"); free_plan(p); return r; }
+  }
   p->batch_max = c.batch_max;
   if (p->batch_max > 0) {
     const int B = p->batch_max;
@@ -370,8 +386,19 @@ toi_status toi_grid(toi_plan_t p, const double* uvw_m, const double* freq_hz, co
   }
   e = toi::launch_prep(p, s, uvw_m, freq_hz, weight, flag, n_bl, n_ch);
   if (e != cudaSuccess) return cuda_fail(p, e, "toi_grid/prep");
-  e = toi::launch_grid(p, s, freq_hz, vis, chan_scale, weight, flag, n_bl, n_ch);
-  if (e != cudaSuccess) return cuda_fail(p, e, "toi_grid/grid");
+  if (p->cfg.mode == 3) {
+    e = toi::mode3_select(p, s, weight, flag, n_bl, n_ch);
+    if (e == cudaErrorNotSupported)
+      return fail(p, TOI_ERR_UNSUPPORTED,
+                  "the snapshot needs N_slab K = " + std::to_string(s.m3.n_slab * s.m3.K) +
+                      " moments, more than max_moments = " + std::to_string(p->cfg.max_moments));
+    if (e != cudaSuccess) return cuda_fail(p, e, "toi_grid/mode3 selection");
+    e = toi::mode3_moments(p, s, vis, chan_scale, weight, flag, n_bl, n_ch);
+    if (e != cudaSuccess) return cuda_fail(p, e, "toi_grid/mode3 moments");
+  } else {
+    e = toi::launch_grid(p, s, freq_hz, vis, chan_scale, weight, flag, n_bl, n_ch);
+    if (e != cudaSuccess) return cuda_fail(p, e, "toi_grid/grid");
+  }
   s.uvw = uvw_m; s.freq = freq_hz; s.vis = vis; s.chan_scale = chan_scale;
   s.weight = weight; s.flag = flag; s.nbl = n_bl; s.nch = n_ch; s.valid = true;
   return TOI_OK;
@@ -382,7 +409,7 @@ toi_status toi_image(toi_plan_t p, int32_t slot, float* image, double* snap_info
   if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
   Slot& s = p->slots[slot];
   if (!s.valid) return fail(p, TOI_ERR_ARG, "slot has not been gridded since its last toi_image");
-  cudaError_t e = toi::launch_fft(p, s);
+  cudaError_t e = p->cfg.mode == 3 ? toi::launch_combine3(p, s) : toi::launch_fft(p, s);
   if (e != cudaSuccess) return cuda_fail(p, e, "toi_image/fft");
   s.valid = false;   // the row pass consumed (and cleared) the grid
   const int cur = ring_idx(p, p->nimg);
@@ -655,6 +682,17 @@ toi_status tlisi_candidates(const float* cube, int32_t S, int32_t nty, int32_t n
   return TOI_OK;
 }
 
+toi_status toi_mode3_info(toi_plan_t p, int32_t slot, double* info) {
+  if (!p || !info) return fail(p, TOI_ERR_ARG, "plan and info must be non-NULL");
+  if (p->cfg.mode != 3) return fail(p, TOI_ERR_ARG, "the plan is not in mode 3");
+  if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
+  const toi::Mode3Plan& m = p->slots[slot].m3;
+  if (!p->slots[slot].uvw) return fail(p, TOI_ERR_ARG, "slot has not been gridded");
+  info[0] = m.n_slab; info[1] = m.K; info[2] = m.phi; info[3] = m.alpha_slab;
+  info[4] = m.dr3; info[5] = m.r3min; info[6] = m.r3max; info[7] = m.t3max;
+  return TOI_OK;
+}
+
 // NULL counts as aligned
 static bool aligned(const void* ptr, uintptr_t a) { return ((uintptr_t)ptr & (a - 1)) == 0; }
 
@@ -669,6 +707,7 @@ toi_status toi_degrid_backward(toi_plan_t p, int32_t slot, const float* grad_ima
   if (grad_weight && !image) return fail(p, TOI_ERR_ARG, "grad_weight needs the image of toi_image");
   Slot& s = p->slots[slot];
   if (!s.uvw) return fail(p, TOI_ERR_ARG, "slot has not been gridded");
+  if (p->cfg.mode == 3) return fail(p, TOI_ERR_UNSUPPORTED, "toi_degrid_backward is 2-D only");
   if (!aligned(grad_image, 4) || !aligned(image, 4) || !aligned(grad_sample, 8) ||
       !aligned(grad_vis, 8) || !aligned(grad_weight, 4))
     return fail(p, TOI_ERR_ARG, "misaligned pointer (element alignment)");

@@ -404,7 +404,7 @@ void launch_adj_g(toi_plan_s* p, Slot& s) {
 }
 
 template <int G>
-void launch_g(toi_plan_s* p, Slot& s) {
+void launch_g(toi_plan_s* p, Slot& s, float* out) {
   const int N = p->N;
   int tok = prof_begin(p, PROF_FFT_ROWS, 1);
   fft_rows_kernel<G><<<G / 2, RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
@@ -413,7 +413,7 @@ void launch_g(toi_plan_s* p, Slot& s) {
   tok = prof_begin(p, PROF_FFT_COLS, 1);
   constexpr int CW = ColCfg<G>::CW;
   fft_cols_kernel<G><<<N / CW, ColCfg<G>::NT, 2 * ColCfg<G>::LEN * sizeof(float2), p->stream>>>(
-      p->fft_tmp, N, p->twiddle, p->corr, s.snap, p->tilted);
+      p->fft_tmp, N, p->twiddle, p->corr, s.snap, out);
   prof_end(p, tok);
 }
 
@@ -430,19 +430,21 @@ cudaError_t fft_configure() {
   return configure_g<8192>();
 }
 
-cudaError_t launch_fft(toi_plan_s* p, Slot& s) {
+cudaError_t launch_fft_to(toi_plan_s* p, Slot& s, float* out) {
   switch (p->G) {
-    case 128: launch_g<128>(p, s); break;
-    case 256: launch_g<256>(p, s); break;
-    case 512: launch_g<512>(p, s); break;
-    case 1024: launch_g<1024>(p, s); break;
-    case 2048: launch_g<2048>(p, s); break;
-    case 4096: launch_g<4096>(p, s); break;
-    case 8192: launch_g<8192>(p, s); break;
+    case 128: launch_g<128>(p, s, out); break;
+    case 256: launch_g<256>(p, s, out); break;
+    case 512: launch_g<512>(p, s, out); break;
+    case 1024: launch_g<1024>(p, s, out); break;
+    case 2048: launch_g<2048>(p, s, out); break;
+    case 4096: launch_g<4096>(p, s, out); break;
+    case 8192: launch_g<8192>(p, s, out); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
+
+cudaError_t launch_fft(toi_plan_s* p, Slot& s) { return launch_fft_to(p, s, p->tilted); }
 
 cudaError_t launch_fft_batch(toi_plan_s* p) {
   switch (p->G) {

@@ -254,6 +254,30 @@ __device__ __forceinline__ void prepare(const Sample& s, float s1hi, float s1lo,
   if (conj) p.c.y = -p.c.y;
 }
 
+// Near-coplanar moments (Section 3.4): a pass grids T_order(s_q) c_q (or
+// -i T_order(s_q) c_q for the imaginary part) of the samples of one r3 slab,
+// with r3_q = r3(baseline) k and s_q = (r3_q - r3_slab) / dr3.  The factor is
+// applied before the mirror conjugation, so mirror tracks store conj of it.
+__device__ __forceinline__ float2 moment_value(float2 c, float r3, const MomentPass& m) {
+  float s = 0.f;
+  if (!m.zero_width) {
+    int p = (int)floorf((r3 - m.r3min) * m.inv2dr3);
+    p = p < 0 ? 0 : (p > m.nslab - 1 ? m.nslab - 1 : p);
+    if (p != m.slab) return make_float2(0.f, 0.f);
+    s = (r3 - m.centre) * m.inv_dr3;
+  }
+  float t = m.order == 0 ? 1.f : s;   // T_order(s) by T_{k+1} = 2 s T_k - T_{k-1}
+  float tm = 1.f;
+  for (int k = 2; k <= m.order; ++k) {
+    const float tn = 2.f * s * t - tm;
+    tm = t;
+    t = tn;
+  }
+  c.x *= t;
+  c.y *= t;
+  return m.imag ? make_float2(c.y, -c.x) : c;
+}
+
 // Per-lane shared-memory staging of the visibility stream: each lane keeps
 // two stages of kStage samples in flight with cp.async (completion tracked by
 // async-copy groups, so no register waits on outstanding loads).
@@ -316,7 +340,7 @@ __device__ __forceinline__ Sample read_staged(const StageBuf& sb, int sidx, int 
 
 // One warp's work: segment `seg` of track `track` (tracks [0, nbl) are the
 // upper-half tracks of the baselines, [nbl, 2 nbl) their mirrors).
-template <bool HALF>
+template <bool HALF, bool MOM>
 __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef,
                                            const float2* __restrict__ kf,
                                            const void* __restrict__ vis,
@@ -324,7 +348,8 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
                                            const float* __restrict__ weight,
                                            const uint8_t* __restrict__ flag, int nbl, int nch,
                                            int npol, int G, float bl2, int run, int track,
-                                           int seg, StageBuf& sb, float2* __restrict__ H) {
+                                           int seg, StageBuf& sb, float2* __restrict__ H,
+                                           const MomentPass& mp) {
   const int lane = threadIdx.x & 31;
   const int mirror = track >= nbl ? 1 : 0;
   const int bl = track - mirror * nbl;
@@ -339,6 +364,21 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
   // fit) stores nothing
   const double reach = fmax(fabs(t.s1), fabs(t.s2)) * fmax(kf0, kf1);
   if (!(reach < 2.0 * G)) return;
+  float r3bl = 0.f;
+  if (MOM) {
+    r3bl = (float)coef[bl].r3;
+    if (!mp.zero_width && mp.nslab > 1) {
+      // skip a segment whose r3 range misses the slab (channels are monotonic)
+      const int w0 = seg * 32 * run, w1 = min(nch, (seg + 1) * 32 * run) - 1;
+      const float2 ka = kf[w0], kb = kf[w1 < w0 ? w0 : w1];
+      const float ra = r3bl * (ka.x + ka.y), rb = r3bl * (kb.x + kb.y);
+      const float lo = fminf(ra, rb), hi = fmaxf(ra, rb);
+      const float slo = mp.r3min + (float)mp.slab / mp.inv2dr3;
+      const float shi = mp.r3min + (float)(mp.slab + 1) / mp.inv2dr3;
+      const float tol = 1e-3f * (shi - slo);
+      if ((mp.slab > 0 && hi < slo - tol) || (mp.slab < mp.nslab - 1 && lo > shi + tol)) return;
+    }
+  }
   const int c_begin = (seg * 32 + lane) * run;
   const int c_end = min(nch, c_begin + run);
   if (c_begin >= nch) return;
@@ -393,7 +433,9 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
   {
     const Sample s0 = read_staged<HALF>(sb, 0, 0, lane, chan_scale, weight, flag, kf,
                                         obase + (size_t)c_begin * npol, c_begin, npol, pa, pb);
-    prepare(s0, s1hi, s1lo, s2hi, s2lo, cx, cy, sx, sy, t.conj, cur);
+    Sample s0m = s0;
+    if (MOM) s0m.c = moment_value(s0.c, r3bl * (s0.k.x + s0.k.y), mp);
+    prepare(s0m, s1hi, s1lo, s2hi, s2lo, cx, cy, sx, sy, t.conj, cur);
   }
   int ox = sx > 0 ? cur.kx0 : cur.kx0 + kW - 1;
   int oy = sy > 0 ? cur.ky0 : cur.ky0 + kW - 1;
@@ -456,6 +498,7 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
       for (int p = 0; p < kWin; ++p) ofy[p] = fsy * (float)((p - ry) & (kWin - 1));
     }
     Prepared nxt;
+    if (MOM) sn.c = moment_value(sn.c, r3bl * (sn.k.x + sn.k.y), mp);
     prepare(sn, s1hi, s1lo, s2hi, s2lo, cx, cy, sx, sy, t.conj, nxt);
     // kernel values in physical order: physical index p holds tap (p - r) mod W
     float px[kWin];
@@ -479,21 +522,21 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
   flush_all(w, H, G, ox, oy, sx, sy, rx, ry);
 }
 
-template <bool HALF>
+template <bool HALF, bool MOM>
 __global__ void __launch_bounds__(kWarps * 32)
 grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restrict__ kf,
                    const void* __restrict__ vis, const float* __restrict__ chan_scale,
                    const float* __restrict__ weight, const uint8_t* __restrict__ flag, int nbl,
                    int nch, int npol, int G, float bl2, int run, int nseg,
-                   float2* __restrict__ H) {
+                   float2* __restrict__ H, MomentPass mp) {
   __shared__ StageBuf stage_all[kWarps];
   const int wib = threadIdx.x >> 5;
   const int warp = blockIdx.x * kWarps + wib;
   if (warp >= 2 * nbl * nseg) return;
   // warps [0, nbl * nseg) walk the upper-half tracks, the rest their mirrors
   // (most mirror warps exit at once, so they are kept out of the busy blocks)
-  grid_track<HALF>(coef, kf, vis, chan_scale, weight, flag, nbl, nch, npol, G, bl2, run,
-                   warp / nseg, warp % nseg, stage_all[wib], H);
+  grid_track<HALF, MOM>(coef, kf, vis, chan_scale, weight, flag, nbl, nch, npol, G, bl2, run,
+                        warp / nseg, warp % nseg, stage_all[wib], H, mp);
 }
 
 // Persistent gridder over a batch: each warp takes work items from a
@@ -530,8 +573,9 @@ grid_batch_kernel(const BatchEntry* __restrict__ E, const BatchHeader* __restric
     const BatchEntry& e = E[ent];
     const int seg = (int)(local % e.nseg);
     const int track = (int)(local / e.nseg) + (mir ? e.nbl : 0);
-    grid_track<HALF>(e.coef, e.kf, e.vis, e.chan_scale, e.weight, e.flag, e.nbl, e.nch, npol, G,
-                     bl2, e.run, track, seg, stage_all[wib], e.grid);
+    const MomentPass none{};
+    grid_track<HALF, false>(e.coef, e.kf, e.vis, e.chan_scale, e.weight, e.flag, e.nbl, e.nch,
+                            npol, G, bl2, e.run, track, seg, stage_all[wib], e.grid, none);
   }
 }
 
@@ -576,10 +620,9 @@ cudaError_t launch_grid_batch(toi_plan_s* p, bool half) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_grid(toi_plan_s* p, Slot& s, const double* freq, const void* vis,
-                        const float* chan_scale, const float* weight, const uint8_t* flag,
-                        int nbl, int nch) {
-  (void)freq;
+static cudaError_t launch_grid_impl(toi_plan_s* p, Slot& s, const void* vis,
+                                    const float* chan_scale, const float* weight,
+                                    const uint8_t* flag, int nbl, int nch, const MomentPass* mp) {
   const int G = p->G;
   const int tok = prof_begin(p, PROF_GRID, 1);
   // the slot is zero: cleared at plan creation, by the row pass of the
@@ -591,16 +634,39 @@ cudaError_t launch_grid(toi_plan_s* p, Slot& s, const double* freq, const void* 
   const int blocks = (int)((nwarps + kWarps - 1) / kWarps);
   const float bl2 = (float)(p->beta_es * 1.4426950408889634);
   const bool half = p->cfg.vis_dtype == TOI_VIS_C16_CHANSCALE;
-  if (half)
-    grid_tracks_kernel<true><<<blocks, kWarps * 32, 0, p->stream>>>(
+  const MomentPass none{};
+  const MomentPass m = mp ? *mp : none;
+  if (half && mp)
+    grid_tracks_kernel<true, true><<<blocks, kWarps * 32, 0, p->stream>>>(
         s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, G, bl2, run, nseg,
-        s.grid);
+        s.grid, m);
+  else if (half)
+    grid_tracks_kernel<true, false><<<blocks, kWarps * 32, 0, p->stream>>>(
+        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, G, bl2, run, nseg,
+        s.grid, m);
+  else if (mp)
+    grid_tracks_kernel<false, true><<<blocks, kWarps * 32, 0, p->stream>>>(
+        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, G, bl2, run, nseg,
+        s.grid, m);
   else
-    grid_tracks_kernel<false><<<blocks, kWarps * 32, 0, p->stream>>>(
+    grid_tracks_kernel<false, false><<<blocks, kWarps * 32, 0, p->stream>>>(
         s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, G, bl2, run, nseg,
-        s.grid);
+        s.grid, m);
   prof_end(p, tok);
   return cudaGetLastError();
+}
+
+cudaError_t launch_grid(toi_plan_s* p, Slot& s, const double* freq, const void* vis,
+                        const float* chan_scale, const float* weight, const uint8_t* flag,
+                        int nbl, int nch) {
+  (void)freq;
+  return launch_grid_impl(p, s, vis, chan_scale, weight, flag, nbl, nch, nullptr);
+}
+
+cudaError_t launch_grid_moment(toi_plan_s* p, Slot& s, const void* vis, const float* chan_scale,
+                               const float* weight, const uint8_t* flag, int nbl, int nch,
+                               const MomentPass& mp) {
+  return launch_grid_impl(p, s, vis, chan_scale, weight, flag, nbl, nch, &mp);
 }
 
 }  // namespace toi

@@ -33,6 +33,22 @@ struct BaselineCoef {
   double a1, a2, r3, pad;
 };
 
+// One gridding pass of the near-coplanar mode: Chebyshev order `order` of
+// r3 slab `slab` (real part, or the imaginary part when imag != 0).
+struct MomentPass {
+  float r3min = 0.f, inv2dr3 = 0.f;   // slab index = floor((r3 - r3min) * inv2dr3), clamped
+  float centre = 0.f, inv_dr3 = 0.f;  // s = (r3 - centre) * inv_dr3
+  int slab = 0, nslab = 1, order = 0, imag = 0;
+  int zero_width = 1;                 // r3 range of zero width: s = 0 for every sample
+};
+
+// Host copy of a snapshot's near-coplanar plan (Section 3.4, Eqs. 26-27).
+struct Mode3Plan {
+  bool ready = false;
+  int n_slab = 0, K = 0;
+  double r3min = 0, r3max = 0, t3max = 0, phi = 0, dr3 = 0, alpha_slab = 0, err = 0;
+};
+
 struct Slot {
   float2* grid = nullptr;          // [G/2][G] Hermitian half-plane grid
   double* snap = nullptr;          // [SNAP_LEN]
@@ -46,6 +62,7 @@ struct Slot {
   const uint8_t* flag = nullptr;
   int nbl = 0, nch = 0;
   bool valid = false;   // holds a grid from toi_grid that toi_image has not consumed
+  Mode3Plan m3;         // near-coplanar mode: the moment plan of the gridded snapshot
 };
 
 // One snapshot of a batch as the batched kernels see it (device copy of a
@@ -134,6 +151,11 @@ struct toi_plan_s {
   double* tile_mom = nullptr;            // [ntl][6]
   int* d_status = nullptr;               // device status word
   double* adj_scratch = nullptr;         // partial sums and <dL/dI, I> of the adjoint
+  // near-coplanar mode
+  float* moments = nullptr;              // [2 max_moments][N][N] Re / Im moment images
+  double* m3_dev = nullptr;              // selection scratch (keys, errors, plan)
+  double* m3_host = nullptr;             // pinned copy of the selection results
+  float* m3_slabs = nullptr;             // [max_moments] slab centres (float)
   long long nimg = 0;                    // images in the ring since reset
   const float* last_image = nullptr;     // output pointer of the last toi_image
   bool fused_pending = false;
@@ -173,6 +195,16 @@ cudaError_t launch_grid(toi_plan_s* p, Slot& s, const double* freq, const void* 
                         int nbl, int nch);
 // fft.cu
 cudaError_t launch_fft(toi_plan_s* p, Slot& s);
+cudaError_t launch_fft_to(toi_plan_s* p, Slot& s, float* out);
+cudaError_t launch_grid_moment(toi_plan_s* p, Slot& s, const void* vis, const float* chan_scale,
+                               const float* weight, const uint8_t* flag, int nbl, int nch,
+                               const MomentPass& mp);
+// mode3.cu
+cudaError_t mode3_select(toi_plan_s* p, Slot& s, const float* weight, const uint8_t* flag,
+                         int nbl, int nch);
+cudaError_t mode3_moments(toi_plan_s* p, Slot& s, const void* vis, const float* chan_scale,
+                          const float* weight, const uint8_t* flag, int nbl, int nch);
+cudaError_t launch_combine3(toi_plan_s* p, Slot& s);
 // finish.cu
 cudaError_t launch_reproject_moments(toi_plan_s* p, Slot& s, float* image_out,
                                      bool with_moments, int cur, int prev1, int prev2);

@@ -81,6 +81,8 @@ class Workload:
     dump_s: float = 8.0
     layout_radius_m: float = 1000.0
     sources: tuple = field(default_factory=tuple)
+    height_sigma_m: float = 0.0   # antenna heights ~ N(0, sigma) (non-coplanar array)
+    curvature: bool = False       # antennas on the Earth's surface (height -(e^2+n^2)/2R)
 
     @property
     def n_bl(self) -> int:
@@ -127,10 +129,20 @@ def layout_meerkat(seed: int, n_core: int = 48, n_arm: int = 16,
 
 def array_layout(w: Workload) -> torch.Tensor:
     if w.layout == "disc":
-        return layout_disc(w.n_ant, w.layout_radius_m, w.seed_layout)
-    if w.layout == "meerkat":
-        return layout_meerkat(w.seed_layout)
-    raise ValueError(w.layout)
+        enu = layout_disc(w.n_ant, w.layout_radius_m, w.seed_layout)
+    elif w.layout == "meerkat":
+        enu = layout_meerkat(w.seed_layout)
+    else:
+        raise ValueError(w.layout)
+    if w.height_sigma_m > 0.0 or w.curvature:
+        enu = enu.clone()
+        if w.height_sigma_m > 0.0:
+            g = torch.Generator().manual_seed(w.seed_layout + 7)
+            enu[:, 2] += w.height_sigma_m * torch.randn(enu.shape[0], generator=g,
+                                                        dtype=enu.dtype)
+        if w.curvature:
+            enu[:, 2] -= (enu[:, 0] ** 2 + enu[:, 1] ** 2) / (2.0 * 6.371e6)
+    return enu
 
 
 def baseline_uvw(enu: torch.Tensor, lat_rad: float, dec_rad: float,
