@@ -128,6 +128,7 @@ void free_plan(toi_plan_s* p) {
   cudaFree(p->ring_max); cudaFree(p->tile_mom); cudaFree(p->d_status);
   cudaFree(p->adj_scratch);
   cudaFree(p->moments); cudaFree(p->m3_dev); cudaFree(p->m3_slabs); cudaFreeHost(p->m3_host);
+  cudaFree(p->grid2);
   if (p->bslots) {
     for (int i = 0; i < p->batch_max; ++i) {
       cudaFree(p->bslots[i].grid);
@@ -273,6 +274,7 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     TOI_ALLOC(p->moments, (size_t)2 * p->cfg.max_moments * N * N, "moment images");
     TOI_ALLOC(p->m3_dev, (size_t)16 + 256 * 32, "near-coplanar selection");
     TOI_ALLOC(p->m3_slabs, (size_t)p->cfg.max_moments, "slab centres");
+    TOI_ALLOC(p->grid2, (size_t)(G / 2) * G, "second grid");
     e = cudaMallocHost((void**)&p->m3_host, sizeof(double) * 16);
     if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "near-coplanar host buffer"); free_plan(p); return r; }
   }
@@ -334,6 +336,7 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     e = cudaMemset(p->slots[i].grid, 0, sizeof(float2) * (size_t)(G / 2) * G);
   for (int i = 0; i < p->batch_max && e == cudaSuccess; ++i)
     e = cudaMemset(p->bslots[i].grid, 0, sizeof(float2) * (size_t)(G / 2) * G);
+  if (p->grid2 && e == cudaSuccess) e = cudaMemset(p->grid2, 0, sizeof(float2) * (size_t)(G / 2) * G);
   if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "initialising plan tables"); free_plan(p); return r; }
   *out = p;
   return TOI_OK;

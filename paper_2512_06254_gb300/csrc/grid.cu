@@ -100,9 +100,23 @@ struct Window {
   float2 a[kWin][kWin];   // a[physical row][physical column]
 };
 
-__device__ __forceinline__ void flush_cell(float2* __restrict__ H, int G, int x, int y, float2 v) {
-  if ((v.x != 0.f || v.y != 0.f) && x >= 0 && x < G && y >= 0 && y < (G >> 1))
-    red_add(H + (size_t)y * G + x, v);
+// Where a window's cells go: the grid H, and in a near-coplanar pass also
+// H2, which receives the imaginary-part moment.  Along one track the
+// imaginary pass's values are -i times the real pass's on an upper track and
+// +i times them on a mirror track (whose values are conjugated), so one
+// window serves both grids: H2 gets rs * (-i v), rs = +1 or -1.
+struct Sink {
+  float2* H;
+  float2* H2;
+  float rs;
+};
+
+__device__ __forceinline__ void flush_cell(const Sink& snk, int G, int x, int y, float2 v) {
+  if ((v.x != 0.f || v.y != 0.f) && x >= 0 && x < G && y >= 0 && y < (G >> 1)) {
+    const size_t idx = (size_t)y * G + x;
+    red_add(snk.H + idx, v);
+    if (snk.H2) red_add(snk.H2 + idx, make_float2(snk.rs * v.y, -snk.rs * v.x));
+  }
 }
 
 // absolute coordinate of physical index p for phase r, origin o, direction s
@@ -110,7 +124,7 @@ __device__ __forceinline__ int phys_to_abs(int p, int r, int o, int s) {
   return o + s * ((p - r) & (kWin - 1));
 }
 
-__device__ __forceinline__ void flush_all(Window& w, float2* __restrict__ H, int G, int ox, int oy,
+__device__ __forceinline__ void flush_all(Window& w, const Sink& H, int G, int ox, int oy,
                                           int sx, int sy, int rx, int ry) {
 #pragma unroll
   for (int j = 0; j < kWin; ++j) {
@@ -124,7 +138,7 @@ __device__ __forceinline__ void flush_all(Window& w, float2* __restrict__ H, int
 }
 
 template <int P>
-__device__ __forceinline__ void flush_col(Window& w, float2* __restrict__ H, int G, int x, int oy,
+__device__ __forceinline__ void flush_col(Window& w, const Sink& H, int G, int x, int oy,
                                           int sy, int ry) {
 #pragma unroll
   for (int j = 0; j < kWin; ++j) {
@@ -134,7 +148,7 @@ __device__ __forceinline__ void flush_col(Window& w, float2* __restrict__ H, int
 }
 
 template <int P>
-__device__ __forceinline__ void flush_row(Window& w, float2* __restrict__ H, int G, int y, int ox,
+__device__ __forceinline__ void flush_row(Window& w, const Sink& H, int G, int y, int ox,
                                           int sx, int rx) {
 #pragma unroll
   for (int i = 0; i < kWin; ++i) {
@@ -144,7 +158,7 @@ __device__ __forceinline__ void flush_row(Window& w, float2* __restrict__ H, int
 }
 
 // slide one column forwards: physical column rx (logical column 0) is final
-__device__ __forceinline__ void slide_x(Window& w, float2* __restrict__ H, int G, int ox, int oy,
+__device__ __forceinline__ void slide_x(Window& w, const Sink& H, int G, int ox, int oy,
                                         int sy, int rx, int ry) {
   switch (rx) {
     case 0: flush_col<0>(w, H, G, ox, oy, sy, ry); break;
@@ -158,7 +172,7 @@ __device__ __forceinline__ void slide_x(Window& w, float2* __restrict__ H, int G
   }
 }
 
-__device__ __forceinline__ void slide_y(Window& w, float2* __restrict__ H, int G, int ox, int oy,
+__device__ __forceinline__ void slide_y(Window& w, const Sink& H, int G, int ox, int oy,
                                         int sx, int rx, int ry) {
   switch (ry) {
     case 0: flush_row<0>(w, H, G, oy, ox, sx, rx); break;
@@ -364,6 +378,7 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
   // fit) stores nothing
   const double reach = fmax(fabs(t.s1), fabs(t.s2)) * fmax(kf0, kf1);
   if (!(reach < 2.0 * G)) return;
+  const Sink snk{H, MOM ? mp.grid2 : nullptr, t.conj ? -1.f : 1.f};
   float r3bl = 0.f;
   if (MOM) {
     r3bl = (float)coef[bl].r3;
@@ -474,7 +489,7 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
     int dx = sx > 0 ? cur.kx0 - ox : ox - (cur.kx0 + kW - 1);
     int dy = sy > 0 ? cur.ky0 - oy : oy - (cur.ky0 + kW - 1);
     if (dx < 0 || dy < 0 || dx >= kWin || dy >= kWin) {
-      flush_all(w, H, G, ox, oy, sx, sy, rx, ry);
+      flush_all(w, snk, G, ox, oy, sx, sy, rx, ry);
       ox = sx > 0 ? cur.kx0 : cur.kx0 + kW - 1;
       oy = sy > 0 ? cur.ky0 : cur.ky0 + kW - 1;
       rx = 0;
@@ -488,12 +503,12 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
       }
     }
     if (dx > 0) {
-      do { slide_x(w, H, G, ox, oy, sy, rx, ry); ox += sx; rx = (rx + 1) & (kWin - 1); } while (--dx > 0);
+      do { slide_x(w, snk, G, ox, oy, sy, rx, ry); ox += sx; rx = (rx + 1) & (kWin - 1); } while (--dx > 0);
 #pragma unroll
       for (int p = 0; p < kWin; ++p) ofx[p] = fsx * (float)((p - rx) & (kWin - 1));
     }
     if (dy > 0) {
-      do { slide_y(w, H, G, ox, oy, sx, rx, ry); oy += sy; ry = (ry + 1) & (kWin - 1); } while (--dy > 0);
+      do { slide_y(w, snk, G, ox, oy, sx, rx, ry); oy += sy; ry = (ry + 1) & (kWin - 1); } while (--dy > 0);
 #pragma unroll
       for (int p = 0; p < kWin; ++p) ofy[p] = fsy * (float)((p - ry) & (kWin - 1));
     }
@@ -519,7 +534,7 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
     cur = nxt;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
-  flush_all(w, H, G, ox, oy, sx, sy, rx, ry);
+  flush_all(w, snk, G, ox, oy, sx, sy, rx, ry);
 }
 
 template <bool HALF, bool MOM>

@@ -20,8 +20,9 @@
 // must match a float64 evaluation); the host reads the plan back once.
 //
 // Moment images are complex; each is formed as two real-output transforms
-// of the Hermitian half-plane grid: the real part from T_k c, the imaginary
-// part from -i T_k c (Re of the transform of -i G is Im of that of G).
+// of Hermitian half-plane grids: the real part from T_k c, the imaginary
+// part from -i T_k c (Re of the transform of -i G is Im of that of G).  One
+// gridding pass fills both grids (see the gridder's Sink).
 #include <math.h>
 #include <string.h>
 
@@ -357,23 +358,26 @@ cudaError_t mode3_moments(toi_plan_s* p, Slot& s, const void* vis, const float* 
                                   cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);   // centres is a host local
   const size_t NN = (size_t)p->N * p->N;
+  Slot s_im = s;          // the same snapshot record with the second grid
+  s_im.grid = p->grid2;
   for (int q = 0; q < m.n_slab && e == cudaSuccess; ++q)
-    for (int k = 0; k < m.K && e == cudaSuccess; ++k)
-      for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
-        MomentPass mp;
-        mp.zero_width = m.dr3 > 0.0 ? 0 : 1;
-        mp.r3min = (float)m.r3min;
-        mp.inv2dr3 = m.dr3 > 0.0 ? (float)(1.0 / (2.0 * m.dr3)) : 0.f;
-        mp.centre = centres[q];
-        mp.inv_dr3 = m.dr3 > 0.0 ? (float)(1.0 / m.dr3) : 0.f;
-        mp.slab = q;
-        mp.nslab = m.n_slab;
-        mp.order = k;
-        mp.imag = part;
-        e = launch_grid_moment(p, s, vis, chan_scale, weight, flag, nbl, nch, mp);
-        if (e == cudaSuccess)
-          e = launch_fft_to(p, s, p->moments + ((size_t)(q * m.K + k) * 2 + part) * NN);
-      }
+    for (int k = 0; k < m.K && e == cudaSuccess; ++k) {
+      MomentPass mp;
+      mp.zero_width = m.dr3 > 0.0 ? 0 : 1;
+      mp.r3min = (float)m.r3min;
+      mp.inv2dr3 = m.dr3 > 0.0 ? (float)(1.0 / (2.0 * m.dr3)) : 0.f;
+      mp.centre = centres[q];
+      mp.inv_dr3 = m.dr3 > 0.0 ? (float)(1.0 / m.dr3) : 0.f;
+      mp.slab = q;
+      mp.nslab = m.n_slab;
+      mp.order = k;
+      mp.imag = 0;
+      mp.grid2 = p->grid2;       // one pass grids both parts
+      float* re_img = p->moments + ((size_t)(q * m.K + k) * 2) * NN;
+      e = launch_grid_moment(p, s, vis, chan_scale, weight, flag, nbl, nch, mp);
+      if (e == cudaSuccess) e = launch_fft_to(p, s, re_img);
+      if (e == cudaSuccess) e = launch_fft_to(p, s_im, re_img + NN);
+    }
   return e;
 }
 

@@ -40,6 +40,8 @@ struct MomentPass {
   float centre = 0.f, inv_dr3 = 0.f;  // s = (r3 - centre) * inv_dr3
   int slab = 0, nslab = 1, order = 0, imag = 0;
   int zero_width = 1;                 // r3 range of zero width: s = 0 for every sample
+  float2* grid2 = nullptr;            // also flush -i (upper) / +i (mirror) times the
+                                      // window here: the imaginary-part moment
 };
 
 // Host copy of a snapshot's near-coplanar plan (Section 3.4, Eqs. 26-27).
@@ -156,6 +158,7 @@ struct toi_plan_s {
   double* m3_dev = nullptr;              // selection scratch (keys, errors, plan)
   double* m3_host = nullptr;             // pinned copy of the selection results
   float* m3_slabs = nullptr;             // [max_moments] slab centres (float)
+  float2* grid2 = nullptr;               // [G/2][G] second grid (imaginary-part moments)
   long long nimg = 0;                    // images in the ring since reset
   const float* last_image = nullptr;     // output pointer of the last toi_image
   bool fused_pending = false;
