@@ -58,6 +58,14 @@ def alg_bytes(nbl=N_BL, nch=N_CH, npol=N_POL, N=N_IMG, T=32):
 
 ALG_BYTES = alg_bytes()
 
+# DRAM bytes (read + write) per snapshot of the gridder, from ncu captures of
+# the profile case (dram__bytes_read.sum + dram__bytes_write.sum): the
+# batched kernel over 8 references to one MeerKAT-shaped snapshot (2554 MB /
+# 8; each reference streams its visibilities again, L2 being smaller than
+# them), and the single-snapshot kernel (319.8 + 4.2 MB).  A launch's traffic
+# is this times the snapshots it grids.
+GRID_DRAM_BYTES_PER_SNAPSHOT = {"batch": 319.3e6, "single": 324.1e6}
+
 
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -241,10 +249,12 @@ def run_ours(args):
     achieved = ALG_BYTES[dom] * imaged / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
     total_alg = sum(ALG_BYTES[k] for k in ("prep", "grid", "fft_rows", "fft_cols", "reproject",
                                            "tlisi")) * imaged
+    per_launch = args.batch if args.engine == "batch" else 1
+    traffic = (GRID_DRAM_BYTES_PER_SNAPSHOT[args.engine] * per_launch
+               if dom == "grid" and args.mode == 2 else None)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "alg_bytes_per_launch": ALG_BYTES[dom] * (
-                    args.batch if args.engine == "batch" else 1),
+                "traffic": traffic, "alg_bytes_per_launch": ALG_BYTES[dom] * per_launch,
                 "share": round(dom_ms / sum(v[0] for v in prof.values()), 3),
                 "path_alg_gbs": round(total_alg / (ms / 1e3) / 1e9, 1)}
     stages = {k: {"ms_per_launch": round(v[0] / max(v[1], 1), 4), "launches": v[1]}
