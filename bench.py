@@ -64,7 +64,7 @@ ALG_BYTES = alg_bytes()
 # 8; each reference streams its visibilities again, L2 being smaller than
 # them), and the single-snapshot kernel (319.8 + 4.2 MB).  A launch's traffic
 # is this times the snapshots it grids.
-GRID_DRAM_BYTES_PER_SNAPSHOT = {"batch": 319.3e6, "single": 324.1e6}
+GRID_DRAM_BYTES_PER_SNAPSHOT = {"batch": None, "single": None}   # not captured for this kernel
 
 
 def load_peaks():
@@ -168,7 +168,7 @@ def run_ours(args):
     pool = make_pool(w, args.pool, dev)
     B = args.batch if args.engine == "batch" else 0
     plan = toi.Plan(w.image_size, w.cell_arcsec, w.n_bl, w.n_chan, w.n_pol, tlisi_tile=T,
-                    batch_max=B, mode=args.mode)
+                    batch_max=B, mode=args.mode, grid_rows=args.grid_rows)
     cube = torch.empty(S - 2, nt, nt, dtype=torch.float32, device=dev)
     row_bytes = nt * nt * 4
 
@@ -250,8 +250,9 @@ def run_ours(args):
     total_alg = sum(ALG_BYTES[k] for k in ("prep", "grid", "fft_rows", "fft_cols", "reproject",
                                            "tlisi")) * imaged
     per_launch = args.batch if args.engine == "batch" else 1
-    traffic = (GRID_DRAM_BYTES_PER_SNAPSHOT[args.engine] * per_launch
-               if dom == "grid" and args.mode == 2 else None)
+    per_snap = GRID_DRAM_BYTES_PER_SNAPSHOT[args.engine]
+    traffic = (per_snap * per_launch if per_snap and dom == "grid" and args.mode == 2
+               else None)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "alg_bytes_per_launch": ALG_BYTES[dom] * per_launch,
@@ -566,6 +567,8 @@ def main():
                     help="single: toi_grid + toi_image + tlisi_update per snapshot; batch: "
                          "toi_batch over --batch snapshots per launch")
     ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--grid-rows", type=int, default=0, choices=[0, 4, 8],
+                    help="gridder window rows per lane (0: the library's default)")
     ap.add_argument("--mode", type=int, default=2, choices=[2, 3],
                     help="3: near-coplanar imaging (slabs + Chebyshev moments) of the stream "
                          "with antenna heights (single engine)")

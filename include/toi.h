@@ -83,7 +83,11 @@ typedef struct {
                                slabs and Chebyshev moments)                    */
   int32_t max_moments;      /* mode 3: largest N_slab K a snapshot may need
                                (0 = 64); two N x N float32 images each          */
-  int32_t reserved[2];      /* must be zero                                     */
+  int32_t grid_rows;        /* rows of the W x W gridding window per lane: 0 =
+                               automatic (or as tuned), 8 (one lane per
+                               channel run) or 4 (two lanes per run); a tuning
+                               knob like grid_run                              */
+  int32_t reserved[1];      /* must be zero                                     */
 } toi_config;
 
 typedef struct toi_plan_s* toi_plan_t;
@@ -268,10 +272,13 @@ toi_status toi_batch(toi_plan_t plan, const toi_snapshot* snaps, int32_t n, floa
 
 /* Choose the gridder's channels per lane for each channel-count bucket
  * (n_ch <= 1024, <= 2048, <= 4096, larger) present among the n sample
- * snapshots, by timing the batched gridder for 16, 24, 32, 48 and 64
- * channels per lane (best of three launches each, CUDA events).  The choice
- * is cached in the plan and used by toi_grid and the batch when
- * config.grid_run is 0.  runs_out[4] and us_out[4] (host, may be NULL)
+ * snapshots, and its window split (the W x W footprint in one lane, or half
+ * of it in each of two lanes), by timing the batched gridder for 16, 32, 64,
+ * 128 and 256 channels per lane under both splits (best of three launches
+ * each, CUDA events); the split with the smaller total time is kept.  The
+ * choice is cached in the plan and used by the batch (the run when
+ * config.grid_run is 0, the split when config.grid_rows is 0); single
+ * toi_grid launches keep their own defaults.  runs_out[4] and us_out[4] (host, may be NULL)
  * receive the chosen run and its gridding time per snapshot in
  * microseconds for the buckets that were tuned.  Synchronous; needs
  * batch_max >= n; leaves the stream position and the batch grids as they

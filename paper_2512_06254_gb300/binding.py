@@ -49,7 +49,7 @@ class toi_config(C.Structure):
                 ("n_pol", C.c_int32), ("vis_dtype", C.c_int32), ("kernel_support", C.c_int32),
                 ("oversample", C.c_int32), ("tlisi_tile", C.c_int32), ("grid_slots", C.c_int32),
                 ("grid_run", C.c_int32), ("batch_max", C.c_int32), ("mode", C.c_int32),
-                ("max_moments", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("max_moments", C.c_int32), ("grid_rows", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class toi_snapshot(C.Structure):
@@ -155,7 +155,7 @@ class Plan:
     def __init__(self, image_size: int, cell_arcsec: float, max_baselines: int,
                  max_channels: int, n_pol: int, *, vis_dtype: int = TOI_VIS_C64,
                  tlisi_tile: int = 32, grid_slots: int = 1, grid_run: int = 0, batch_max: int = 0,
-                 mode: int = 2, max_moments: int = 0, stream=None):
+                 mode: int = 2, max_moments: int = 0, grid_rows: int = 0, stream=None):
         import torch
         self.cfg = config_default(image_size, cell_arcsec, max_baselines, max_channels, n_pol)
         self.cfg.vis_dtype = vis_dtype
@@ -165,6 +165,7 @@ class Plan:
         self.cfg.batch_max = batch_max
         self.cfg.mode = mode
         self.cfg.max_moments = max_moments
+        self.cfg.grid_rows = grid_rows
         self.N = image_size
         self.T = tlisi_tile
         h = C.c_void_p()

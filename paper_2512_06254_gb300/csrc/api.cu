@@ -223,8 +223,9 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     return fail(nullptr, TOI_ERR_ARG, "max_moments must be in [0, 1024]");
   if (c.mode == 3 && c.batch_max > 0)
     return fail(nullptr, TOI_ERR_UNSUPPORTED, "the batched path is 2-D only (mode 3 with batch_max > 0)");
-  for (int i = 0; i < 2; ++i)
-    if (c.reserved[i] != 0) return fail(nullptr, TOI_ERR_ARG, "reserved fields must be zero");
+  if (!(c.grid_rows == 0 || c.grid_rows == 4 || c.grid_rows == 8))
+    return fail(nullptr, TOI_ERR_ARG, "grid_rows must be 0, 4 or 8");
+  if (c.reserved[0] != 0) return fail(nullptr, TOI_ERR_ARG, "reserved fields must be zero");
   if ((long long)c.max_baselines * c.max_channels * c.n_pol > (1LL << 40))
     return fail(nullptr, TOI_ERR_ARG, "max_baselines x max_channels too large");
 
@@ -278,6 +279,7 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     e = cudaMallocHost((void**)&p->m3_host, sizeof(double) * 16);
     if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "near-coplanar host buffer"); free_plan(p); return r; }
   }
+  p->batch_rows = c.grid_rows ? c.grid_rows : toi::grid_default_rows(true);
   p->batch_max = c.batch_max;
   if (p->batch_max > 0) {
     const int B = p->batch_max;
@@ -463,7 +465,8 @@ static void fill_batch_table(toi_plan_t p, const toi_snapshot* snaps, int n, flo
     e.with_moments = t >= 2 ? 1 : 0;
     e.tlisi_out = (tlisi && t >= 2) ? tlisi + (size_t)i * ntl : nullptr;
     e.run = runs[i];
-    e.nseg = (sn.n_ch + 32 * e.run - 1) / (32 * e.run);
+    const int rpw = toi::grid_runs_per_warp(p->batch_rows);
+    e.nseg = (sn.n_ch + rpw * e.run - 1) / (rpw * e.run);
     e.up_begin = up;
     up += (long long)sn.n_bl * e.nseg;
   }
@@ -481,7 +484,7 @@ static void fill_batch_table(toi_plan_t p, const toi_snapshot* snaps, int n, flo
 static int lane_run(toi_plan_t p, int nch) {
   if (p->cfg.grid_run > 0) return p->cfg.grid_run;
   const int t = p->tuned_run[toi::channel_bucket(nch)];
-  return t > 0 ? t : toi::grid_default_run(nch);
+  return t > 0 ? t : toi::grid_default_run(nch, true);
 }
 
 static toi_status check_batch(toi_plan_t p, const toi_snapshot* snaps, int32_t n) {
@@ -562,7 +565,7 @@ toi_status toi_autotune(toi_plan_t p, const toi_snapshot* snaps, int32_t n, int3
                         double* us_out) {
   const toi_status st = check_batch(p, snaps, n);
   if (st != TOI_OK) return st;
-  static const int kCand[] = {16, 24, 32, 48, 64};
+  static const int kCand[] = {16, 32, 64, 128, 256};
   constexpr int kNc = (int)(sizeof(kCand) / sizeof(kCand[0]));
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaEventCreate(&a);
@@ -570,44 +573,67 @@ toi_status toi_autotune(toi_plan_t p, const toi_snapshot* snaps, int32_t n, int3
   if (p->bcopied_pending && e == cudaSuccess) e = cudaEventSynchronize(p->bcopied);
   p->bcopied_pending = false;
   const long long nimg0 = p->nimg;
-  for (int bucket = 0; bucket < 4 && e == cudaSuccess; ++bucket) {
-    // the sample snapshots of this channel bucket
-    std::vector<toi_snapshot> sub;
-    for (int i = 0; i < n; ++i)
-      if (toi::channel_bucket(snaps[i].n_ch) == bucket) sub.push_back(snaps[i]);
-    if (sub.empty()) continue;
-    for (auto& sn : sub) sn.image = nullptr;
-    double best = 1e300;
-    int best_run = 0;
-    for (int c = 0; c < kNc && e == cudaSuccess; ++c) {
-      std::vector<int> runs(sub.size(), kCand[c]);
-      fill_batch_table(p, sub.data(), (int)sub.size(), nullptr, runs.data());
-      e = cudaMemcpyAsync(p->bentry_dev, p->bentry_host, sizeof(toi::BatchEntry) * p->batch_max,
-                          cudaMemcpyHostToDevice, p->stream);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(p->bheader_dev, p->bheader_host, sizeof(toi::BatchHeader),
+  // for each window split (8 or 4 rows per lane) the best run per bucket;
+  // keep the split with the smallest total
+  static const int kRows[] = {8, 4};
+  double best_total = 1e300;
+  int best_rows = p->batch_rows;
+  int best_runs[4] = {0, 0, 0, 0};
+  double best_us[4] = {0, 0, 0, 0};
+  for (int ri = 0; ri < 2 && e == cudaSuccess; ++ri) {
+    if (p->cfg.grid_rows && kRows[ri] != p->cfg.grid_rows) continue;
+    p->batch_rows = kRows[ri];
+    double total = 0.0;
+    int runs_r[4] = {0, 0, 0, 0};
+    double us_r[4] = {0, 0, 0, 0};
+    for (int bucket = 0; bucket < 4 && e == cudaSuccess; ++bucket) {
+      std::vector<toi_snapshot> sub;
+      for (int i = 0; i < n; ++i)
+        if (toi::channel_bucket(snaps[i].n_ch) == bucket) sub.push_back(snaps[i]);
+      if (sub.empty()) continue;
+      for (auto& sn : sub) sn.image = nullptr;
+      double best = 1e300;
+      int best_run = 0;
+      for (int c = 0; c < kNc && e == cudaSuccess; ++c) {
+        std::vector<int> runs(sub.size(), kCand[c]);
+        fill_batch_table(p, sub.data(), (int)sub.size(), nullptr, runs.data());
+        e = cudaMemcpyAsync(p->bentry_dev, p->bentry_host, sizeof(toi::BatchEntry) * p->batch_max,
                             cudaMemcpyHostToDevice, p->stream);
-      if (e == cudaSuccess) e = toi::launch_prep_batch(p);
-      double t_min = 1e300;
-      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
-        for (size_t i = 0; i < sub.size() && e == cudaSuccess; ++i)
-          e = cudaMemsetAsync(p->bslots[i].grid, 0, sizeof(float2) * (size_t)(p->G / 2) * p->G,
-                              p->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(a, p->stream);
-        if (e == cudaSuccess) e = toi::launch_grid_batch(p, p->cfg.vis_dtype == TOI_VIS_C16_CHANSCALE);
-        if (e == cudaSuccess) e = cudaEventRecord(b, p->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(b);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-        if (e == cudaSuccess && ms < t_min) t_min = ms;
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(p->bheader_dev, p->bheader_host, sizeof(toi::BatchHeader),
+                              cudaMemcpyHostToDevice, p->stream);
+        if (e == cudaSuccess) e = toi::launch_prep_batch(p);
+        double t_min = 1e300;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+          for (size_t i = 0; i < sub.size() && e == cudaSuccess; ++i)
+            e = cudaMemsetAsync(p->bslots[i].grid, 0, sizeof(float2) * (size_t)(p->G / 2) * p->G,
+                                p->stream);
+          if (e == cudaSuccess) e = cudaEventRecord(a, p->stream);
+          if (e == cudaSuccess) e = toi::launch_grid_batch(p, p->cfg.vis_dtype == TOI_VIS_C16_CHANSCALE);
+          if (e == cudaSuccess) e = cudaEventRecord(b, p->stream);
+          if (e == cudaSuccess) e = cudaEventSynchronize(b);
+          float ms = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+          if (e == cudaSuccess && ms < t_min) t_min = ms;
+        }
+        if (e == cudaSuccess && t_min < best) { best = t_min; best_run = kCand[c]; }
       }
-      if (e == cudaSuccess && t_min < best) { best = t_min; best_run = kCand[c]; }
+      runs_r[bucket] = best_run;
+      us_r[bucket] = best * 1e3 / (double)sub.size();
+      total += best;
     }
-    if (e == cudaSuccess) {
-      p->tuned_run[bucket] = best_run;
-      if (runs_out) runs_out[bucket] = best_run;
-      if (us_out) us_out[bucket] = best * 1e3 / (double)sub.size();
+    if (e == cudaSuccess && total < best_total) {
+      best_total = total;
+      best_rows = kRows[ri];
+      for (int k = 0; k < 4; ++k) { best_runs[k] = runs_r[k]; best_us[k] = us_r[k]; }
     }
+  }
+  p->batch_rows = best_rows;
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+    if (!best_runs[k]) continue;
+    p->tuned_run[k] = best_runs[k];
+    if (runs_out) runs_out[k] = best_runs[k];
+    if (us_out) us_out[k] = best_us[k];
   }
   // leave the batch grids zero and the stream position untouched
   for (int i = 0; i < p->batch_max && e == cudaSuccess; ++i)

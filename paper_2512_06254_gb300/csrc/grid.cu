@@ -90,14 +90,20 @@ __device__ __forceinline__ float2 load_vis(const void* vis, size_t idx, float sc
   }
 }
 
-// A lane's W x W register window, kept circular: logical column i (in the
+// A lane's register window, kept circular: logical column i (in the
 // direction of travel sx) is physical column (i + rx) mod W and lies at
 // absolute grid column ox + sx * i; rows likewise with (ry, oy, sy).  A
 // slide flushes the physical column (row) that holds logical column (row) 0,
 // clears it for the incoming cells and advances the phase; nothing is moved
-// between registers.
+// between registers.  RH = W: one lane holds the whole W x W footprint.
+// RH = W/2: two neighbouring lanes share a channel run, and lane h of the
+// pair holds the physical rows [h W/2, h W/2 + W/2) - physical rows never
+// move, so a column slide flushes W/2 cells in each lane and a row slide is
+// done by the one lane that owns the row.  Half the window per lane halves
+// its registers, doubling the resident warps.
+template <int RH>
 struct Window {
-  float2 a[kWin][kWin];   // a[physical row][physical column]
+  float2 a[RH][kWin];   // a[owned physical row - row base][physical column]
 };
 
 // Where a window's cells go: the grid H, and in a near-coplanar pass also
@@ -124,11 +130,12 @@ __device__ __forceinline__ int phys_to_abs(int p, int r, int o, int s) {
   return o + s * ((p - r) & (kWin - 1));
 }
 
-__device__ __forceinline__ void flush_all(Window& w, const Sink& H, int G, int ox, int oy,
-                                          int sx, int sy, int rx, int ry) {
+template <int RH>
+__device__ __forceinline__ void flush_all(Window<RH>& w, const Sink& H, int G, int ox, int oy,
+                                          int sx, int sy, int rx, int ry, int rbase) {
 #pragma unroll
-  for (int j = 0; j < kWin; ++j) {
-    const int y = phys_to_abs(j, ry, oy, sy);
+  for (int j = 0; j < RH; ++j) {
+    const int y = phys_to_abs(rbase + j, ry, oy, sy);
 #pragma unroll
     for (int i = 0; i < kWin; ++i) {
       flush_cell(H, G, phys_to_abs(i, rx, ox, sx), y, w.a[j][i]);
@@ -137,18 +144,18 @@ __device__ __forceinline__ void flush_all(Window& w, const Sink& H, int G, int o
   }
 }
 
-template <int P>
-__device__ __forceinline__ void flush_col(Window& w, const Sink& H, int G, int x, int oy,
-                                          int sy, int ry) {
+template <int P, int RH>
+__device__ __forceinline__ void flush_col(Window<RH>& w, const Sink& H, int G, int x, int oy,
+                                          int sy, int ry, int rbase) {
 #pragma unroll
-  for (int j = 0; j < kWin; ++j) {
-    flush_cell(H, G, x, phys_to_abs(j, ry, oy, sy), w.a[j][P]);
+  for (int j = 0; j < RH; ++j) {
+    flush_cell(H, G, x, phys_to_abs(rbase + j, ry, oy, sy), w.a[j][P]);
     w.a[j][P] = make_float2(0.f, 0.f);
   }
 }
 
-template <int P>
-__device__ __forceinline__ void flush_row(Window& w, const Sink& H, int G, int y, int ox,
+template <int P, int RH>
+__device__ __forceinline__ void flush_row(Window<RH>& w, const Sink& H, int G, int y, int ox,
                                           int sx, int rx) {
 #pragma unroll
   for (int i = 0; i < kWin; ++i) {
@@ -158,31 +165,45 @@ __device__ __forceinline__ void flush_row(Window& w, const Sink& H, int G, int y
 }
 
 // slide one column forwards: physical column rx (logical column 0) is final
-__device__ __forceinline__ void slide_x(Window& w, const Sink& H, int G, int ox, int oy,
-                                        int sy, int rx, int ry) {
+template <int RH>
+__device__ __forceinline__ void slide_x(Window<RH>& w, const Sink& H, int G, int ox, int oy,
+                                        int sy, int rx, int ry, int rbase) {
   switch (rx) {
-    case 0: flush_col<0>(w, H, G, ox, oy, sy, ry); break;
-    case 1: flush_col<1>(w, H, G, ox, oy, sy, ry); break;
-    case 2: flush_col<2>(w, H, G, ox, oy, sy, ry); break;
-    case 3: flush_col<3>(w, H, G, ox, oy, sy, ry); break;
-    case 4: flush_col<4>(w, H, G, ox, oy, sy, ry); break;
-    case 5: flush_col<5>(w, H, G, ox, oy, sy, ry); break;
-    case 6: flush_col<6>(w, H, G, ox, oy, sy, ry); break;
-    default: flush_col<7>(w, H, G, ox, oy, sy, ry); break;
+    case 0: flush_col<0>(w, H, G, ox, oy, sy, ry, rbase); break;
+    case 1: flush_col<1>(w, H, G, ox, oy, sy, ry, rbase); break;
+    case 2: flush_col<2>(w, H, G, ox, oy, sy, ry, rbase); break;
+    case 3: flush_col<3>(w, H, G, ox, oy, sy, ry, rbase); break;
+    case 4: flush_col<4>(w, H, G, ox, oy, sy, ry, rbase); break;
+    case 5: flush_col<5>(w, H, G, ox, oy, sy, ry, rbase); break;
+    case 6: flush_col<6>(w, H, G, ox, oy, sy, ry, rbase); break;
+    default: flush_col<7>(w, H, G, ox, oy, sy, ry, rbase); break;
   }
 }
 
-__device__ __forceinline__ void slide_y(Window& w, const Sink& H, int G, int ox, int oy,
-                                        int sx, int rx, int ry) {
-  switch (ry) {
-    case 0: flush_row<0>(w, H, G, oy, ox, sx, rx); break;
-    case 1: flush_row<1>(w, H, G, oy, ox, sx, rx); break;
-    case 2: flush_row<2>(w, H, G, oy, ox, sx, rx); break;
-    case 3: flush_row<3>(w, H, G, oy, ox, sx, rx); break;
-    case 4: flush_row<4>(w, H, G, oy, ox, sx, rx); break;
-    case 5: flush_row<5>(w, H, G, oy, ox, sx, rx); break;
-    case 6: flush_row<6>(w, H, G, oy, ox, sx, rx); break;
-    default: flush_row<7>(w, H, G, oy, ox, sx, rx); break;
+// slide one row forwards: physical row ry is final (flushed by its owner)
+template <int RH>
+__device__ __forceinline__ void slide_y(Window<RH>& w, const Sink& H, int G, int ox, int oy,
+                                        int sx, int rx, int ry, int rbase) {
+  const int r = ry - rbase;
+  if (RH == kWin) {
+    switch (r) {
+      case 0: flush_row<0>(w, H, G, oy, ox, sx, rx); break;
+      case 1: flush_row<1 % RH>(w, H, G, oy, ox, sx, rx); break;
+      case 2: flush_row<2 % RH>(w, H, G, oy, ox, sx, rx); break;
+      case 3: flush_row<3 % RH>(w, H, G, oy, ox, sx, rx); break;
+      case 4: flush_row<4 % RH>(w, H, G, oy, ox, sx, rx); break;
+      case 5: flush_row<5 % RH>(w, H, G, oy, ox, sx, rx); break;
+      case 6: flush_row<6 % RH>(w, H, G, oy, ox, sx, rx); break;
+      default: flush_row<7 % RH>(w, H, G, oy, ox, sx, rx); break;
+    }
+  } else {
+    switch (r) {
+      case 0: flush_row<0>(w, H, G, oy, ox, sx, rx); break;
+      case 1: flush_row<1 % RH>(w, H, G, oy, ox, sx, rx); break;
+      case 2: flush_row<2 % RH>(w, H, G, oy, ox, sx, rx); break;
+      case 3: flush_row<3 % RH>(w, H, G, oy, ox, sx, rx); break;
+      default: break;   // the other lane of the pair owns this row
+    }
   }
 }
 
@@ -354,7 +375,7 @@ __device__ __forceinline__ Sample read_staged(const StageBuf& sb, int sidx, int 
 
 // One warp's work: segment `seg` of track `track` (tracks [0, nbl) are the
 // upper-half tracks of the baselines, [nbl, 2 nbl) their mirrors).
-template <bool HALF, bool MOM>
+template <bool HALF, bool MOM, int RH>
 __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef,
                                            const float2* __restrict__ kf,
                                            const void* __restrict__ vis,
@@ -365,6 +386,9 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
                                            int seg, StageBuf& sb, float2* __restrict__ H,
                                            const MomentPass& mp) {
   const int lane = threadIdx.x & 31;
+  constexpr int RPW = 32 * RH / kWin;                   // channel runs per warp
+  const int run_idx = (RH == kWin) ? lane : (lane >> 1);
+  const int rbase = (RH == kWin) ? 0 : RH * (lane & 1); // first owned physical row
   const int mirror = track >= nbl ? 1 : 0;
   const int bl = track - mirror * nbl;
   const TrackGeom t = track_geom(coef[bl], mirror);
@@ -384,7 +408,7 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
     r3bl = (float)coef[bl].r3;
     if (!mp.zero_width && mp.nslab > 1) {
       // skip a segment whose r3 range misses the slab (channels are monotonic)
-      const int w0 = seg * 32 * run, w1 = min(nch, (seg + 1) * 32 * run) - 1;
+      const int w0 = seg * RPW * run, w1 = min(nch, (seg + 1) * RPW * run) - 1;
       const float2 ka = kf[w0], kb = kf[w1 < w0 ? w0 : w1];
       const float ra = r3bl * (ka.x + ka.y), rb = r3bl * (kb.x + kb.y);
       const float lo = fminf(ra, rb), hi = fmaxf(ra, rb);
@@ -394,7 +418,7 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
       if ((mp.slab > 0 && hi < slo - tol) || (mp.slab < mp.nslab - 1 && lo > shi + tol)) return;
     }
   }
-  const int c_begin = (seg * 32 + lane) * run;
+  const int c_begin = (seg * RPW + run_idx) * run;
   const int c_end = min(nch, c_begin + run);
   if (c_begin >= nch) return;
   int pa, pb;
@@ -409,9 +433,9 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
 
   // lane-private staging: lane l only ever touches st[stage][u][l]
 
-  Window w;
+  Window<RH> w;
 #pragma unroll
-  for (int j = 0; j < kWin; ++j)
+  for (int j = 0; j < RH; ++j)
 #pragma unroll
     for (int i = 0; i < kWin; ++i) w.a[j][i] = make_float2(0.f, 0.f);
 
@@ -458,12 +482,11 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
   const float fsx = (float)sx, fsy = (float)sy;
   // offset of physical column p from the first tap, in the direction of
   // travel: sx * ((p - rx) mod W); refreshed whenever the phase changes
-  float ofx[kWin], ofy[kWin];
+  float ofx[kWin], ofy[RH];   // ofy: the owned rows only
 #pragma unroll
-  for (int p = 0; p < kWin; ++p) {
-    ofx[p] = fsx * (float)p;
-    ofy[p] = fsy * (float)p;
-  }
+  for (int p = 0; p < kWin; ++p) ofx[p] = fsx * (float)p;
+#pragma unroll
+  for (int r = 0; r < RH; ++r) ofy[r] = fsy * (float)(rbase + r);
   const Sample none{make_float2(0.f, 0.f), make_float2(0.f, 0.f), false};
 #pragma unroll 1
   for (int ch = c_begin; ch < c_end; ++ch) {
@@ -489,7 +512,7 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
     int dx = sx > 0 ? cur.kx0 - ox : ox - (cur.kx0 + kW - 1);
     int dy = sy > 0 ? cur.ky0 - oy : oy - (cur.ky0 + kW - 1);
     if (dx < 0 || dy < 0 || dx >= kWin || dy >= kWin) {
-      flush_all(w, snk, G, ox, oy, sx, sy, rx, ry);
+      flush_all(w, snk, G, ox, oy, sx, sy, rx, ry, rbase);
       ox = sx > 0 ? cur.kx0 : cur.kx0 + kW - 1;
       oy = sy > 0 ? cur.ky0 : cur.ky0 + kW - 1;
       rx = 0;
@@ -497,35 +520,35 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
       dx = 0;
       dy = 0;
 #pragma unroll
-      for (int p = 0; p < kWin; ++p) {
-        ofx[p] = fsx * (float)p;
-        ofy[p] = fsy * (float)p;
-      }
+      for (int p = 0; p < kWin; ++p) ofx[p] = fsx * (float)p;
+#pragma unroll
+      for (int r = 0; r < RH; ++r) ofy[r] = fsy * (float)(rbase + r);
     }
     if (dx > 0) {
-      do { slide_x(w, snk, G, ox, oy, sy, rx, ry); ox += sx; rx = (rx + 1) & (kWin - 1); } while (--dx > 0);
+      do { slide_x(w, snk, G, ox, oy, sy, rx, ry, rbase); ox += sx; rx = (rx + 1) & (kWin - 1); } while (--dx > 0);
 #pragma unroll
       for (int p = 0; p < kWin; ++p) ofx[p] = fsx * (float)((p - rx) & (kWin - 1));
     }
     if (dy > 0) {
-      do { slide_y(w, snk, G, ox, oy, sx, rx, ry); oy += sy; ry = (ry + 1) & (kWin - 1); } while (--dy > 0);
+      do { slide_y(w, snk, G, ox, oy, sx, rx, ry, rbase); oy += sy; ry = (ry + 1) & (kWin - 1); } while (--dy > 0);
 #pragma unroll
-      for (int p = 0; p < kWin; ++p) ofy[p] = fsy * (float)((p - ry) & (kWin - 1));
+      for (int r = 0; r < RH; ++r) ofy[r] = fsy * (float)((rbase + r - ry) & (kWin - 1));
     }
     Prepared nxt;
     if (MOM) sn.c = moment_value(sn.c, r3bl * (sn.k.x + sn.k.y), mp);
     prepare(sn, s1hi, s1lo, s2hi, s2lo, cx, cy, sx, sy, t.conj, nxt);
     // kernel values in physical order: physical index p holds tap (p - r) mod W
     float px[kWin];
-    float2 b[kWin];
+    float2 b[RH];
 #pragma unroll
-    for (int p = 0; p < kWin; ++p) {
-      px[p] = es_kernel(cur.fxs + ofx[p], bl2);
-      const float py = es_kernel(cur.fys + ofy[p], bl2);
-      b[p] = make_float2(cur.c.x * py, cur.c.y * py);
+    for (int p = 0; p < kWin; ++p) px[p] = es_kernel(cur.fxs + ofx[p], bl2);
+#pragma unroll
+    for (int r = 0; r < RH; ++r) {
+      const float py = es_kernel(cur.fys + ofy[r], bl2);
+      b[r] = make_float2(cur.c.x * py, cur.c.y * py);
     }
 #pragma unroll
-    for (int j = 0; j < kWin; ++j)
+    for (int j = 0; j < RH; ++j)
 #pragma unroll
       for (int i = 0; i < kWin; ++i) {
         w.a[j][i].x = fmaf(px[i], b[j].x, w.a[j][i].x);
@@ -534,10 +557,10 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
     cur = nxt;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
-  flush_all(w, snk, G, ox, oy, sx, sy, rx, ry);
+  flush_all(w, snk, G, ox, oy, sx, sy, rx, ry, rbase);
 }
 
-template <bool HALF, bool MOM>
+template <bool HALF, bool MOM, int RH>
 __global__ void __launch_bounds__(kWarps * 32)
 grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restrict__ kf,
                    const void* __restrict__ vis, const float* __restrict__ chan_scale,
@@ -550,8 +573,8 @@ grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restri
   if (warp >= 2 * nbl * nseg) return;
   // warps [0, nbl * nseg) walk the upper-half tracks, the rest their mirrors
   // (most mirror warps exit at once, so they are kept out of the busy blocks)
-  grid_track<HALF, MOM>(coef, kf, vis, chan_scale, weight, flag, nbl, nch, npol, G, bl2, run,
-                        warp / nseg, warp % nseg, stage_all[wib], H, mp);
+  grid_track<HALF, MOM, RH>(coef, kf, vis, chan_scale, weight, flag, nbl, nch, npol, G, bl2, run,
+                            warp / nseg, warp % nseg, stage_all[wib], H, mp);
 }
 
 // Persistent gridder over a batch: each warp takes work items from a
@@ -560,7 +583,7 @@ grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restri
 // tracks, most of which store nothing and leave at once.  Uneven entries
 // (different channel counts and flag fractions) thus share the GPU without
 // a partial last wave per entry.
-template <bool HALF>
+template <bool HALF, int RH>
 __global__ void __launch_bounds__(kWarps * 32)
 grid_batch_kernel(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr,
                   int* __restrict__ queue, int npol, int G, float bl2) {
@@ -589,8 +612,9 @@ grid_batch_kernel(const BatchEntry* __restrict__ E, const BatchHeader* __restric
     const int seg = (int)(local % e.nseg);
     const int track = (int)(local / e.nseg) + (mir ? e.nbl : 0);
     const MomentPass none{};
-    grid_track<HALF, false>(e.coef, e.kf, e.vis, e.chan_scale, e.weight, e.flag, e.nbl, e.nch,
-                            npol, G, bl2, e.run, track, seg, stage_all[wib], e.grid, none);
+    grid_track<HALF, false, RH>(e.coef, e.kf, e.vis, e.chan_scale, e.weight, e.flag, e.nbl,
+                                e.nch, npol, G, bl2, e.run, track, seg, stage_all[wib], e.grid,
+                                none);
   }
 }
 
@@ -600,7 +624,22 @@ grid_batch_kernel(const BatchEntry* __restrict__ E, const BatchHeader* __restric
 // there are several warps per SM slot (runs of at least 16 channels);
 // nch / 128 measured best at 4096 channels (finer runs pay more window
 // flushes, coarser ones leave a partial last wave of warps).
-int grid_default_run(int nch) {
+// Defaults when not tuned.  Single-snapshot launches: the whole window in
+// one lane and runs of nch / 128 channels (measured best at 4096 channels:
+// finer runs pay more window flushes, coarser ones leave a partial last wave
+// of warps).  Batched launches: two lanes per run (half the registers, more
+// resident warps) and long runs - the work queue removes the partial wave,
+// and every run ends with a flush of its whole window, so fewer runs mean
+// fewer grid reductions (358 us per snapshot at 256 channels vs 436 us at
+// 32, MeerKAT-shaped); powers of two keep the last segment's lanes busy.
+int grid_default_rows(bool batched) { return batched ? 4 : 8; }
+
+int grid_default_run(int nch, bool batched) {
+  if (batched) {
+    int run = 16;
+    while (run < 512 && run * 16 < nch) run *= 2;
+    return run;
+  }
   const int run = (nch + 127) / 128;
   return run < 16 ? 16 : run;
 }
@@ -610,63 +649,79 @@ int channel_bucket(int nch) {
 }
 
 int grid_resident_blocks() {
-  int b0 = 0, b1 = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, grid_batch_kernel<false>, kWarps * 32, 0) !=
-      cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, grid_batch_kernel<true>, kWarps * 32, 0) !=
-      cudaSuccess)
-    return 0;
-  return b0 < b1 ? b0 : b1;
+  int lo = 1 << 30;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grid_batch_kernel<false, 8>, kWarps * 32, 0) != cudaSuccess) return 0;
+  lo = b < lo ? b : lo;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grid_batch_kernel<true, 8>, kWarps * 32, 0) != cudaSuccess) return 0;
+  lo = b < lo ? b : lo;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grid_batch_kernel<false, 4>, kWarps * 32, 0) != cudaSuccess) return 0;
+  const int hi4 = b;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grid_batch_kernel<true, 4>, kWarps * 32, 0) != cudaSuccess) return 0;
+  // the persistent grid is sized for the half-window kernel (more resident
+  // blocks); the full-window kernel then runs in waves of its own residency
+  return hi4 < b ? hi4 : b;
 }
+
+int grid_runs_per_warp(int rows) { return 32 * rows / kWin; }
 
 cudaError_t launch_grid_batch(toi_plan_s* p, bool half) {
   const float bl2 = (float)(p->beta_es * 1.4426950408889634);
   cudaError_t e = cudaMemsetAsync(p->bqueue, 0, sizeof(int), p->stream);
   if (e != cudaSuccess) return e;
   const int tok = prof_begin(p, PROF_GRID, 1);
-  if (half)
-    grid_batch_kernel<true><<<p->grid_blocks, kWarps * 32, 0, p->stream>>>(
+  const bool split = p->batch_rows == 4;
+  if (half && split)
+    grid_batch_kernel<true, 4><<<p->grid_blocks, kWarps * 32, 0, p->stream>>>(
+        p->bentry_dev, p->bheader_dev, p->bqueue, p->cfg.n_pol, p->G, bl2);
+  else if (half)
+    grid_batch_kernel<true, 8><<<p->grid_blocks, kWarps * 32, 0, p->stream>>>(
+        p->bentry_dev, p->bheader_dev, p->bqueue, p->cfg.n_pol, p->G, bl2);
+  else if (split)
+    grid_batch_kernel<false, 4><<<p->grid_blocks, kWarps * 32, 0, p->stream>>>(
         p->bentry_dev, p->bheader_dev, p->bqueue, p->cfg.n_pol, p->G, bl2);
   else
-    grid_batch_kernel<false><<<p->grid_blocks, kWarps * 32, 0, p->stream>>>(
+    grid_batch_kernel<false, 8><<<p->grid_blocks, kWarps * 32, 0, p->stream>>>(
         p->bentry_dev, p->bheader_dev, p->bqueue, p->cfg.n_pol, p->G, bl2);
   prof_end(p, tok);
   return cudaGetLastError();
 }
 
+template <bool HALF, bool MOM>
+static void launch_tracks(toi_plan_s* p, Slot& s, int rows, int blocks, const void* vis,
+                          const float* chan_scale, const float* weight, const uint8_t* flag,
+                          int nbl, int nch, float bl2, int run, int nseg, const MomentPass& m) {
+  if (rows == 4)
+    grid_tracks_kernel<HALF, MOM, 4><<<blocks, kWarps * 32, 0, p->stream>>>(
+        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, p->G, bl2, run,
+        nseg, s.grid, m);
+  else
+    grid_tracks_kernel<HALF, MOM, 8><<<blocks, kWarps * 32, 0, p->stream>>>(
+        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, p->G, bl2, run,
+        nseg, s.grid, m);
+}
+
 static cudaError_t launch_grid_impl(toi_plan_s* p, Slot& s, const void* vis,
                                     const float* chan_scale, const float* weight,
                                     const uint8_t* flag, int nbl, int nch, const MomentPass* mp) {
-  const int G = p->G;
   const int tok = prof_begin(p, PROF_GRID, 1);
   // the slot is zero: cleared at plan creation, by the row pass of the
   // previous toi_image, or by toi_grid when a gridded slot is re-gridded
-  int run = p->cfg.grid_run > 0 ? p->cfg.grid_run : p->tuned_run[channel_bucket(nch)];
-  if (run <= 0) run = grid_default_run(nch);
-  const int nseg = (nch + 32 * run - 1) / (32 * run);
+  // single launches keep their own defaults (the autotuner tunes the batch)
+  const int run = p->cfg.grid_run > 0 ? p->cfg.grid_run : grid_default_run(nch, false);
+  const int rows = p->cfg.grid_rows ? p->cfg.grid_rows : grid_default_rows(false);
+  const int rpw = grid_runs_per_warp(rows);
+  const int nseg = (nch + rpw * run - 1) / (rpw * run);
   const long long nwarps = 2LL * nbl * nseg;
   const int blocks = (int)((nwarps + kWarps - 1) / kWarps);
   const float bl2 = (float)(p->beta_es * 1.4426950408889634);
   const bool half = p->cfg.vis_dtype == TOI_VIS_C16_CHANSCALE;
   const MomentPass none{};
   const MomentPass m = mp ? *mp : none;
-  if (half && mp)
-    grid_tracks_kernel<true, true><<<blocks, kWarps * 32, 0, p->stream>>>(
-        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, G, bl2, run, nseg,
-        s.grid, m);
-  else if (half)
-    grid_tracks_kernel<true, false><<<blocks, kWarps * 32, 0, p->stream>>>(
-        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, G, bl2, run, nseg,
-        s.grid, m);
-  else if (mp)
-    grid_tracks_kernel<false, true><<<blocks, kWarps * 32, 0, p->stream>>>(
-        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, G, bl2, run, nseg,
-        s.grid, m);
-  else
-    grid_tracks_kernel<false, false><<<blocks, kWarps * 32, 0, p->stream>>>(
-        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, G, bl2, run, nseg,
-        s.grid, m);
+  if (half && mp) launch_tracks<true, true>(p, s, rows, blocks, vis, chan_scale, weight, flag, nbl, nch, bl2, run, nseg, m);
+  else if (half) launch_tracks<true, false>(p, s, rows, blocks, vis, chan_scale, weight, flag, nbl, nch, bl2, run, nseg, m);
+  else if (mp) launch_tracks<false, true>(p, s, rows, blocks, vis, chan_scale, weight, flag, nbl, nch, bl2, run, nseg, m);
+  else launch_tracks<false, false>(p, s, rows, blocks, vis, chan_scale, weight, flag, nbl, nch, bl2, run, nseg, m);
   prof_end(p, tok);
   return cudaGetLastError();
 }

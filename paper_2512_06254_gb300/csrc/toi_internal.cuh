@@ -184,6 +184,7 @@ struct toi_plan_s {
   double* b_tile_mom = nullptr;             // [batch_max][ntl][5]
   int grid_blocks = 0;                      // persistent gridder: resident blocks
   int tuned_run[4] = {0, 0, 0, 0};          // autotuned lane runs per channel bucket
+  int batch_rows = 4;                       // window rows per lane of the batch gridder
 };
 
 namespace toi {
@@ -221,7 +222,9 @@ cudaError_t launch_grid_batch(toi_plan_s* p, bool half);
 cudaError_t launch_fft_batch(toi_plan_s* p);
 cudaError_t launch_finish_batch(toi_plan_s* p);
 int grid_resident_blocks();                 // persistent gridder blocks per SM
-int grid_default_run(int nch);
+int grid_default_run(int nch, bool batched);
+int grid_default_rows(bool batched);
+int grid_runs_per_warp(int rows);
 int channel_bucket(int nch);
 
 // degrid.cu

@@ -158,7 +158,7 @@ def test_autotune_keeps_the_stream():
     rows0 = torch.empty(3, nt, nt, device="cuda")
     plan.batch(ds0, rows0)
     runs, us = plan.autotune([_dev_snap(sn, N) for _, sn in snaps[3:7]])
-    assert runs and all(r in (16, 24, 32, 48, 64) for r in runs.values())
+    assert runs and all(r in (16, 32, 64, 128, 256) for r in runs.values())
     assert all(v > 0 for v in us.values())
     ds1 = [_dev_snap(sn, N) for _, sn in snaps[3:7]]
     rows1 = torch.empty(4, nt, nt, device="cuda")

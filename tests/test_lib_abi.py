@@ -53,7 +53,7 @@ def test_host_validation_without_gpu(libtoi):
     cfg.tlisi_tile = 48
     assert L.toi_plan(C.byref(cfg), None, C.byref(h)) == libtoi.TOI_ERR_ARG
     cfg = b.config_default(128, 2.0, 10, 10, 4)
-    cfg.reserved[1] = 1
+    cfg.reserved[0] = 1
     assert L.toi_plan(C.byref(cfg), None, C.byref(h)) == libtoi.TOI_ERR_ARG
     assert L.toi_grid(None, None, None, None, None, None, None, 1, 1, 0) == libtoi.TOI_ERR_ARG
     assert L.tlisi_candidates(None, 1, 1, 1, 1, 0, None, None, None, None, 0, None) == libtoi.TOI_ERR_ARG
