@@ -58,13 +58,13 @@ def alg_bytes(nbl=N_BL, nch=N_CH, npol=N_POL, N=N_IMG, T=32):
 
 ALG_BYTES = alg_bytes()
 
-# DRAM bytes (read + write) per snapshot of the gridder, from ncu captures of
-# the profile case (dram__bytes_read.sum + dram__bytes_write.sum): the
-# batched kernel over 8 references to one MeerKAT-shaped snapshot (2554 MB /
-# 8; each reference streams its visibilities again, L2 being smaller than
-# them), and the single-snapshot kernel (319.8 + 4.2 MB).  A launch's traffic
-# is this times the snapshots it grids.
-GRID_DRAM_BYTES_PER_SNAPSHOT = {"batch": None, "single": None}   # not captured for this kernel
+# DRAM bytes (read + write) per snapshot of the gridder, from an ncu capture
+# of the profile case (dram__bytes_read.sum + dram__bytes_write.sum): the
+# batched kernel over 16 references to one MeerKAT-shaped snapshot (4987 +
+# 186 MB; each reference streams its visibilities again, L2 being smaller
+# than them).  A launch's traffic is this times the snapshots it grids.  The
+# single-snapshot kernel has not been captured in its current form.
+GRID_DRAM_BYTES_PER_SNAPSHOT = {"batch": 5173.7e6 / 16, "single": None}
 
 
 def load_peaks():
@@ -445,6 +445,74 @@ def run_uneven(args):
         p.close()
 
 
+def run_adjoint(args):
+    """Forward and reverse mode of the MeerKAT-shaped snapshot image: per
+    snapshot toi_grid + toi_image, then toi_degrid_backward for a fixed
+    image cotangent with the visibility and weight gradients."""
+    import torch
+
+    import paper_2512_06254_gb300 as toi
+    from paper_2512_06254_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    S = args.snapshots
+    w = synth.meerkat_workload(n_snap=S)
+    pool = make_pool(w, args.pool, dev)
+    N = w.image_size
+    plan = toi.Plan(N, w.cell_arcsec, w.n_bl, w.n_chan, w.n_pol)
+    g = torch.Generator(device=dev).manual_seed(5)
+    grad_img = torch.randn(N, N, generator=g, device=dev)
+    img = torch.empty(N, N, device=dev)
+    gv = torch.empty(w.n_bl, w.n_chan, w.n_pol, dtype=torch.complex64, device=dev)
+    gw = torch.empty(w.n_bl, w.n_chan, w.n_pol, dtype=torch.float32, device=dev)
+
+    def step():
+        for s in range(S):
+            p = pool[s % len(pool)]
+            plan.grid(p["uvw"], p["freq"], p["vis"], flag=p["flag"])
+            plan.image(0, img)
+            plan.degrid_backward(grad_img, image=img, grad_vis=gv, grad_weight=gw)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if plan.sync_status() != toi.TOI_OK:
+        raise RuntimeError(plan.last_error())
+    plan.profile_read()
+    plan.profile_enable(True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    prof = plan.profile_read()
+    plan.close()
+    n = S * args.steps
+    bw_ms = prof["backward"][0]
+    peak, peak_kind = load_peaks()
+    achieved = ALG_BYTES["backward"] * n / (bw_ms / 1e3) / 1e9
+    print(json.dumps({
+        "metric": "snapshots/s forward image + reverse mode (grad vis and weights) at MeerKAT shape",
+        "value": round(n / (ms / 1e3), 2), "unit": "snapshots/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded MeerKAT-shaped snapshots, resident pool)",
+        "config": {"workload": "meerkat-adjoint-" + str(S) + "snap", "resident_pool": args.pool},
+        "roofline": {"bound": "hbm", "kernel": "backward", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "alg_bytes_per_launch": ALG_BYTES["backward"]},
+        "stages": {k: {"ms_per_snapshot": round(v[0] / n, 4)} for k, v in prof.items() if v[1]},
+        "clocks": ck}))
+
+
 CPU_SNIPPET = r"""
 import json, os, sys, time
 sys.path.insert(0, {root!r})
@@ -574,7 +642,7 @@ def main():
                          "with antenna heights (single engine)")
     ap.add_argument("--copy-streams", type=int, default=4,
                     help="e2e: copy streams each snapshot's host-to-device copy is split over")
-    ap.add_argument("--workload", default="meerkat", choices=["meerkat", "uneven"],
+    ap.add_argument("--workload", default="meerkat", choices=["meerkat", "uneven", "adjoint"],
                     help="meerkat: the headline stream; uneven: the batched uneven stream "
                          "(512 snapshots, 1024-4096 channels, 0-60%% flags, 1024/2048 px)")
     ap.add_argument("--graph", action="store_true",
@@ -592,6 +660,8 @@ def main():
         run_reference(args)
     elif args.workload == "uneven":
         run_uneven(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -253,7 +253,7 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   if ((st = dev_alloc(p, &(ptr), (n), what)) != TOI_OK) { g_last_error = p->err; free_plan(p); return st; }
   for (int i = 0; i < p->nslot; ++i) {
     TOI_ALLOC(p->slots[i].grid, (size_t)(G / 2) * G, "grid slot");
-    TOI_ALLOC(p->slots[i].snap, toi::SNAP_LEN, "snapshot record");
+    TOI_ALLOC(p->slots[i].snap, toi::SNAP_ALLOC, "snapshot record");
     TOI_ALLOC(p->slots[i].coef, (size_t)c.max_baselines, "baseline coefficients");
   }
   TOI_ALLOC(p->kch, (size_t)c.max_channels, "channel table");
@@ -287,7 +287,7 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     if (!p->bslots) { free_plan(p); return fail(nullptr, TOI_ERR_OOM, "host allocation failed"); }
     for (int i = 0; i < B; ++i) {
       TOI_ALLOC(p->bslots[i].grid, (size_t)(G / 2) * G, "batch grid");
-      TOI_ALLOC(p->bslots[i].snap, toi::SNAP_LEN, "batch snapshot record");
+      TOI_ALLOC(p->bslots[i].snap, toi::SNAP_ALLOC, "batch snapshot record");
       TOI_ALLOC(p->bslots[i].coef, (size_t)c.max_baselines, "batch baseline coefficients");
     }
     TOI_ALLOC(p->b_kch, (size_t)B * c.max_channels, "batch channel tables");

@@ -92,17 +92,15 @@ __device__ __forceinline__ void image_tile_body(const float* __restrict__ src, i
                                                 double* __restrict__ tile_mom,
                                                 unsigned int* __restrict__ max_cur, int tile) {
   __shared__ double sh[kFinThreads / 32][5];
-  __shared__ float kk[3];
   const int ntx = N / T;
   const int tx = tile % ntx, ty = tile / ntx;
-  if (threadIdx.x == 0) {
-    if (REPRO) {
-      kk[0] = (float)(-snap[SNAP_XI] / beta_rad);
-      kk[1] = (float)(snap[SNAP_ETA] / beta_rad);
-      kk[2] = (float)(beta_rad * beta_rad);
-    }
+  // constants made once per snapshot by the plane fit (no block barrier)
+  float kk[3] = {0.f, 0.f, 0.f};
+  if (REPRO) {
+    kk[0] = (float)snap[SNAP_REPRO];
+    kk[1] = (float)snap[SNAP_REPRO + 1];
+    kk[2] = (float)snap[SNAP_REPRO + 2];
   }
-  __syncthreads();
   float sa = 0.f, sb = 0.f, saa = 0.f, sbb = 0.f, sab = 0.f, mx = 0.f;
   // kBatch pixels per thread at a time: all their sources first, then every
   // load (clamped to valid addresses, so they issue back to back), then the
@@ -312,9 +310,9 @@ reproject_adjoint_kernel(const float* __restrict__ gimg, int N, const double* __
   const int j1 = blockIdx.x * 16 + (threadIdx.x & 15);
   const int j2 = blockIdx.y * 16 + (threadIdx.x >> 4);
   if (j1 >= N || j2 >= N) return;
-  const float K1 = (float)(-snap[SNAP_XI] / beta_rad);
-  const float K2 = (float)(snap[SNAP_ETA] / beta_rad);
-  const float b2 = (float)(beta_rad * beta_rad);
+  const float K1 = (float)snap[SNAP_REPRO];
+  const float K2 = (float)snap[SNAP_REPRO + 1];
+  const float b2 = (float)snap[SNAP_REPRO + 2];
   const double omega = snap[SNAP_OMEGA], sumw = snap[SNAP_SUMW];
   const float norm = sumw > 0.0 ? (float)(1.0 / (omega * sumw)) : 0.f;
   const float D1 = (float)(j1 - N / 2), D2 = (float)(j2 - N / 2);

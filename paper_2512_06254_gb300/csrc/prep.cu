@@ -375,7 +375,8 @@ __device__ bool smallest_eigvec(const double Cd[3][3], double v3[3]) {
 }
 
 __device__ __forceinline__ void prep_finalize_body(const double* __restrict__ bpart, int nbpart,
-                                                   double* __restrict__ snap, int* status) {
+                                                   double* __restrict__ snap, int* status,
+                                                   double beta_rad) {
   // one warp per sum: lanes take partials in a fixed stride, then a fixed tree
   __shared__ double v[11];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -426,12 +427,16 @@ __device__ __forceinline__ void prep_finalize_body(const double* __restrict__ bp
   snap[SNAP_SUMW] = empty ? 0.0 : v[10];
   snap[SNAP_NVIS] = empty ? 0.0 : N;
   snap[14] = 0.0;   // largest stored grid row touched (written by the coefficient kernel)
+  // re-projection constants, once per snapshot instead of per block
+  snap[SNAP_REPRO] = (double)(float)(-snap[SNAP_XI] / beta_rad);
+  snap[SNAP_REPRO + 1] = (double)(float)(snap[SNAP_ETA] / beta_rad);
+  snap[SNAP_REPRO + 2] = (double)(float)(beta_rad * beta_rad);
   snap[15] = 0.0;
 }
 
 __global__ void prep_finalize_kernel(const double* __restrict__ bpart, int nbpart,
-                                     double* __restrict__ snap, int* status) {
-  prep_finalize_body(bpart, nbpart, snap, status);
+                                     double* __restrict__ snap, int* status, double beta_rad) {
+  prep_finalize_body(bpart, nbpart, snap, status, beta_rad);
 }
 
 // Per baseline: R = V uvw (float64), grid coefficients a1 = -r1 beta G,
@@ -495,10 +500,11 @@ prep_baselines_batch(const BatchEntry* __restrict__ E, const BatchHeader* __rest
 }
 
 __global__ void prep_finalize_batch(const BatchEntry* __restrict__ E,
-                                    const BatchHeader* __restrict__ hdr, int* status) {
+                                    const BatchHeader* __restrict__ hdr, int* status,
+                                    double beta_rad) {
   if ((int)blockIdx.y >= hdr->n) return;
   const BatchEntry& e = E[blockIdx.y];
-  prep_finalize_body(e.bpart, (e.nbl + kMomWarps - 1) / kMomWarps, e.snap, status);
+  prep_finalize_body(e.bpart, (e.nbl + kMomWarps - 1) / kMomWarps, e.snap, status, beta_rad);
 }
 
 __global__ void prep_coef_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr,
@@ -520,7 +526,8 @@ cudaError_t launch_prep(toi_plan_s* p, Slot& s, const double* uvw, const double*
                                                      p->d_status);
   prep_baselines_kernel<<<nbblk, kMomWarps * 32, 0, p->stream>>>(
       flag, weight, p->kch, p->kch_sum, nkblk, uvw, nbl, nch, p->cfg.n_pol, p->bpart);
-  prep_finalize_kernel<<<1, 352, 0, p->stream>>>(p->bpart, nbblk, s.snap, p->d_status);
+  prep_finalize_kernel<<<1, 352, 0, p->stream>>>(p->bpart, nbblk, s.snap, p->d_status,
+                                                 p->beta_rad);
   prep_coef_kernel<<<(nbl + 127) / 128, 128, 0, p->stream>>>(uvw, nbl, nch, p->kch, s.snap,
                                                              p->beta_rad, p->G, p->W, s.coef,
                                                              p->d_status);
@@ -537,7 +544,7 @@ cudaError_t launch_prep_batch(toi_plan_s* p) {
   prep_baselines_batch<<<dim3((maxbl + kMomWarps - 1) / kMomWarps, B), kMomWarps * 32, 0,
                          p->stream>>>(p->bentry_dev, p->bheader_dev, p->cfg.n_pol);
   prep_finalize_batch<<<dim3(1, B), 352, 0, p->stream>>>(p->bentry_dev, p->bheader_dev,
-                                                         p->d_status);
+                                                         p->d_status, p->beta_rad);
   prep_coef_batch<<<dim3((maxbl + 127) / 128, B), 128, 0, p->stream>>>(
       p->bentry_dev, p->bheader_dev, p->beta_rad, p->G, p->W, p->d_status);
   prof_end(p, tok);

@@ -24,7 +24,9 @@ enum SnapField {
   SNAP_SUMW = 12,
   SNAP_NVIS = 13,
   SNAP_ROWMAX = 14,  // largest stored grid row reached by a footprint (+1 margin)
-  SNAP_LEN = 16
+  SNAP_LEN = 16,     // the part copied to snap_info
+  SNAP_REPRO = 16,   // float32 re-projection constants -xi/beta, eta/beta, beta^2 (as doubles)
+  SNAP_ALLOC = 20
 };
 
 // Per-baseline record written by the plane fit: coefficients of the grid
@@ -53,7 +55,7 @@ struct Mode3Plan {
 
 struct Slot {
   float2* grid = nullptr;          // [G/2][G] Hermitian half-plane grid
-  double* snap = nullptr;          // [SNAP_LEN]
+  double* snap = nullptr;          // [SNAP_ALLOC]
   BaselineCoef* coef = nullptr;    // [max_bl]
   // pointers of the last toi_grid call (for the adjoint)
   const double* uvw = nullptr;
