@@ -269,7 +269,7 @@ def run_ours(args):
             hpool.append({k: v.cpu().pin_memory() for k, v in p.items()})
         cube_host = torch.empty(S - 2, nt, nt, dtype=torch.float32).pin_memory()
         si = StreamingImager(plan, w.n_bl, w.n_chan, w.n_pol, batch=B,
-                             copy_streams=args.copy_streams)
+                             copy_streams=args.copy_streams, depth=args.e2e_depth)
         for _ in range(args.e2e_warmup):
             si.run(hpool, S, cube, cube_host, T)
         si.h2d_bytes = si.d2h_bytes = 0
@@ -287,6 +287,7 @@ def run_ours(args):
                "h2d_bytes_per_step": si.h2d_bytes // args.e2e_steps,
                "d2h_bytes_per_step": si.d2h_bytes // args.e2e_steps,
                "host_pool_snapshots": args.host_pool, "copy_streams": args.copy_streams,
+               "staging_depth": args.e2e_depth,
                "engine": args.engine + (f"{B}" if B else "")}
 
     mode3_plan = plan.mode3_info() if args.mode == 3 else None
@@ -640,6 +641,8 @@ def main():
     ap.add_argument("--mode", type=int, default=2, choices=[2, 3],
                     help="3: near-coplanar imaging (slabs + Chebyshev moments) of the stream "
                          "with antenna heights (single engine)")
+    ap.add_argument("--e2e-depth", type=int, default=2,
+                    help="e2e: staging slots (of a batch each with the batch engine)")
     ap.add_argument("--copy-streams", type=int, default=4,
                     help="e2e: copy streams each snapshot's host-to-device copy is split over")
     ap.add_argument("--workload", default="meerkat", choices=["meerkat", "uneven", "adjoint"],
