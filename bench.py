@@ -155,7 +155,15 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = synth.meerkat_workload(n_snap=args.snapshots)
+    cell = args.fov_deg * 3600.0 / args.image_size if args.fov_deg else 2.0
+    w = synth.meerkat_workload(n_snap=args.snapshots, n_chan=args.channels,
+                               image_size=args.image_size, cell_arcsec=cell)
+    default_shape = (args.image_size, args.channels, args.fov_deg) == (N_IMG, N_CH, None)
+    workload = (WORKLOAD if default_shape else
+                f"meerkat-64ant-2016bl-{w.n_chan}ch-4pol-{w.image_size}px-"
+                f"fov{w.image_size * cell / 3600.0:g}deg-{args.snapshots}snap")
+    ab = alg_bytes(w.n_bl, w.n_chan, w.n_pol, w.image_size)
+    snap_mb = w.n_bl * w.n_chan * w.n_pol * 9 / 1e6
     if args.mode == 3:
         # antenna heights of ~16 m rms give this array Phi_max ~ 5 (one
         # slab, K = 16), the MeerKAT row of the paper's Table 2
@@ -246,16 +254,16 @@ def run_ours(args):
         imaged = (last - first) * args.steps
     else:
         imaged = S * args.steps
-    achieved = ALG_BYTES[dom] * imaged / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
-    total_alg = sum(ALG_BYTES[k] for k in ("prep", "grid", "fft_rows", "fft_cols", "reproject",
-                                           "tlisi")) * imaged
+    achieved = ab[dom] * imaged / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    total_alg = sum(ab[k] for k in ("prep", "grid", "fft_rows", "fft_cols", "reproject",
+                                    "tlisi")) * imaged
     per_launch = args.batch if args.engine == "batch" else 1
     per_snap = GRID_DRAM_BYTES_PER_SNAPSHOT[args.engine]
-    traffic = (per_snap * per_launch if per_snap and dom == "grid" and args.mode == 2
-               else None)
+    traffic = (per_snap * per_launch
+               if per_snap and dom == "grid" and args.mode == 2 and default_shape else None)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic, "alg_bytes_per_launch": ALG_BYTES[dom] * per_launch,
+                "traffic": traffic, "alg_bytes_per_launch": ab[dom] * per_launch,
                 "share": round(dom_ms / sum(v[0] for v in prof.values()), 3),
                 "path_alg_gbs": round(total_alg / (ms / 1e3) / 1e9, 1)}
     stages = {k: {"ms_per_launch": round(v[0] / max(v[1], 1), 4), "launches": v[1]}
@@ -292,7 +300,7 @@ def run_ours(args):
 
     mode3_plan = plan.mode3_info() if args.mode == 3 else None
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and default_shape:
         cpu = cpu_baseline()
     plan.close()
     if rank == 0:
@@ -301,13 +309,16 @@ def run_ours(args):
                "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
                "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (seeded MeerKAT-shaped snapshots, resident pool)",
-               "config": {"workload": WORKLOAD + ("-3d-heights16m" if args.mode == 3 else ""),
+               "config": {"workload": workload + ("-3d-heights16m" if args.mode == 3 else ""),
                           "snapshots_per_step": S, "mode": args.mode,
                           "mode3_plan": mode3_plan,
                           "engine": args.engine + (f"{B}" if B else ""),
-                          "resident_pool": args.pool, "image": N_IMG, "grid": G,
+                          "resident_pool": args.pool, "image": w.image_size,
+                          "grid": 2 * w.image_size, "cell_arcsec": round(cell, 6),
                           "tlisi_tile": T, "candidate_mode": "periodic",
-                          "l2": "inputs larger than L2 (297 MB per snapshot, 40 distinct = one pulsar period)",
+                          "l2": (f"inputs larger than L2 ({snap_mb:.0f} MB per snapshot, "
+                                 f"{args.pool} distinct = {snap_mb * args.pool / 1e3:.1f} GB "
+                                 f"cycled; 40 = one pulsar period)"),
                           "parallelism": (f"snapshot-shards{world}" if sharded
                                           else f"replicas{world}")},
                "roofline": roofline, "stages": stages, "gpu_launches": int(launches),
@@ -641,6 +652,12 @@ def main():
     ap.add_argument("--mode", type=int, default=2, choices=[2, 3],
                     help="3: near-coplanar imaging (slabs + Chebyshev moments) of the stream "
                          "with antenna heights (single engine)")
+    ap.add_argument("--image-size", type=int, default=N_IMG,
+                    help="N of the MeerKAT-shaped stream (the paper's sweep: 2048 ... 10240)")
+    ap.add_argument("--fov-deg", type=float, default=None,
+                    help="field of view in degrees (cell = fov / N; default 2 arcsec cells)")
+    ap.add_argument("--channels", type=int, default=N_CH,
+                    help="channels per snapshot (the paper's MeerKAT set has 1024)")
     ap.add_argument("--e2e-depth", type=int, default=2,
                     help="e2e: staging slots (of a batch each with the batch engine)")
     ap.add_argument("--copy-streams", type=int, default=4,

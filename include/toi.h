@@ -59,7 +59,7 @@ typedef enum { TOI_VIS_C64 = 0, TOI_VIS_C16_CHANSCALE = 1 } toi_vis_dtype;
 typedef enum { TOI_CAND_PERIODIC = 0, TOI_CAND_NONPERIODIC = 1 } toi_cand_mode;
 
 typedef struct {
-  int32_t image_size;       /* N: power of two, 64 <= N <= 4096 (Section 2:
+  int32_t image_size;       /* N: power of two, 64 <= N <= 8192 (Section 2:
                                user-supplied image size)                        */
   double  cell_arcsec;      /* beta, pixel size in arcseconds (> 0)             */
   int32_t max_baselines;    /* largest n_bl a call may pass                     */

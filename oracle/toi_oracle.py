@@ -349,7 +349,15 @@ def reproject_source_pixels(N: int, cell_deg: float, xi: float, eta: float,
     0-based float source indices (j1, j2) as arrays [N, N] (row = j2)."""
     j2o, j1o = np.meshgrid(np.arange(N, dtype=np.float64), np.arange(N, dtype=np.float64),
                            indexing="ij")
-    p1o, p2o = j1o + 1, j2o + 1
+    return reproject_source_at(j1o, j2o, N, cell_deg, xi, eta, iters)
+
+
+def reproject_source_at(j1o, j2o, N: int, cell_deg: float, xi: float, eta: float,
+                        iters: int = 8):
+    """The fixed point of reproject_source_pixels for given 0-based output
+    pixels (j1o = column, j2o = row), any array shape."""
+    p1o = np.asarray(j1o, dtype=np.float64) + 1
+    p2o = np.asarray(j2o, dtype=np.float64) + 1
     p1, p2 = p1o.copy(), p2o.copy()
     for _ in range(iters):
         m1, m2 = reproject_map_reduced(p1, p2, N, cell_deg, xi, eta)

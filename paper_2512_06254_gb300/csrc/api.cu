@@ -10,7 +10,8 @@
 #include "toi_internal.cuh"
 
 namespace toi {
-cudaError_t fft_configure();
+cudaError_t fft_configure(int G);
+bool fft_length_supported(int G);
 size_t candidates_scratch_bytes(int S, int nt);
 cudaError_t candidates_run(const float* cube, int S, int nty, int ntx, int T, int mode,
                            cudaStream_t st, void* scratch, double* scores_out, int max_boxes,
@@ -86,7 +87,6 @@ toi_status cuda_fail(toi_plan_s* p, cudaError_t e, const char* where) {
   return fail(p, TOI_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 // lengths of the per-snapshot partial-sum buffers of the plane fit
 size_t kpart_len(int max_ch) { return 2 * (((size_t)max_ch + 255) / 256) + 2; }
@@ -195,8 +195,9 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   const toi_config c = *cfg;
   if (c.image_size < 64)
     return fail(nullptr, TOI_ERR_ARG, "image_size must be at least 64");
-  if (!is_pow2(c.image_size) || c.image_size > 4096)
-    return fail(nullptr, TOI_ERR_UNSUPPORTED, "image_size must be a power of two in [64, 4096]");
+  if (c.image_size > 10240 || !toi::fft_length_supported(2 * c.image_size))
+    return fail(nullptr, TOI_ERR_UNSUPPORTED,
+                "image_size must be 2^a (64 ... 8192), 3 2^a (96 ... 6144) or 5 2^a (160 ... 10240)");
   if (!(c.cell_arcsec > 0.0) || !isfinite(c.cell_arcsec))
     return fail(nullptr, TOI_ERR_ARG, "cell_arcsec must be positive and finite");
   if (c.max_baselines < 1 || c.max_channels < 1)
@@ -245,7 +246,7 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   const int N = p->N, G = p->G;
   const int ntl = (N / p->T) * (N / p->T);
   toi_status st = TOI_OK;
-  cudaError_t e = toi::fft_configure();
+  cudaError_t e = toi::fft_configure(G);
   if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "configuring FFT kernels"); free_plan(p); return r; }
   p->slots = new (std::nothrow) Slot[p->nslot];
   if (!p->slots) { free_plan(p); return fail(nullptr, TOI_ERR_OOM, "host allocation failed"); }

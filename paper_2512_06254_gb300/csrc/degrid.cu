@@ -144,7 +144,8 @@ degrid_backward_kernel(const float2* __restrict__ K, int G, const BaselineCoef* 
           const float2* row = K + (size_t)(-r) * G;
 #pragma unroll
           for (int a = 0; a < kW; ++a) {
-            const float2 v = row[(G - (k1 + a)) & (G - 1)];
+            const int n = k1 + a;
+            const float2 v = row[n == 0 ? 0 : G - n];
             acc.x += wx[a] * v.x;
             acc.y += wx[a] * v.y;
           }

@@ -1,477 +1,73 @@
-// S4-S5: centred inverse 2-D FFT of the Hermitian half-plane grid, output
-// pruned to the central N x N, Re, grid correction and normalisation
-// (Section 4.1 stage 4; Section 3.2 with Eq. 11).
-//
-// With k' = k - G/2 and j' = j - N/2 the image is
-//   I[j2', j1'] = 1/2 sum_{k2'} sum_{k1'} H[k2', k1'] e^{2 pi i (k1' j1' + k2' j2') / G}
-// where H holds rows k2' >= 0 and rows k2' < 0 are conj(H[-k']) (the grid is
-// stored as H = G + conj(G(-k)), hence the 1/2).
-//   Pass 1 (rows, along k1'): T[k2', j1'] = sum_{k1'} H[k2', k1'] e^{..}; only
-//            the N central j1' are written, as (-1)^j1' Z[j1' mod G] of the
-//            plain inverse DFT Z of the row.  Rows beyond the last one any
-//            footprint reached are zero and skipped (input pruning); each row
-//            read is cleared in the grid, which leaves the slot zeroed for the
-//            next gridding.
-//   Pass 2 (columns, along k2'): each column sequence is Hermitian in k2', so
-//            its transform is real; two columns a, b are transformed together
-//            as Z = U_a + i U_b (Re -> column a, Im -> column b), rebuilt over
-//            the full length G from the stored half.  1/2 of the N central
-//            outputs is multiplied by 1/psi_hat(j1') 1/psi_hat(j2') /
-//            (omega sum w).
-// Each transform is a Stockham autosort FFT in shared memory: radix-8 passes
-// (then one radix-4 or radix-2 pass) whose butterflies run in registers,
-// twiddles from a float32 table e^{+2 pi i m / G} made in float64 at plan time
-// (three table reads per radix-8 butterfly, the other powers by products).
-// Shared memory is padded by one slot per eight to avoid bank conflicts of
-// the strided Stockham stores.
-#include "toi_internal.cuh"
+// S4-S5 transform lengths G = 2^a (image sizes 64 ... 8192) and the
+// plan-facing FFT entry points, which dispatch on G to the translation unit
+// of its length family (2^a here, 3 2^a in fft_r3.cu, 5 2^a in fft_r5.cu).
+// The kernels themselves are in fft_kernels.cuh.
+#include "fft_kernels.cuh"
 
 namespace toi {
+
+cudaError_t fft_configure_pow2(int G) {
+  switch (G) {
+    case 128: return configure_g<128>();
+    case 256: return configure_g<256>();
+    case 512: return configure_g<512>();
+    case 1024: return configure_g<1024>();
+    case 2048: return configure_g<2048>();
+    case 4096: return configure_g<4096>();
+    case 8192: return configure_g<8192>();
+    case 16384: return configure_g<16384>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t fft_run_pow2(toi_plan_s* p, FftOp op, Slot* s, float* out) {
+  switch (p->G) {
+    case 128: return run_g<128>(p, op, s, out);
+    case 256: return run_g<256>(p, op, s, out);
+    case 512: return run_g<512>(p, op, s, out);
+    case 1024: return run_g<1024>(p, op, s, out);
+    case 2048: return run_g<2048>(p, op, s, out);
+    case 4096: return run_g<4096>(p, op, s, out);
+    case 8192: return run_g<8192>(p, op, s, out);
+    case 16384: return run_g<16384>(p, op, s, out);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 namespace {
 
-__device__ __forceinline__ int pad(int a) { return a + (a >> 3); }
+bool is_pow2_len(int G) { return G > 0 && (G & (G - 1)) == 0; }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-// multiply by +i
-__device__ __forceinline__ float2 cmuli(float2 a) { return make_float2(-a.y, a.x); }
-
-// In-register inverse DFTs V[k] = sum_j v[j] e^{+2 pi i j k / R}.
-__device__ __forceinline__ void dft2(float2* v) {
-  const float2 a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = csub(a, b);
-}
-
-__device__ __forceinline__ void dft4(float2* v) {
-  const float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
-  const float2 b0 = cadd(v[1], v[3]), b1 = cmuli(csub(v[1], v[3]));
-  v[0] = cadd(a0, b0);
-  v[2] = csub(a0, b0);
-  v[1] = cadd(a1, b1);
-  v[3] = csub(a1, b1);
-}
-
-__device__ __forceinline__ void dft8(float2* v) {
-  const float r = 0.70710678118654752f;
-  // decimation in frequency: first stage span 4 with twiddles e^{+2 pi i j/8}
-  float2 t[8];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    t[j] = cadd(v[j], v[j + 4]);
-    t[j + 4] = csub(v[j], v[j + 4]);
-  }
-  t[5] = make_float2(r * (t[5].x - t[5].y), r * (t[5].x + t[5].y));    // * (1+i)/sqrt2
-  t[6] = cmuli(t[6]);                                                  // * i
-  t[7] = make_float2(-r * (t[7].x + t[7].y), r * (t[7].x - t[7].y));   // * (-1+i)/sqrt2
-  float2 a[4] = {t[0], t[1], t[2], t[3]};
-  float2 b[4] = {t[4], t[5], t[6], t[7]};
-  dft4(a);
-  dft4(b);
-  v[0] = a[0]; v[2] = a[1]; v[4] = a[2]; v[6] = a[3];
-  v[1] = b[0]; v[3] = b[1]; v[5] = b[2]; v[7] = b[3];
-}
-
-template <int R>
-__device__ __forceinline__ void dftR(float2* v) {
-  if (R == 8) dft8(v);
-  else if (R == 4) dft4(v);
-  else dft2(v);
-}
-
-// twiddle powers w^r, r = 1..R-1, with w = e^{+2 pi i step / G}
-template <int R>
-__device__ __forceinline__ void twiddles(const float2* __restrict__ tw, int step, float2* w) {
-  if (R == 8) {
-    const float2 w1 = __ldg(tw + step), w2 = __ldg(tw + 2 * step), w4 = __ldg(tw + 4 * step);
-    w[1] = w1; w[2] = w2; w[4] = w4;
-    w[3] = cmul(w2, w1);
-    w[5] = cmul(w4, w1);
-    w[6] = cmul(w4, w2);
-    w[7] = cmul(w4, w[3]);
-  } else if (R == 4) {
-    const float2 w1 = __ldg(tw + step), w2 = __ldg(tw + 2 * step);
-    w[1] = w1; w[2] = w2;
-    w[3] = cmul(w2, w1);
-  } else {
-    w[1] = __ldg(tw + step);
-  }
-}
-
-// One Stockham pass of radix R over `nseq` padded sequences of length G in
-// shared memory (in place: all loads, barrier, all stores, barrier).
-template <int G, int R, int BPT>
-__device__ __forceinline__ void stockham_pass(float2* x, int nseq, int Ns, const float2* __restrict__ tw) {
-  constexpr int NB = G / R;       // butterflies per sequence
-  constexpr int LEN = G + G / 8;  // padded sequence length
-  float2 v[BPT][R];
-  int jj[BPT], ss[BPT];
-#pragma unroll
-  for (int b = 0; b < BPT; ++b) {
-    const int id = threadIdx.x + b * blockDim.x;
-    const int seq = id / NB, j = id - seq * NB;
-    jj[b] = j;
-    ss[b] = seq;
-    if (seq < nseq) {
-      const float2* xs = x + (size_t)seq * LEN;
-      const int k = j & (Ns - 1);
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = xs[pad(j + r * NB)];
-      if (k > 0) {
-        float2 w[R];
-        twiddles<R>(tw, (G / (Ns * R)) * k, w);
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
-      }
-      dftR<R>(v[b]);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int b = 0; b < BPT; ++b) {
-    if (ss[b] < nseq) {
-      float2* xs = x + (size_t)ss[b] * LEN;
-      const int j = jj[b];
-      const int k = j & (Ns - 1);
-      const int base = (j - k) * R + k;
-#pragma unroll
-      for (int r = 0; r < R; ++r) xs[pad(base + r * Ns)] = v[b][r];
-    }
-  }
-  __syncthreads();
-}
-
-template <int G, int NSEQ, int NT>
-__device__ __forceinline__ void fft_smem(float2* x, const float2* __restrict__ tw) {
-  constexpr int LOG = (G >= 8192) ? 13 : (G >= 4096) ? 12 : (G >= 2048) ? 11 : (G >= 1024) ? 10
-                    : (G >= 512) ? 9 : (G >= 256) ? 8 : 7;
-  constexpr int N8 = LOG / 3;
-  constexpr int REM = LOG - 3 * N8;
-  constexpr int BPT8 = (NSEQ * (G / 8) + NT - 1) / NT;
-  int Ns = 1;
-#pragma unroll
-  for (int p = 0; p < N8; ++p) {
-    stockham_pass<G, 8, BPT8>(x, NSEQ, Ns, tw);
-    Ns *= 8;
-  }
-  if (REM == 2) {
-    constexpr int BPT4 = (NSEQ * (G / 4) + NT - 1) / NT;
-    stockham_pass<G, 4, BPT4>(x, NSEQ, Ns, tw);
-  } else if (REM == 1) {
-    constexpr int BPT2 = (NSEQ * (G / 2) + NT - 1) / NT;
-    stockham_pass<G, 2, BPT2>(x, NSEQ, Ns, tw);
-  }
-}
-
-__device__ __forceinline__ int row_limit(const double* snap, int G) {
-  const int r = (int)ceil(snap[SNAP_ROWMAX]);
-  return r < G / 2 ? r : G / 2 - 1;
-}
-
-template <int G>
-struct RowCfg {
-  static constexpr int NT = (G / 8 < 64) ? 64 : (G / 8 > 512 ? 512 : G / 8);
-};
-
-template <int G>
-__device__ __forceinline__ void fft_rows_body(float2* __restrict__ H, int N,
-                                              const float2* __restrict__ tw,
-                                              const double* __restrict__ snap,
-                                              float2* __restrict__ T, int row) {
-  extern __shared__ float2 x[];
-  if (row > row_limit(snap, G)) return;
-  float2* src = H + (size_t)row * G;
-  constexpr int PER = (G + RowCfg<G>::NT - 1) / RowCfg<G>::NT;
-  float2 v[PER];
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {   // all loads first, then the stores
-    const int n = threadIdx.x + u * RowCfg<G>::NT;
-    v[u] = n < G ? src[n] : make_float2(0.f, 0.f);
-  }
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const int n = threadIdx.x + u * RowCfg<G>::NT;
-    if (n < G) x[pad(n)] = v[u];
-  }
-  __syncthreads();
-  fft_smem<G, 1, RowCfg<G>::NT>(x, tw);
-  float2* dst = T + (size_t)row * N;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const int jp = j - N / 2;
-    float2 v = x[pad(jp < 0 ? jp + G : jp)];
-    if (jp & 1) { v.x = -v.x; v.y = -v.y; }
-    dst[j] = v;
-  }
-  // leave the grid slot cleared for the next gridding
-  for (int n = threadIdx.x; n < G; n += blockDim.x) src[n] = make_float2(0.f, 0.f);
-}
-
-template <int G>
-__global__ void __launch_bounds__(RowCfg<G>::NT)
-fft_rows_kernel(float2* __restrict__ H, int N, const float2* __restrict__ tw,
-                const double* __restrict__ snap, float2* __restrict__ T) {
-  fft_rows_body<G>(H, N, tw, snap, T, blockIdx.x);
-}
-
-template <int G>
-__global__ void __launch_bounds__(RowCfg<G>::NT)
-fft_rows_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
-               const float2* __restrict__ tw) {
-  if ((int)blockIdx.y >= hdr->n) return;
-  const BatchEntry& e = E[blockIdx.y];
-  fft_rows_body<G>(e.grid, N, tw, e.snap, e.fft_tmp, blockIdx.x);
-}
-
-template <int G>
-struct ColCfg {
-  static constexpr int CW = 4;            // columns per block: two complex transforms
-  static constexpr int NT = 512;
-  static constexpr int LEN = G + G / 8;
-};
-
-template <int G>
-__device__ __forceinline__ void fft_cols_body(const float2* __restrict__ T, int N,
-                                              const float2* __restrict__ tw,
-                                              const float* __restrict__ corr,
-                                              const double* __restrict__ snap,
-                                              float* __restrict__ out, int blk) {
-  constexpr int CW = ColCfg<G>::CW, LEN = ColCfg<G>::LEN;
-  extern __shared__ float2 x[];
-  const int col0 = blk * CW;
-  constexpr int half = G / 2;
-  const int rmax = row_limit(snap, G);
-  for (int e = threadIdx.x; e < half * 2; e += blockDim.x) {
-    const int r = e >> 1, pr = e & 1;     // row, column pair
-    float2* xs = x + (size_t)pr * LEN;
-    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-    if (r <= rmax) {
-      const float4 ab = *reinterpret_cast<const float4*>(T + (size_t)r * N + col0 + 2 * pr);
-      a = make_float2(ab.x, ab.y);
-      b = make_float2(ab.z, ab.w);
-    }
-    // Z[r] = U_a[r] + i U_b[r];  Z[-r] = conj(U_a[r]) + i conj(U_b[r])
-    xs[pad(r)] = make_float2(a.x - b.y, a.y + b.x);
-    if (r > 0) xs[pad(G - r)] = make_float2(a.x + b.y, b.x - a.y);
-    else xs[pad(half)] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  fft_smem<G, 2, ColCfg<G>::NT>(x, tw);
-  const double omega = snap[SNAP_OMEGA], sumw = snap[SNAP_SUMW];
-  const float norm = sumw > 0.0 ? (float)(0.5 / (omega * sumw)) : 0.f;
-  const float ca = corr[col0], cb = corr[col0 + 1], cc = corr[col0 + 2], cd = corr[col0 + 3];
-  for (int j2 = threadIdx.x; j2 < N; j2 += blockDim.x) {
-    const int jp = j2 - N / 2;
-    const int m = pad(jp < 0 ? jp + G : jp);
-    const float2 z0 = x[m], z1 = x[LEN + m];
-    const float s = norm * corr[j2];
-    float4 o;
-    o.x = z0.x * (s * ca);
-    o.y = z0.y * (s * cb);
-    o.z = z1.x * (s * cc);
-    o.w = z1.y * (s * cd);
-    *reinterpret_cast<float4*>(out + (size_t)j2 * N + col0) = o;
-  }
-}
-
-template <int G>
-__global__ void __launch_bounds__(ColCfg<G>::NT)
-fft_cols_kernel(const float2* __restrict__ T, int N, const float2* __restrict__ tw,
-                const float* __restrict__ corr, const double* __restrict__ snap,
-                float* __restrict__ out) {
-  fft_cols_body<G>(T, N, tw, corr, snap, out, blockIdx.x);
-}
-
-template <int G>
-__global__ void __launch_bounds__(ColCfg<G>::NT)
-fft_cols_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
-               const float2* __restrict__ tw, const float* __restrict__ corr) {
-  if ((int)blockIdx.y >= hdr->n) return;
-  const BatchEntry& e = E[blockIdx.y];
-  fft_cols_body<G>(e.fft_tmp, N, tw, corr, e.snap, e.tilted, blockIdx.x);
-}
-
-// ---------------------------------------------------------------------------
-// Adjoint passes (toi_degrid_backward).  The sample cotangents need
-//   Hbar[k'] = sum_j' U[j'] e^{-2 pi i (k1' j1' + k2' j2') / G}
-// for rows k2' = 0..R, U the real N x N cotangent (already scaled by the grid
-// correction and 1/(omega sum w)); rows k2' < 0 are conj(Hbar[-k']).  Both
-// passes run the same e^{+} transform core and use that U is real:
-//   pass A (columns, along j2'): Y[k2', j1'] = sum_j2' U e^{+2 pi i k2' j2' / G},
-//       two real columns per complex transform (Z = U_a + i U_b, then
-//       Y_a[k] = (Z[k] + conj Z[-k]) / 2, Y_b[k] = (Z[k] - conj Z[-k]) / 2i);
-//   pass B (rows, along j1'): K[k2', n] = sum_j1' (-1)^j1' Y[k2', j1'] e^{+2 pi i n j1' / G},
-//       n = k1' + G/2, so that Hbar[k2', n] = conj(K[k2', n]).
-// They are the adjoints of pass 2 and pass 1 of the image, with the same row
-// pruning.
-
-template <int G>
-__global__ void __launch_bounds__(ColCfg<G>::NT)
-fft_adj_cols_kernel(const float* __restrict__ U, int N, const float2* __restrict__ tw,
-                    const double* __restrict__ snap, float2* __restrict__ Y) {
-  constexpr int CW = ColCfg<G>::CW, LEN = ColCfg<G>::LEN;
-  extern __shared__ float2 x[];
-  const int col0 = blockIdx.x * CW;
-  const int rmax = row_limit(snap, G);
-  for (int e = threadIdx.x; e < 2 * LEN; e += blockDim.x) x[e] = make_float2(0.f, 0.f);
-  __syncthreads();
-  for (int j2 = threadIdx.x; j2 < N; j2 += blockDim.x) {
-    const float4 u = *reinterpret_cast<const float4*>(U + (size_t)j2 * N + col0);
-    const int jp = j2 - N / 2;
-    const int m = pad(jp < 0 ? jp + G : jp);
-    x[m] = make_float2(u.x, u.y);          // columns col0, col0 + 1
-    x[LEN + m] = make_float2(u.z, u.w);    // columns col0 + 2, col0 + 3
-  }
-  __syncthreads();
-  fft_smem<G, 2, ColCfg<G>::NT>(x, tw);
-  for (int e = threadIdx.x; e < (rmax + 1) * 2; e += blockDim.x) {
-    const int r = e >> 1, pr = e & 1;
-    const float2* xs = x + (size_t)pr * LEN;
-    const float2 z = xs[pad(r)], zm = xs[pad((G - r) & (G - 1))];
-    const float4 o = make_float4(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y),
-                                 0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
-    *reinterpret_cast<float4*>(Y + (size_t)r * N + col0 + 2 * pr) = o;
-  }
-}
-
-template <int G>
-__global__ void __launch_bounds__(RowCfg<G>::NT)
-fft_adj_rows_kernel(const float2* __restrict__ Y, int N, const float2* __restrict__ tw,
-                    const double* __restrict__ snap, float2* __restrict__ K) {
-  extern __shared__ float2 x[];
-  const int row = blockIdx.x;
-  if (row > row_limit(snap, G)) return;
-  for (int n = threadIdx.x; n < G; n += blockDim.x) x[pad(n)] = make_float2(0.f, 0.f);
-  __syncthreads();
-  const float2* src = Y + (size_t)row * N;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const int jp = j - N / 2;
-    float2 v = src[j];
-    if (jp & 1) { v.x = -v.x; v.y = -v.y; }
-    x[pad(jp < 0 ? jp + G : jp)] = v;
-  }
-  __syncthreads();
-  fft_smem<G, 1, RowCfg<G>::NT>(x, tw);
-  float2* dst = K + (size_t)row * G;
-  for (int n = threadIdx.x; n < G; n += blockDim.x) dst[n] = x[pad(n)];
-}
-
-template <int G>
-cudaError_t configure_g() {
-  const int row_smem = (G + G / 8) * (int)sizeof(float2);
-  const int col_smem = 2 * ColCfg<G>::LEN * (int)sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       row_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fft_cols_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fft_adj_rows_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             row_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fft_adj_cols_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             col_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fft_rows_batch<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fft_cols_batch<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
-  return e;
-}
-
-template <int G>
-void launch_batch_g(toi_plan_s* p) {
-  const int N = p->N, B = p->batch_max;
-  constexpr int CW = ColCfg<G>::CW;
-  int tok = prof_begin(p, PROF_FFT_ROWS, 1);
-  fft_rows_batch<G><<<dim3(G / 2, B), RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
-      p->bentry_dev, p->bheader_dev, N, p->twiddle);
-  prof_end(p, tok);
-  tok = prof_begin(p, PROF_FFT_COLS, 1);
-  fft_cols_batch<G><<<dim3(N / CW, B), ColCfg<G>::NT, 2 * ColCfg<G>::LEN * sizeof(float2),
-                      p->stream>>>(p->bentry_dev, p->bheader_dev, N, p->twiddle, p->corr);
-  prof_end(p, tok);
-}
-
-template <int G>
-void launch_adj_g(toi_plan_s* p, Slot& s) {
-  const int N = p->N;
-  constexpr int CW = ColCfg<G>::CW;
-  fft_adj_cols_kernel<G><<<N / CW, ColCfg<G>::NT, 2 * ColCfg<G>::LEN * sizeof(float2), p->stream>>>(
-      p->tilted, N, p->twiddle, s.snap, p->fft_tmp);
-  fft_adj_rows_kernel<G><<<G / 2, RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
-      p->fft_tmp, N, p->twiddle, s.snap, s.grid);
-}
-
-template <int G>
-void launch_g(toi_plan_s* p, Slot& s, float* out) {
-  const int N = p->N;
-  int tok = prof_begin(p, PROF_FFT_ROWS, 1);
-  fft_rows_kernel<G><<<G / 2, RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
-      s.grid, N, p->twiddle, s.snap, p->fft_tmp);
-  prof_end(p, tok);
-  tok = prof_begin(p, PROF_FFT_COLS, 1);
-  constexpr int CW = ColCfg<G>::CW;
-  fft_cols_kernel<G><<<N / CW, ColCfg<G>::NT, 2 * ColCfg<G>::LEN * sizeof(float2), p->stream>>>(
-      p->fft_tmp, N, p->twiddle, p->corr, s.snap, out);
-  prof_end(p, tok);
+cudaError_t run(toi_plan_s* p, FftOp op, Slot* s, float* out) {
+  if (is_pow2_len(p->G)) return fft_run_pow2(p, op, s, out);
+  if (p->G % 3 == 0) return fft_run_r3(p, op, s, out);
+  return fft_run_r5(p, op, s, out);
 }
 
 }  // namespace
 
-cudaError_t fft_configure() {
-  cudaError_t e;
-  if ((e = configure_g<128>()) != cudaSuccess) return e;
-  if ((e = configure_g<256>()) != cudaSuccess) return e;
-  if ((e = configure_g<512>()) != cudaSuccess) return e;
-  if ((e = configure_g<1024>()) != cudaSuccess) return e;
-  if ((e = configure_g<2048>()) != cudaSuccess) return e;
-  if ((e = configure_g<4096>()) != cudaSuccess) return e;
-  return configure_g<8192>();
+bool fft_length_supported(int G) {
+  if (G < 128 || G % 8 != 0) return false;
+  int m = G;
+  while (m % 2 == 0) m /= 2;
+  if (m == 1) return G <= 16384;
+  if (m == 3) return G >= 192 && G <= 12288;
+  if (m == 5) return G >= 320 && G <= 20480;
+  return false;
 }
 
-cudaError_t launch_fft_to(toi_plan_s* p, Slot& s, float* out) {
-  switch (p->G) {
-    case 128: launch_g<128>(p, s, out); break;
-    case 256: launch_g<256>(p, s, out); break;
-    case 512: launch_g<512>(p, s, out); break;
-    case 1024: launch_g<1024>(p, s, out); break;
-    case 2048: launch_g<2048>(p, s, out); break;
-    case 4096: launch_g<4096>(p, s, out); break;
-    case 8192: launch_g<8192>(p, s, out); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+cudaError_t fft_configure(int G) {
+  if (is_pow2_len(G)) return fft_configure_pow2(G);
+  if (G % 3 == 0) return fft_configure_r3(G);
+  return fft_configure_r5(G);
 }
+
+cudaError_t launch_fft_to(toi_plan_s* p, Slot& s, float* out) { return run(p, FFT_FORWARD, &s, out); }
 
 cudaError_t launch_fft(toi_plan_s* p, Slot& s) { return launch_fft_to(p, s, p->tilted); }
 
-cudaError_t launch_fft_batch(toi_plan_s* p) {
-  switch (p->G) {
-    case 128: launch_batch_g<128>(p); break;
-    case 256: launch_batch_g<256>(p); break;
-    case 512: launch_batch_g<512>(p); break;
-    case 1024: launch_batch_g<1024>(p); break;
-    case 2048: launch_batch_g<2048>(p); break;
-    case 4096: launch_batch_g<4096>(p); break;
-    case 8192: launch_batch_g<8192>(p); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
+cudaError_t launch_fft_batch(toi_plan_s* p) { return run(p, FFT_BATCH, nullptr, nullptr); }
 
-cudaError_t launch_fft_adjoint(toi_plan_s* p, Slot& s) {
-  switch (p->G) {
-    case 128: launch_adj_g<128>(p, s); break;
-    case 256: launch_adj_g<256>(p, s); break;
-    case 512: launch_adj_g<512>(p, s); break;
-    case 1024: launch_adj_g<1024>(p, s); break;
-    case 2048: launch_adj_g<2048>(p, s); break;
-    case 4096: launch_adj_g<4096>(p, s); break;
-    case 8192: launch_adj_g<8192>(p, s); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
+cudaError_t launch_fft_adjoint(toi_plan_s* p, Slot& s) { return run(p, FFT_ADJOINT, &s, nullptr); }
 
 }  // namespace toi

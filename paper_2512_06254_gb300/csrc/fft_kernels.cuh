@@ -1,0 +1,532 @@
+// S4-S5: centred inverse 2-D FFT of the Hermitian half-plane grid, output
+// pruned to the central N x N, Re, grid correction and normalisation
+// (Section 4.1 stage 4; Section 3.2 with Eq. 11).
+//
+// With k' = k - G/2 and j' = j - N/2 the image is
+//   I[j2', j1'] = 1/2 sum_{k2'} sum_{k1'} H[k2', k1'] e^{2 pi i (k1' j1' + k2' j2') / G}
+// where H holds rows k2' >= 0 and rows k2' < 0 are conj(H[-k']) (the grid is
+// stored as H = G + conj(G(-k)), hence the 1/2).
+//   Pass 1 (rows, along k1'): T[k2', j1'] = sum_{k1'} H[k2', k1'] e^{..}; only
+//            the N central j1' are written, as (-1)^j1' Z[j1' mod G] of the
+//            plain inverse DFT Z of the row.  Rows beyond the last one any
+//            footprint reached are zero and skipped (input pruning); each row
+//            read is cleared in the grid, which leaves the slot zeroed for the
+//            next gridding.
+//   Pass 2 (columns, along k2'): each column sequence is Hermitian in k2', so
+//            its transform is real; two columns a, b are transformed together
+//            as Z = U_a + i U_b (Re -> column a, Im -> column b), rebuilt over
+//            the full length G from the stored half.  1/2 of the N central
+//            outputs is multiplied by 1/psi_hat(j1') 1/psi_hat(j2') /
+//            (omega sum w).
+// Each transform is a Stockham autosort FFT in shared memory: radix-8 passes
+// (then one radix-4 or radix-2 pass, and for G = 3 2^a or 5 2^a one radix-3
+// or radix-5 pass) whose butterflies run in registers,
+// twiddles from a float32 table e^{+2 pi i m / G} made in float64 at plan time
+// (three table reads per radix-8 butterfly, the other powers by products).
+// Shared memory is padded by one slot per eight to avoid bank conflicts of
+// the strided Stockham stores.
+#pragma once
+#include "toi_internal.cuh"
+
+namespace toi {
+
+enum FftOp { FFT_FORWARD, FFT_BATCH, FFT_ADJOINT };
+
+namespace {
+
+__device__ __forceinline__ int pad(int a) { return a + (a >> 3); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiply by +i
+__device__ __forceinline__ float2 cmuli(float2 a) { return make_float2(-a.y, a.x); }
+
+// In-register inverse DFTs V[k] = sum_j v[j] e^{+2 pi i j k / R}.
+__device__ __forceinline__ void dft2(float2* v) {
+  const float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+__device__ __forceinline__ void dft4(float2* v) {
+  const float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+  const float2 b0 = cadd(v[1], v[3]), b1 = cmuli(csub(v[1], v[3]));
+  v[0] = cadd(a0, b0);
+  v[2] = csub(a0, b0);
+  v[1] = cadd(a1, b1);
+  v[3] = csub(a1, b1);
+}
+
+__device__ __forceinline__ void dft8(float2* v) {
+  const float r = 0.70710678118654752f;
+  // decimation in frequency: first stage span 4 with twiddles e^{+2 pi i j/8}
+  float2 t[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    t[j] = cadd(v[j], v[j + 4]);
+    t[j + 4] = csub(v[j], v[j + 4]);
+  }
+  t[5] = make_float2(r * (t[5].x - t[5].y), r * (t[5].x + t[5].y));    // * (1+i)/sqrt2
+  t[6] = cmuli(t[6]);                                                  // * i
+  t[7] = make_float2(-r * (t[7].x + t[7].y), r * (t[7].x - t[7].y));   // * (-1+i)/sqrt2
+  float2 a[4] = {t[0], t[1], t[2], t[3]};
+  float2 b[4] = {t[4], t[5], t[6], t[7]};
+  dft4(a);
+  dft4(b);
+  v[0] = a[0]; v[2] = a[1]; v[4] = a[2]; v[6] = a[3];
+  v[1] = b[0]; v[3] = b[1]; v[5] = b[2]; v[7] = b[3];
+}
+
+// radix 3: with s = sin(2 pi / 3), V1,2 = v0 - (v1 + v2) / 2 +- i s (v1 - v2)
+__device__ __forceinline__ void dft3(float2* v) {
+  const float s = 0.86602540378443865f;
+  const float2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+  const float2 m = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
+  const float2 is = make_float2(-s * t2.y, s * t2.x);
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(m, is);
+  v[2] = csub(m, is);
+}
+
+// radix 5 from the symmetric and antisymmetric pairs (v1, v4), (v2, v3):
+// V1,4 = v0 + c1 t1 + c2 t2 +- i (s1 d1 + s2 d2),
+// V2,3 = v0 + c2 t1 + c1 t2 +- i (s2 d1 - s1 d2),
+// with t = v1 + v4, v2 + v3, d = v1 - v4, v2 - v3, c_k = cos(2 pi k / 5),
+// s_k = sin(2 pi k / 5).
+__device__ __forceinline__ void dft5(float2* v) {
+  const float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;
+  const float s1 = 0.95105651629515357f, s2 = 0.58778525229247313f;
+  const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  const float2 d1 = csub(v[1], v[4]), d2 = csub(v[2], v[3]);
+  const float2 a1 = make_float2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+  const float2 a2 = make_float2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+  const float2 b1 = make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
+  const float2 b2 = make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+  v[0] = cadd(v[0], cadd(t1, t2));
+  v[1] = cadd(a1, cmuli(b1));
+  v[4] = csub(a1, cmuli(b1));
+  v[2] = cadd(a2, cmuli(b2));
+  v[3] = csub(a2, cmuli(b2));
+}
+
+template <int R>
+__device__ __forceinline__ void dftR(float2* v) {
+  if constexpr (R == 8) dft8(v);
+  else if constexpr (R == 5) dft5(v);
+  else if constexpr (R == 4) dft4(v);
+  else if constexpr (R == 3) dft3(v);
+  else dft2(v);
+}
+
+// twiddle powers w^r, r = 1..R-1, with w = e^{+2 pi i step / G}
+template <int R>
+__device__ __forceinline__ void twiddles(const float2* __restrict__ tw, int step, float2* w) {
+  if constexpr (R == 8) {
+    const float2 w1 = __ldg(tw + step), w2 = __ldg(tw + 2 * step), w4 = __ldg(tw + 4 * step);
+    w[1] = w1; w[2] = w2; w[4] = w4;
+    w[3] = cmul(w2, w1);
+    w[5] = cmul(w4, w1);
+    w[6] = cmul(w4, w2);
+    w[7] = cmul(w4, w[3]);
+  } else if constexpr (R == 5) {
+    const float2 w1 = __ldg(tw + step), w2 = __ldg(tw + 2 * step);
+    w[1] = w1; w[2] = w2;
+    w[3] = cmul(w2, w1);
+    w[4] = cmul(w2, w2);
+  } else if constexpr (R == 4 || R == 3) {
+    const float2 w1 = __ldg(tw + step), w2 = __ldg(tw + 2 * step);
+    w[1] = w1; w[2] = w2;
+    if constexpr (R == 4) w[3] = cmul(w2, w1);
+  } else {
+    w[1] = __ldg(tw + step);
+  }
+}
+
+// One Stockham pass of radix R over `nseq` padded sequences of length G in
+// shared memory (in place: all loads, barrier, all stores, barrier).
+template <int G, int R, int BPT>
+__device__ __forceinline__ void stockham_pass(float2* x, int nseq, int Ns, const float2* __restrict__ tw) {
+  constexpr int NB = G / R;       // butterflies per sequence
+  constexpr int LEN = G + G / 8;  // padded sequence length
+  float2 v[BPT][R];
+  int jj[BPT], ss[BPT];
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    const int id = threadIdx.x + b * blockDim.x;
+    const int seq = id / NB, j = id - seq * NB;
+    jj[b] = j;
+    ss[b] = seq;
+    if (seq < nseq) {
+      const float2* xs = x + (size_t)seq * LEN;
+      const int k = j & (Ns - 1);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = xs[pad(j + r * NB)];
+      if (k > 0) {
+        float2 w[R];
+        twiddles<R>(tw, (G / (Ns * R)) * k, w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
+      }
+      dftR<R>(v[b]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    if (ss[b] < nseq) {
+      float2* xs = x + (size_t)ss[b] * LEN;
+      const int j = jj[b];
+      const int k = j & (Ns - 1);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) xs[pad(base + r * Ns)] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+// G = F 2^LOG with F in {1, 3, 5}: radix-8 passes, one radix-4 or radix-2
+// pass for the rest of the power of two, then one radix-F pass (last, so
+// that every pass before it has a power-of-two span Ns).
+template <int G>
+struct Factors {
+  static constexpr int F = (G % 3 == 0) ? 3 : ((G % 5 == 0) ? 5 : 1);
+  static constexpr int LOG = ilog2(G / F);
+  static_assert(F * (1 << LOG) == G, "transform length must be 2^a, 3 2^a or 5 2^a");
+  static_assert(G % 8 == 0, "transform length must be a multiple of 8");
+};
+
+template <int G, int NSEQ, int NT>
+__device__ __forceinline__ void fft_smem(float2* x, const float2* __restrict__ tw) {
+  constexpr int F = Factors<G>::F, LOG = Factors<G>::LOG;
+  constexpr int N8 = LOG / 3;
+  constexpr int REM = LOG - 3 * N8;
+  constexpr int BPT8 = (NSEQ * (G / 8) + NT - 1) / NT;
+  int Ns = 1;
+#pragma unroll
+  for (int p = 0; p < N8; ++p) {
+    stockham_pass<G, 8, BPT8>(x, NSEQ, Ns, tw);
+    Ns *= 8;
+  }
+  if constexpr (REM == 2) {
+    constexpr int BPT4 = (NSEQ * (G / 4) + NT - 1) / NT;
+    stockham_pass<G, 4, BPT4>(x, NSEQ, Ns, tw);
+    Ns *= 4;
+  } else if constexpr (REM == 1) {
+    constexpr int BPT2 = (NSEQ * (G / 2) + NT - 1) / NT;
+    stockham_pass<G, 2, BPT2>(x, NSEQ, Ns, tw);
+    Ns *= 2;
+  }
+  if constexpr (F > 1) {
+    constexpr int BPTF = (NSEQ * (G / F) + NT - 1) / NT;
+    stockham_pass<G, F, BPTF>(x, NSEQ, Ns, tw);
+  }
+}
+
+__device__ __forceinline__ int row_limit(const double* snap, int G) {
+  const int r = (int)ceil(snap[SNAP_ROWMAX]);
+  return r < G / 2 ? r : G / 2 - 1;
+}
+
+template <int G>
+struct RowCfg {
+  static constexpr int NT = (G / 8 < 64) ? 64 : (G / 8 > 512 ? 512 : G / 8);
+};
+
+template <int G>
+__device__ __forceinline__ void fft_rows_body(float2* __restrict__ H, int N,
+                                              const float2* __restrict__ tw,
+                                              const double* __restrict__ snap,
+                                              float2* __restrict__ T, int row) {
+  extern __shared__ float2 x[];
+  if (row > row_limit(snap, G)) return;
+  float2* src = H + (size_t)row * G;
+  constexpr int PER = (G + RowCfg<G>::NT - 1) / RowCfg<G>::NT;
+  float2 v[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {   // all loads first, then the stores
+    const int n = threadIdx.x + u * RowCfg<G>::NT;
+    v[u] = n < G ? src[n] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int n = threadIdx.x + u * RowCfg<G>::NT;
+    if (n < G) x[pad(n)] = v[u];
+  }
+  __syncthreads();
+  fft_smem<G, 1, RowCfg<G>::NT>(x, tw);
+  float2* dst = T + (size_t)row * N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const int jp = j - N / 2;
+    float2 v = x[pad(jp < 0 ? jp + G : jp)];
+    if (jp & 1) { v.x = -v.x; v.y = -v.y; }
+    dst[j] = v;
+  }
+  // leave the grid slot cleared for the next gridding
+  for (int n = threadIdx.x; n < G; n += blockDim.x) src[n] = make_float2(0.f, 0.f);
+}
+
+template <int G>
+__global__ void __launch_bounds__(RowCfg<G>::NT)
+fft_rows_kernel(float2* __restrict__ H, int N, const float2* __restrict__ tw,
+                const double* __restrict__ snap, float2* __restrict__ T) {
+  fft_rows_body<G>(H, N, tw, snap, T, blockIdx.x);
+}
+
+template <int G>
+__global__ void __launch_bounds__(RowCfg<G>::NT)
+fft_rows_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
+               const float2* __restrict__ tw) {
+  if ((int)blockIdx.y >= hdr->n) return;
+  const BatchEntry& e = E[blockIdx.y];
+  fft_rows_body<G>(e.grid, N, tw, e.snap, e.fft_tmp, blockIdx.x);
+}
+
+template <int G>
+struct ColCfg {
+  // two real columns per complex transform; two transforms per block while
+  // both fit in shared memory (G <= 8192), one beyond
+  static constexpr int NSEQ = G <= 8192 ? 2 : 1;
+  static constexpr int CW = 2 * NSEQ;     // columns per block
+  static constexpr int NT = 512;
+  static constexpr int LEN = G + G / 8;
+};
+
+template <int G>
+__device__ __forceinline__ void fft_cols_body(const float2* __restrict__ T, int N,
+                                              const float2* __restrict__ tw,
+                                              const float* __restrict__ corr,
+                                              const double* __restrict__ snap,
+                                              float* __restrict__ out, int blk) {
+  constexpr int CW = ColCfg<G>::CW, LEN = ColCfg<G>::LEN, NSEQ = ColCfg<G>::NSEQ;
+  extern __shared__ float2 x[];
+  const int col0 = blk * CW;
+  constexpr int half = G / 2;
+  const int rmax = row_limit(snap, G);
+  // all of a thread's loads first (one memory latency per block), then the
+  // shared-memory stores
+  constexpr int NT = ColCfg<G>::NT, ITEMS = half * NSEQ;
+  constexpr int PER = (ITEMS + NT - 1) / NT;
+  float4 ld[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int e = threadIdx.x + u * NT;
+    const int r = e / NSEQ, pr = e - r * NSEQ;   // row, column pair
+    ld[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e < ITEMS && r <= rmax)
+      ld[u] = *reinterpret_cast<const float4*>(T + (size_t)r * N + col0 + 2 * pr);
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int e = threadIdx.x + u * NT;
+    if (e >= ITEMS) break;
+    const int r = e / NSEQ, pr = e - r * NSEQ;
+    float2* xs = x + (size_t)pr * LEN;
+    const float2 a = make_float2(ld[u].x, ld[u].y), b = make_float2(ld[u].z, ld[u].w);
+    // Z[r] = U_a[r] + i U_b[r];  Z[-r] = conj(U_a[r]) + i conj(U_b[r])
+    xs[pad(r)] = make_float2(a.x - b.y, a.y + b.x);
+    if (r > 0) xs[pad(G - r)] = make_float2(a.x + b.y, b.x - a.y);
+    else xs[pad(half)] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_smem<G, NSEQ, ColCfg<G>::NT>(x, tw);
+  const double omega = snap[SNAP_OMEGA], sumw = snap[SNAP_SUMW];
+  const float norm = sumw > 0.0 ? (float)(0.5 / (omega * sumw)) : 0.f;
+  if constexpr (NSEQ == 2) {
+    const float ca = corr[col0], cb = corr[col0 + 1], cc = corr[col0 + 2], cd = corr[col0 + 3];
+    for (int j2 = threadIdx.x; j2 < N; j2 += blockDim.x) {
+      const int jp = j2 - N / 2;
+      const int m = pad(jp < 0 ? jp + G : jp);
+      const float2 z0 = x[m], z1 = x[LEN + m];
+      const float s = norm * corr[j2];
+      float4 o;
+      o.x = z0.x * (s * ca);
+      o.y = z0.y * (s * cb);
+      o.z = z1.x * (s * cc);
+      o.w = z1.y * (s * cd);
+      *reinterpret_cast<float4*>(out + (size_t)j2 * N + col0) = o;
+    }
+  } else {
+    const float ca = corr[col0], cb = corr[col0 + 1];
+    for (int j2 = threadIdx.x; j2 < N; j2 += blockDim.x) {
+      const int jp = j2 - N / 2;
+      const float2 z0 = x[pad(jp < 0 ? jp + G : jp)];
+      const float s = norm * corr[j2];
+      *reinterpret_cast<float2*>(out + (size_t)j2 * N + col0) =
+          make_float2(z0.x * (s * ca), z0.y * (s * cb));
+    }
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(ColCfg<G>::NT)
+fft_cols_kernel(const float2* __restrict__ T, int N, const float2* __restrict__ tw,
+                const float* __restrict__ corr, const double* __restrict__ snap,
+                float* __restrict__ out) {
+  fft_cols_body<G>(T, N, tw, corr, snap, out, blockIdx.x);
+}
+
+template <int G>
+__global__ void __launch_bounds__(ColCfg<G>::NT)
+fft_cols_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
+               const float2* __restrict__ tw, const float* __restrict__ corr) {
+  if ((int)blockIdx.y >= hdr->n) return;
+  const BatchEntry& e = E[blockIdx.y];
+  fft_cols_body<G>(e.fft_tmp, N, tw, corr, e.snap, e.tilted, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint passes (toi_degrid_backward).  The sample cotangents need
+//   Hbar[k'] = sum_j' U[j'] e^{-2 pi i (k1' j1' + k2' j2') / G}
+// for rows k2' = 0..R, U the real N x N cotangent (already scaled by the grid
+// correction and 1/(omega sum w)); rows k2' < 0 are conj(Hbar[-k']).  Both
+// passes run the same e^{+} transform core and use that U is real:
+//   pass A (columns, along j2'): Y[k2', j1'] = sum_j2' U e^{+2 pi i k2' j2' / G},
+//       two real columns per complex transform (Z = U_a + i U_b, then
+//       Y_a[k] = (Z[k] + conj Z[-k]) / 2, Y_b[k] = (Z[k] - conj Z[-k]) / 2i);
+//   pass B (rows, along j1'): K[k2', n] = sum_j1' (-1)^j1' Y[k2', j1'] e^{+2 pi i n j1' / G},
+//       n = k1' + G/2, so that Hbar[k2', n] = conj(K[k2', n]).
+// They are the adjoints of pass 2 and pass 1 of the image, with the same row
+// pruning.
+
+template <int G>
+__global__ void __launch_bounds__(ColCfg<G>::NT)
+fft_adj_cols_kernel(const float* __restrict__ U, int N, const float2* __restrict__ tw,
+                    const double* __restrict__ snap, float2* __restrict__ Y) {
+  constexpr int CW = ColCfg<G>::CW, LEN = ColCfg<G>::LEN, NSEQ = ColCfg<G>::NSEQ;
+  extern __shared__ float2 x[];
+  const int col0 = blockIdx.x * CW;
+  const int rmax = row_limit(snap, G);
+  for (int e = threadIdx.x; e < NSEQ * LEN; e += blockDim.x) x[e] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int j2 = threadIdx.x; j2 < N; j2 += blockDim.x) {
+    const int jp = j2 - N / 2;
+    const int m = pad(jp < 0 ? jp + G : jp);
+    if constexpr (NSEQ == 2) {
+      const float4 u = *reinterpret_cast<const float4*>(U + (size_t)j2 * N + col0);
+      x[m] = make_float2(u.x, u.y);          // columns col0, col0 + 1
+      x[LEN + m] = make_float2(u.z, u.w);    // columns col0 + 2, col0 + 3
+    } else {
+      x[m] = *reinterpret_cast<const float2*>(U + (size_t)j2 * N + col0);
+    }
+  }
+  __syncthreads();
+  fft_smem<G, NSEQ, ColCfg<G>::NT>(x, tw);
+  for (int e = threadIdx.x; e < (rmax + 1) * NSEQ; e += blockDim.x) {
+    const int r = e / NSEQ, pr = e - (e / NSEQ) * NSEQ;
+    const float2* xs = x + (size_t)pr * LEN;
+    const float2 z = xs[pad(r)], zm = xs[pad(r == 0 ? 0 : G - r)];
+    const float4 o = make_float4(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y),
+                                 0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+    *reinterpret_cast<float4*>(Y + (size_t)r * N + col0 + 2 * pr) = o;
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(RowCfg<G>::NT)
+fft_adj_rows_kernel(const float2* __restrict__ Y, int N, const float2* __restrict__ tw,
+                    const double* __restrict__ snap, float2* __restrict__ K) {
+  extern __shared__ float2 x[];
+  const int row = blockIdx.x;
+  if (row > row_limit(snap, G)) return;
+  for (int n = threadIdx.x; n < G; n += blockDim.x) x[pad(n)] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const float2* src = Y + (size_t)row * N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const int jp = j - N / 2;
+    float2 v = src[j];
+    if (jp & 1) { v.x = -v.x; v.y = -v.y; }
+    x[pad(jp < 0 ? jp + G : jp)] = v;
+  }
+  __syncthreads();
+  fft_smem<G, 1, RowCfg<G>::NT>(x, tw);
+  float2* dst = K + (size_t)row * G;
+  for (int n = threadIdx.x; n < G; n += blockDim.x) dst[n] = x[pad(n)];
+}
+
+template <int G>
+cudaError_t configure_g() {
+  const int row_smem = (G + G / 8) * (int)sizeof(float2);
+  const int col_smem = ColCfg<G>::NSEQ * ColCfg<G>::LEN * (int)sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       row_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_cols_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_adj_rows_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             row_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_adj_cols_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             col_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_rows_batch<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_cols_batch<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+  return e;
+}
+
+template <int G>
+void launch_batch_g(toi_plan_s* p) {
+  const int N = p->N, B = p->batch_max;
+  constexpr int CW = ColCfg<G>::CW;
+  int tok = prof_begin(p, PROF_FFT_ROWS, 1);
+  fft_rows_batch<G><<<dim3(G / 2, B), RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
+      p->bentry_dev, p->bheader_dev, N, p->twiddle);
+  prof_end(p, tok);
+  tok = prof_begin(p, PROF_FFT_COLS, 1);
+  fft_cols_batch<G><<<dim3(N / CW, B), ColCfg<G>::NT, ColCfg<G>::NSEQ * ColCfg<G>::LEN * sizeof(float2),
+                      p->stream>>>(p->bentry_dev, p->bheader_dev, N, p->twiddle, p->corr);
+  prof_end(p, tok);
+}
+
+template <int G>
+void launch_adj_g(toi_plan_s* p, Slot& s) {
+  const int N = p->N;
+  constexpr int CW = ColCfg<G>::CW;
+  fft_adj_cols_kernel<G><<<N / CW, ColCfg<G>::NT, ColCfg<G>::NSEQ * ColCfg<G>::LEN * sizeof(float2), p->stream>>>(
+      p->tilted, N, p->twiddle, s.snap, p->fft_tmp);
+  fft_adj_rows_kernel<G><<<G / 2, RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
+      p->fft_tmp, N, p->twiddle, s.snap, s.grid);
+}
+
+template <int G>
+void launch_g(toi_plan_s* p, Slot& s, float* out) {
+  const int N = p->N;
+  int tok = prof_begin(p, PROF_FFT_ROWS, 1);
+  fft_rows_kernel<G><<<G / 2, RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
+      s.grid, N, p->twiddle, s.snap, p->fft_tmp);
+  prof_end(p, tok);
+  tok = prof_begin(p, PROF_FFT_COLS, 1);
+  constexpr int CW = ColCfg<G>::CW;
+  fft_cols_kernel<G><<<N / CW, ColCfg<G>::NT, ColCfg<G>::NSEQ * ColCfg<G>::LEN * sizeof(float2), p->stream>>>(
+      p->fft_tmp, N, p->twiddle, p->corr, s.snap, out);
+  prof_end(p, tok);
+}
+
+template <int G>
+cudaError_t run_g(toi_plan_s* p, FftOp op, Slot* s, float* out) {
+  switch (op) {
+    case FFT_FORWARD: launch_g<G>(p, *s, out); break;
+    case FFT_BATCH: launch_batch_g<G>(p); break;
+    case FFT_ADJOINT: launch_adj_g<G>(p, *s); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// One translation unit per transform-length family (2^a, 3 2^a, 5 2^a):
+// each returns cudaErrorInvalidValue for a length outside its family.
+cudaError_t fft_configure_pow2(int G);
+cudaError_t fft_run_pow2(toi_plan_s* p, FftOp op, Slot* s, float* out);
+cudaError_t fft_configure_r3(int G);
+cudaError_t fft_run_r3(toi_plan_s* p, FftOp op, Slot* s, float* out);
+cudaError_t fft_configure_r5(int G);
+cudaError_t fft_run_r5(toi_plan_s* p, FftOp op, Slot* s, float* out);
+
+}  // namespace toi

@@ -216,14 +216,15 @@ def tiny_workload() -> Workload:
 
 
 def meerkat_workload(n_snap: int = 1500, n_chan: int = 4096,
-                     image_size: int = 2048) -> Workload:
+                     image_size: int = 2048, cell_arcsec: float = 2.0) -> Workload:
     """64-antenna MeerKAT-like array (dense core, arms to 4 km radius), 2016
     baselines, 4096 channels 856-1712 MHz, 4 linear pols, 8 s dumps,
     2048x2048 pixels of 2 arcsec; 10 steady power-law sources (0.1-10 Jy),
-    a 1 Jy pulsar on for 20 of every 40 snapshots; 5% flags."""
+    a 1 Jy pulsar on for 20 of every 40 snapshots; 5% flags.  Other image
+    sizes and cells keep the sources inside their own field of view."""
     w = Workload(f"meerkat-64ant-{n_chan}ch-{image_size}px", n_ant=64,
                  layout="meerkat", n_chan=n_chan, f_lo_hz=856e6, f_hi_hz=1712e6,
-                 n_pol=4, n_snap=n_snap, image_size=image_size, cell_arcsec=2.0,
+                 n_pol=4, n_snap=n_snap, image_size=image_size, cell_arcsec=cell_arcsec,
                  noise_sigma=0.1, flag_frac=0.05)
     src = steady_sources(10, 0.1, 10.0, w.fov_rad, w.seed_sky, powerlaw=True)
     l, m = random_position(w.fov_rad, w.seed_sky + 100)

@@ -92,6 +92,9 @@ def test_uneven_batches_match_oracle():
 
 
 def test_batch_equals_single_path():
+    """Images to 1e-6 (the two gridders sum in different orders); tLISI to
+    5e-5: it is made from differences of consecutive images, about a tenth
+    of their peak, so the images' float32 rounding weighs ~10x more there."""
     base, snaps = _stream(6, seed=9)
     N = base.image_size
     nt = N // T_TILE
@@ -114,7 +117,7 @@ def test_batch_equals_single_path():
         a = d["image"].cpu().numpy()
         assert rel_err(a, out_single[i]) < 1e-6
         if tl_single[i] is not None:
-            assert np.abs(rows[i].cpu().numpy() - tl_single[i]).max() < 1e-5
+            assert np.abs(rows[i].cpu().numpy() - tl_single[i]).max() < 5e-5
     plan.close()
 
 

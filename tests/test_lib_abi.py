@@ -41,6 +41,11 @@ def test_host_validation_without_gpu(libtoi):
     L = libtoi.lib()
     h = C.c_void_p()
     cases = [((100, 2.0, 10, 10, 4), libtoi.TOI_ERR_UNSUPPORTED),
+             ((112, 2.0, 10, 10, 4), libtoi.TOI_ERR_UNSUPPORTED),     # 7 x 16
+             ((16384, 1.0, 10, 10, 4), libtoi.TOI_ERR_UNSUPPORTED),   # above 8192
+             ((12288, 1.0, 10, 10, 4), libtoi.TOI_ERR_UNSUPPORTED),   # 3 x 2^12 > 6144
+             ((20480, 1.0, 10, 10, 4), libtoi.TOI_ERR_UNSUPPORTED),   # above 10240
+             ((48, 2.0, 10, 10, 4), libtoi.TOI_ERR_ARG),              # below 64
              ((32, 2.0, 10, 10, 4), libtoi.TOI_ERR_ARG),
              ((128, -1.0, 10, 10, 4), libtoi.TOI_ERR_ARG),
              ((128, 2.0, 0, 10, 4), libtoi.TOI_ERR_ARG),
