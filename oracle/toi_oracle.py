@@ -24,6 +24,8 @@ It is a plain, slow, step-by-step restatement of the method in float64:
                              of the same order reproduces it bit for bit.
   3-D mode  Section 3.4, App. B, Table 2: t3 on the sphere, slabs,
                              Chebyshev moments (Jacobi-Anger), the order rule
+  localisation              windowed point-source model, loss and its exact
+                             gradients (candidate windows of Section 6)
   adjoint                   reverse mode of S2..S6 (Section 1 names the
                              adjoint route to gradients): bilinear transpose,
                              correction, forward DFT, ES degridding (the
@@ -47,6 +49,10 @@ Parity status per function (pins live in tests/):
   *_adjoint, point_source_gradient: pinned by the adjoint identity
     <A x, y> = <x, A^T y> against the forward routines, central finite
     differences of the forward, and the brute-force DFT adjoint.
+  window_*, source_of_pixel, localise: pinned by central finite differences
+    of the loss (l, m, S and weights), a zero loss and gradient at the true
+    source, the coplanar peak S / omega at the pixel source_of_pixel names,
+    the window transpose identity and the gridded full image on the window.
 """
 from __future__ import annotations
 
@@ -543,6 +549,116 @@ def point_source_gradient(uvw_m, freq_hz, grad_vis, l: float, m: float, flux: fl
     return dict(l=float((np.conj(gsum) * dl).real.sum()),
                 m=float((np.conj(gsum) * dm).real.sum()),
                 flux=float((np.conj(gsum) * v).real.sum()))
+
+
+# ==========================================================================
+# Windowed point-source localisation (Section 1's adjoint route to gradients,
+# applied to sub-pixel positions of candidates, Section 6)
+# ==========================================================================
+#
+# A candidate window is a LOC_WINDOW x LOC_WINDOW block of the tilted-plane
+# image with corner (row j2c, column j1c).  Its model is the 2-D dirty image
+# of Section 3.2 of one point source (l, m, S) (point_source_vis, with the
+# data's flags and weights), restricted to the window.  The loss of a window
+# is the squared residual between the data's tilted image and the model,
+# summed over its pixels; the total loss sums the windows.  Every image value
+# here is the exact brute-force sum (dirty_image_dft), not the gridded one.
+
+LOC_WINDOW = 32
+
+
+def window_axes(corner, size: int = LOC_WINDOW):
+    """Rows and columns (0-based) of the window with corner (j2c, j1c)."""
+    j2c, j1c = int(corner[0]), int(corner[1])
+    return np.arange(j2c, j2c + size), np.arange(j1c, j1c + size)
+
+
+def window_image_exact(p: Dict, N: int, cell_arcsec: float, corner,
+                       size: int = LOC_WINDOW) -> np.ndarray:
+    """The Section 3.2 dirty image of prepare()'s samples on one window."""
+    rows, cols = window_axes(corner, size)
+    return dirty_image_dft(p["r"][:, 0], p["r"][:, 1], p["c"], N, cell_arcsec, p["omega"],
+                           p["sumw"], rows, cols)
+
+
+def window_adjoint_exact(p: Dict, N: int, cell_arcsec: float, corner,
+                         grad_window: np.ndarray) -> np.ndarray:
+    """dL/dc_q (the complex convention above) of a loss whose cotangent on the
+    window's image is grad_window:
+        1/(omega sum w) sum_j g_j exp(-2 pi i (r1 t1_j + r2 t2_j)),
+    the transpose of window_image_exact (the image is Re of the sum)."""
+    size = grad_window.shape[0]
+    rows, cols = window_axes(corner, size)
+    beta = cell_arcsec * ARCSEC
+    t1 = -beta * (cols - N // 2)
+    t2 = beta * (rows - N // 2)
+    e1 = np.exp(-2j * np.pi * np.outer(p["r"][:, 0], t1))     # [q, cols]
+    e2 = np.exp(-2j * np.pi * np.outer(p["r"][:, 1], t2))     # [q, rows]
+    return np.einsum("qb,ba,qa->q", e2, grad_window, e1) / (p["omega"] * p["sumw"])
+
+
+def source_of_pixel(t1: float, t2: float, V: np.ndarray) -> Tuple[float, float]:
+    """(l, m) of the point source whose 2-D image peaks at tilted-plane
+    position (t1, t2): its phase b.(s - z) equals r.tau with tau = V (s - z),
+    so s = V^T tau + z with tau3 the root of |s| = 1 nearest 0 (the t3 of
+    App. B with t = tau)."""
+    tau = np.array([t1, t2, float(t3_of(t1, t2, V))])
+    s = V.T @ tau + np.array([0.0, 0.0, 1.0])
+    return float(s[0]), float(s[1])
+
+
+def localise(uvw_m, freq_hz, vis, flag, weight, N: int, cell_arcsec: float, windows,
+             sources, size: int = LOC_WINDOW) -> Dict:
+    """Loss, models and gradients of the windowed point-source fit.
+    windows: [n_win, 2] corners (j2c, j1c); sources: [n_win, 3] (l, m, S).
+    For window w with data image D and model M (both exact):
+      L_w = sum (D - M)^2;  g^M = dL/dM = -2 (D - M);  g^D = -g^M;
+      grad_src[w]  = d L / d(l, m, S) through point_source_gradient of
+                     grad_vis = w_p dL/dc^M_q (the model's sample values);
+      grad_weight[p] = sum_w Re(conj(dL/dc^M) V^M_p) + Re(conj(dL/dc^D) V_p)
+                       - (<g^M, M> + <g^D, D>) / sum w
+                     on the unflagged parallel hands of selected samples
+                     (c = w_a V_a + w_b V_b is linear in w_p and both images
+                     carry 1 / sum w), else 0."""
+    vis = np.asarray(vis)
+    nbl, nch, n_pol = vis.shape
+    windows = np.asarray(windows, dtype=np.int64).reshape(-1, 2)
+    sources = np.asarray(sources, dtype=np.float64).reshape(-1, 3)
+    pd = prepare(uvw_m, freq_hz, vis, flag, weight)
+    pa, pb = parallel_hands(n_pol)
+    f = np.asarray(flag).astype(bool)
+    wp = np.where(f, 0.0, 1.0 if weight is None else np.asarray(weight, dtype=np.float64))
+    sel = pd["sel"]
+    loss = np.zeros(len(windows))
+    models = np.zeros((len(windows), size, size))
+    data = np.zeros((len(windows), size, size))
+    grad_src = np.zeros((len(windows), 3))
+    grad_weight = np.zeros(vis.shape)
+    for i, (corner, (l, m, S)) in enumerate(zip(windows, sources)):
+        vm = point_source_vis(uvw_m, freq_hz, n_pol, l, m, S)
+        pm = prepare(uvw_m, freq_hz, vm, flag, weight)
+        D = window_image_exact(pd, N, cell_arcsec, corner, size)
+        M = window_image_exact(pm, N, cell_arcsec, corner, size)
+        R = D - M
+        loss[i] = float((R * R).sum())
+        models[i], data[i] = M, D
+        gM = -2.0 * R
+        gq_m = np.zeros((nbl, nch), dtype=np.complex128)
+        gq_m[sel] = window_adjoint_exact(pm, N, cell_arcsec, corner, gM)
+        gq_d = -gq_m                       # the data's cotangent is -g^M
+        grad_vis = np.zeros(vis.shape, dtype=np.complex128)
+        for p in sorted({pa, pb}):
+            grad_vis[:, :, p] = np.where(sel, wp[:, :, p] * gq_m, 0.0)
+        gs = point_source_gradient(uvw_m, freq_hz, grad_vis, l, m, S)
+        grad_src[i] = (gs["l"], gs["m"], gs["flux"])
+        dot = float((gM * M).sum() + (-gM * D).sum())
+        for p in sorted({pa, pb}):
+            use = sel & ~f[:, :, p]
+            gw = ((np.conj(gq_m) * vm[:, :, p]).real +
+                  (np.conj(gq_d) * vis[:, :, p].astype(np.complex128)).real - dot / pd["sumw"])
+            grad_weight[:, :, p] += np.where(use, gw, 0.0)
+    return dict(loss=loss, model=models, data=data, grad_src=grad_src,
+                grad_weight=grad_weight, V=pd["V"], omega=pd["omega"], sumw=pd["sumw"])
 
 
 # ==========================================================================
