@@ -59,8 +59,10 @@ typedef enum { TOI_VIS_C64 = 0, TOI_VIS_C16_CHANSCALE = 1 } toi_vis_dtype;
 typedef enum { TOI_CAND_PERIODIC = 0, TOI_CAND_NONPERIODIC = 1 } toi_cand_mode;
 
 typedef struct {
-  int32_t image_size;       /* N: power of two, 64 <= N <= 8192 (Section 2:
-                               user-supplied image size)                        */
+  int32_t image_size;       /* N (Section 2: user-supplied image size): 2^a
+                               (64 ... 8192), 3 2^a (96 ... 6144) or 5 2^a
+                               (160 ... 10240), the paper's sweep 2048 ...
+                               10240 included                                  */
   double  cell_arcsec;      /* beta, pixel size in arcseconds (> 0)             */
   int32_t max_baselines;    /* largest n_bl a call may pass                     */
   int32_t max_channels;     /* largest n_ch a call may pass                     */
@@ -87,6 +89,9 @@ typedef struct {
                                automatic (or as tuned), 8 (one lane per
                                channel run) or 4 (two lanes per run); a tuning
                                knob like grid_run                              */
+  int32_t max_windows;      /* largest n_win of toi_localise (0 = none,
+                               default; at most 256); 64 KiB of facet grids
+                               and a table of 16 B per baseline per window     */
   int32_t reserved[1];      /* must be zero                                     */
 } toi_config;
 
@@ -327,6 +332,59 @@ toi_status toi_degrid_backward(toi_plan_t plan, int32_t slot, const float* grad_
                                const float* image, void* grad_sample, void* grad_vis,
                                float* grad_weight);
 
+/* Side of a localisation window (pixels of the tilted-plane image). */
+#define TOI_LOC_WINDOW 32
+
+/* Candidate windows of one snapshot from its tLISI matrix (the sub-pixel
+ * localisation of candidates, Sections 2 and 6): the n_win tiles with the
+ * smallest tLISI (ties by tile index; NaN last) each give a TOI_LOC_WINDOW^2
+ * window of the tilted-plane image centred on the tile (clamped to the
+ * image), and a starting source at the window's largest pixel: with
+ * tau = (t1, t2) of that pixel (t1 = -beta (j1 - N/2), t2 = beta (j2 - N/2))
+ * and tau3 the root of |V^T tau + z| = 1 nearest 0, (l, m) = the first two
+ * components of V^T tau and S = omega x the pixel value (the peak of an
+ * unresolved source in the 2-D image is S / omega).
+ *   tlisi  dev float32 [N/T][N/T], e.g. the row tlisi_update wrote.
+ *   win    dev int32 [n_win][2] out: window corners (row j2c, column j1c).
+ *   src    dev float64 [n_win][3] out: (l, m, S).
+ * The slot's plane fit and the plan's tilted image must be this snapshot's
+ * (toi_image(slot) was the last image call).  1 <= n_win <= max_windows and
+ * (N/T)^2 <= 2048 floor(4096 / n_win) (TOI_ERR_UNSUPPORTED otherwise).
+ * Asynchronous.  Errors: TOI_ERR_ARG, TOI_ERR_UNSUPPORTED, TOI_ERR_CUDA. */
+toi_status toi_localise_seed(toi_plan_t plan, int32_t slot, const float* tlisi, int32_t n_win,
+                             int32_t* win, double* src);
+
+/* Windowed point-source fit of one snapshot: loss and gradients (the
+ * differentiable localisation that Section 1's adjoint route permits).
+ * Window w is the TOI_LOC_WINDOW^2 block of the tilted-plane image with
+ * corner win[w]; its model M_w is the 2-D dirty image (Section 3.2) of one
+ * point source (l, m, S) = src[w], V_p = S exp(-2 pi i k (u l + v m +
+ * w (n - 1))) in the parallel hands (Section 1), with the snapshot's flags
+ * and weights.  The model is made by faceted gridding: the samples rotated
+ * to the window centre and gridded on a 2 TOI_LOC_WINDOW grid over the full
+ * uv extent, so it equals the full image of the model on the window to the
+ * ES kernel's accuracy.  With D the tilted image on the window:
+ *   loss[w]        = sum (D - M_w)^2           (dev float64 [n_win], or NULL)
+ *   model          = M_w                        (dev float32 [n_win][32][32], or NULL)
+ *   grad_src[w]    = dL/d(l, m, S), L = sum_w loss[w]  (dev float64 [n_win][3], or NULL)
+ *   grad_weight[p] = dL/dw_p for the unflagged parallel hands of selected
+ *                    samples (both D and every M_w depend on the weights,
+ *                    through c_q and 1 / sum w), else 0
+ *                                               (dev float32 [n_bl][n_ch][n_pol], or NULL)
+ * The plane fit (V, omega, the selection) is held fixed, as in
+ * toi_degrid_backward.  Reads the inputs of the last toi_grid on `slot`
+ * again (they must still hold the same data) and the plan's tilted image,
+ * which must be this snapshot's (toi_image(slot) was the last image call).
+ * With grad_weight the tilted image, the FFT scratch and the slot's grid are
+ * used as workspace (the tilted image is not this snapshot's afterwards).
+ * 1 <= n_win <= max_windows.  2-D mode only.  Asynchronous; a window off the
+ * image or a source with l^2 + m^2 >= 1 gets zero loss and gradients and
+ * latches TOI_ERR_RANGE (toi_sync_status).  Errors: TOI_ERR_ARG,
+ * TOI_ERR_UNSUPPORTED, TOI_ERR_CUDA. */
+toi_status toi_localise(toi_plan_t plan, int32_t slot, int32_t n_win, const int32_t* win,
+                        const double* src, float* model, double* loss, double* grad_src,
+                        float* grad_weight);
+
 /* Copy of a plan-owned buffer, for checking intermediate stages:
  * which = 0 grid slot `slot` (complex float32 [G/2][G], the Hermitian
  * half-plane grid, rows k2' = 0..G/2-1, columns k1 = 0..G-1), 1 tilted-plane
@@ -342,7 +400,8 @@ toi_status toi_plan_buffer(toi_plan_t plan, int32_t which, int32_t slot, void* d
  * recorded on the plan's stream around each stage's kernels.  Stages:
  * 0 plane fit (4 kernels), 1 reserved (always 0), 2 gridding, 3 FFT rows,
  * 4 FFT columns + correction, 5 re-projection + tLISI moments, 6 tLISI
- * finish / external-image moments, 7 toi_degrid_backward.  toi_batch_run's
+ * finish / external-image moments, 7 toi_degrid_backward, 8 toi_localise and
+ * toi_localise_seed.  toi_batch_run's
  * kernels count under the same stages (one launch per stage per batch).
  * Kernel launches are counted per stage whether or not timing is enabled. */
 toi_status toi_profile_enable(toi_plan_t plan, int32_t enable);

@@ -594,7 +594,7 @@ def window_adjoint_exact(p: Dict, N: int, cell_arcsec: float, corner,
     t2 = beta * (rows - N // 2)
     e1 = np.exp(-2j * np.pi * np.outer(p["r"][:, 0], t1))     # [q, cols]
     e2 = np.exp(-2j * np.pi * np.outer(p["r"][:, 1], t2))     # [q, rows]
-    return np.einsum("qb,ba,qa->q", e2, grad_window, e1) / (p["omega"] * p["sumw"])
+    return ((e2 @ grad_window) * e1).sum(axis=1) / (p["omega"] * p["sumw"])
 
 
 def source_of_pixel(t1: float, t2: float, V: np.ndarray) -> Tuple[float, float]:

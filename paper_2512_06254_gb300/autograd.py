@@ -49,3 +49,34 @@ def image_snapshot(plan, uvw, freq, vis, flag=None, weight=None, slot: int = 0):
     respect to vis (complex64 [n_bl, n_ch, n_pol]) and weight (float32, same
     shape, or None for unit weights)."""
     return _ImageSnapshot.apply(vis, weight, plan, uvw, freq, flag, slot)
+
+
+class _Localise(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, src, weight, plan, win, slot):
+        n = win.shape[0]
+        dev = src.device
+        loss = torch.empty(n, dtype=torch.float64, device=dev)
+        need_src, need_w = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        gsrc = torch.empty(n, 3, dtype=torch.float64, device=dev) if need_src else None
+        gw = torch.empty_like(weight) if (need_w and weight is not None) else None
+        plan.localise(win, src.detach().contiguous(), loss=loss, grad_src=gsrc, grad_weight=gw,
+                      slot=slot)
+        ctx.save_for_backward(gsrc, gw)
+        return loss.sum()
+
+    @staticmethod
+    def backward(ctx, g):
+        gsrc, gw = ctx.saved_tensors
+        return (None if gsrc is None else g * gsrc, None if gw is None else g * gw.to(g.dtype),
+                None, None, None)
+
+
+def localise_loss(plan, win, src, weight=None, slot: int = 0):
+    """Sum over the windows of the squared residual between the snapshot's
+    tilted image and a point-source model (toi_localise), differentiable with
+    respect to src (float64 [n_win, 3]: l, m, S) and weight (the float32
+    weight tensor given to toi_grid for this slot, or None).  The gradients
+    are computed with the loss by the same call.  With weight requiring grad
+    the plan's tilted image is used as workspace (one call per image)."""
+    return _Localise.apply(src, weight, plan, win, slot)

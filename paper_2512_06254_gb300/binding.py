@@ -32,9 +32,12 @@ EXPORTS = ("toi_config_default", "toi_plan", "toi_plan_destroy", "toi_set_stream
            "toi_image", "tlisi_update", "tlisi_reset", "tlisi_candidates",
            "tlisi_candidates_noalloc",
            "toi_degrid_backward", "toi_batch_prepare", "toi_batch_run", "toi_batch",
-           "toi_autotune", "toi_mode3_info", "toi_plan_buffer", "toi_profile_enable", "toi_profile_read",
+           "toi_autotune", "toi_mode3_info", "toi_localise_seed", "toi_localise",
+           "toi_plan_buffer", "toi_profile_enable", "toi_profile_read",
            "toi_sync_status", "toi_last_error", "toi_status_string")
-PROF_STAGES = ("prep", "bin", "grid", "fft_rows", "fft_cols", "reproject", "tlisi", "backward")
+PROF_STAGES = ("prep", "bin", "grid", "fft_rows", "fft_cols", "reproject", "tlisi", "backward",
+               "localise")
+LOC_WINDOW = 32
 
 
 class ToiError(RuntimeError):
@@ -49,7 +52,8 @@ class toi_config(C.Structure):
                 ("n_pol", C.c_int32), ("vis_dtype", C.c_int32), ("kernel_support", C.c_int32),
                 ("oversample", C.c_int32), ("tlisi_tile", C.c_int32), ("grid_slots", C.c_int32),
                 ("grid_run", C.c_int32), ("batch_max", C.c_int32), ("mode", C.c_int32),
-                ("max_moments", C.c_int32), ("grid_rows", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("max_moments", C.c_int32), ("grid_rows", C.c_int32), ("max_windows", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class toi_snapshot(C.Structure):
@@ -88,6 +92,8 @@ def lib():
         "toi_batch": [P, P, I, P, C.POINTER(I)],
         "toi_autotune": [P, P, I, P, P],
         "toi_mode3_info": [P, I, P],
+        "toi_localise_seed": [P, I, P, I, P, P],
+        "toi_localise": [P, I, I, P, P, P, P, P, P],
         "toi_plan_buffer": [P, I, I, P, C.c_int64, C.POINTER(C.c_int64)],
         "toi_profile_enable": [P, I],
         "toi_profile_read": [P, P, P, I],
@@ -155,7 +161,8 @@ class Plan:
     def __init__(self, image_size: int, cell_arcsec: float, max_baselines: int,
                  max_channels: int, n_pol: int, *, vis_dtype: int = TOI_VIS_C64,
                  tlisi_tile: int = 32, grid_slots: int = 1, grid_run: int = 0, batch_max: int = 0,
-                 mode: int = 2, max_moments: int = 0, grid_rows: int = 0, stream=None):
+                 mode: int = 2, max_moments: int = 0, grid_rows: int = 0, max_windows: int = 0,
+                 stream=None):
         import torch
         self.cfg = config_default(image_size, cell_arcsec, max_baselines, max_channels, n_pol)
         self.cfg.vis_dtype = vis_dtype
@@ -166,6 +173,7 @@ class Plan:
         self.cfg.mode = mode
         self.cfg.max_moments = max_moments
         self.cfg.grid_rows = grid_rows
+        self.cfg.max_windows = max_windows
         self.N = image_size
         self.T = tlisi_tile
         h = C.c_void_p()
@@ -219,6 +227,30 @@ class Plan:
             self.handle, slot, _dev(grad_image, t.float32, "grad_image"),
             _dev(image, t.float32, "image"), _dev(grad_sample, t.complex64, "grad_sample"),
             _dev(grad_vis, t.complex64, "grad_vis"), _dev(grad_weight, t.float32, "grad_weight")),
+            self.handle)
+
+    # --------------------------------------------------------- localisation
+    def localise_seed(self, tlisi, n_win: int, win=None, src=None, slot: int = 0):
+        """toi_localise_seed: (win int32 [n_win, 2], src float64 [n_win, 3])
+        from a tLISI matrix of this slot's snapshot."""
+        t = self._torch
+        win = t.empty(n_win, 2, dtype=t.int32, device="cuda") if win is None else win
+        src = t.empty(n_win, 3, dtype=t.float64, device="cuda") if src is None else src
+        _check(lib().toi_localise_seed(self.handle, slot, _dev(tlisi, t.float32, "tlisi"), n_win,
+                                       _dev(win, t.int32, "win"), _dev(src, t.float64, "src")),
+               self.handle)
+        return win, src
+
+    def localise(self, win, src, model=None, loss=None, grad_src=None, grad_weight=None,
+                 slot: int = 0):
+        """toi_localise: fills the given outputs (float32 model [n_win, 32, 32],
+        float64 loss [n_win], float64 grad_src [n_win, 3], float32
+        grad_weight [n_bl, n_ch, n_pol])."""
+        t = self._torch
+        _check(lib().toi_localise(
+            self.handle, slot, win.shape[0], _dev(win, t.int32, "win"), _dev(src, t.float64, "src"),
+            _dev(model, t.float32, "model"), _dev(loss, t.float64, "loss"),
+            _dev(grad_src, t.float64, "grad_src"), _dev(grad_weight, t.float32, "grad_weight")),
             self.handle)
 
     # ---------------------------------------------------------------- batch

@@ -129,6 +129,9 @@ void free_plan(toi_plan_s* p) {
   cudaFree(p->adj_scratch);
   cudaFree(p->moments); cudaFree(p->m3_dev); cudaFree(p->m3_slabs); cudaFreeHost(p->m3_host);
   cudaFree(p->grid2);
+  cudaFree(p->loc_k); cudaFree(p->loc_coef); cudaFree(p->loc_win); cudaFree(p->loc_facets);
+  cudaFree(p->loc_K); cudaFree(p->loc_gD); cudaFree(p->loc_corr); cudaFree(p->loc_loss2);
+  cudaFree(p->loc_dot); cudaFree(p->loc_part); cudaFree(p->loc_keys); cudaFree(p->loc_tiles);
   if (p->bslots) {
     for (int i = 0; i < p->batch_max; ++i) {
       cudaFree(p->bslots[i].grid);
@@ -226,6 +229,8 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     return fail(nullptr, TOI_ERR_UNSUPPORTED, "the batched path is 2-D only (mode 3 with batch_max > 0)");
   if (!(c.grid_rows == 0 || c.grid_rows == 4 || c.grid_rows == 8))
     return fail(nullptr, TOI_ERR_ARG, "grid_rows must be 0, 4 or 8");
+  if (c.max_windows < 0 || c.max_windows > 256)
+    return fail(nullptr, TOI_ERR_ARG, "max_windows must be in [0, 256]");
   if (c.reserved[0] != 0) return fail(nullptr, TOI_ERR_ARG, "reserved fields must be zero");
   if ((long long)c.max_baselines * c.max_channels * c.n_pol > (1LL << 40))
     return fail(nullptr, TOI_ERR_ARG, "max_baselines x max_channels too large");
@@ -280,6 +285,22 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     e = cudaMallocHost((void**)&p->m3_host, sizeof(double) * 16);
     if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "near-coplanar host buffer"); free_plan(p); return r; }
   }
+  if (c.max_windows > 0) {
+    const size_t nw = (size_t)c.max_windows;
+    TOI_ALLOC(p->loc_k, (size_t)c.max_channels, "localisation channel table");
+    TOI_ALLOC(p->loc_coef, nw * c.max_baselines, "localisation coefficients");
+    TOI_ALLOC(p->loc_win, nw, "localisation windows");
+    TOI_ALLOC(p->loc_facets, nw * 64 * 64, "facet grids");
+    TOI_ALLOC(p->loc_K, nw * 64 * 64, "facet adjoints");
+    TOI_ALLOC(p->loc_gD, nw * TOI_LOC_WINDOW * TOI_LOC_WINDOW, "window cotangents");
+    TOI_ALLOC(p->loc_corr, (size_t)TOI_LOC_WINDOW, "facet correction");
+    TOI_ALLOC(p->loc_loss2, nw, "window losses");
+    TOI_ALLOC(p->loc_dot, 1, "localisation dot");
+    TOI_ALLOC(p->loc_part, toi::loc_part_doubles(c.max_baselines, c.max_channels, c.max_windows),
+              "localisation partial sums");
+    TOI_ALLOC(p->loc_keys, (size_t)4096, "window selection keys");
+    TOI_ALLOC(p->loc_tiles, nw, "selected tiles");
+  }
   p->batch_rows = c.grid_rows ? c.grid_rows : toi::grid_default_rows(true);
   p->batch_max = c.batch_max;
   if (p->batch_max > 0) {
@@ -331,6 +352,11 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   if (e == cudaSuccess) e = cudaMemcpy(p->corr, corr, sizeof(float) * N, cudaMemcpyHostToDevice);
   delete[] tw;
   delete[] corr;
+  if (e == cudaSuccess && p->loc_corr) {
+    float fc[TOI_LOC_WINDOW];
+    toi::es_fourier_table(TOI_LOC_WINDOW, 2 * TOI_LOC_WINDOW, p->W, p->beta_es, fc);
+    e = cudaMemcpy(p->loc_corr, fc, sizeof(fc), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->ring_max, 0, p->ring.size() * sizeof(unsigned int));
   for (size_t i = 0; i < p->ring.size() && e == cudaSuccess; ++i)
@@ -407,6 +433,7 @@ toi_status toi_grid(toi_plan_t p, const double* uvw_m, const double* freq_hz, co
   }
   s.uvw = uvw_m; s.freq = freq_hz; s.vis = vis; s.chan_scale = chan_scale;
   s.weight = weight; s.flag = flag; s.nbl = n_bl; s.nch = n_ch; s.valid = true;
+  if (p->tilted_slot == slot) p->tilted_slot = -1;   // the slot holds another snapshot now
   return TOI_OK;
 }
 
@@ -430,6 +457,7 @@ toi_status toi_image(toi_plan_t p, int32_t slot, float* image, double* snap_info
   p->nimg += 1;
   p->last_image = image ? image : p->ring[cur];
   p->fused_pending = true;
+  p->tilted_slot = p->cfg.mode == 3 ? -1 : slot;
   return TOI_OK;
 }
 
@@ -744,9 +772,63 @@ toi_status toi_degrid_backward(toi_plan_t p, int32_t slot, const float* grad_ima
   cudaError_t e = toi::launch_degrid_backward(p, s, grad_image, image,
                                               reinterpret_cast<float2*>(grad_sample),
                                               reinterpret_cast<float2*>(grad_vis), grad_weight);
-  // the adjoint used the slot's grid memory (and left it cleared)
+  // the adjoint used the slot's grid memory (and left it cleared) and the
+  // tilted image as workspace
   s.valid = false;
+  p->tilted_slot = -1;
   if (e != cudaSuccess) return cuda_fail(p, e, "toi_degrid_backward");
+  return TOI_OK;
+}
+
+static toi_status localise_checks(toi_plan_t p, int32_t slot, int32_t n_win) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  if (slot < 0 || slot >= p->nslot) return fail(p, TOI_ERR_ARG, "slot outside [0, grid_slots)");
+  if (p->cfg.mode == 3) return fail(p, TOI_ERR_UNSUPPORTED, "localisation is 2-D only");
+  if (p->cfg.max_windows < 1) return fail(p, TOI_ERR_ARG, "the plan has max_windows = 0");
+  if (n_win < 1 || n_win > p->cfg.max_windows)
+    return fail(p, TOI_ERR_ARG, "n_win must be in [1, max_windows]");
+  if (!p->slots[slot].uvw) return fail(p, TOI_ERR_ARG, "slot has not been gridded");
+  if (p->tilted_slot != slot)
+    return fail(p, TOI_ERR_ARG, "the tilted image is not this slot's (toi_image(slot) must be "
+                                "the last image call)");
+  return TOI_OK;
+}
+
+toi_status toi_localise_seed(toi_plan_t p, int32_t slot, const float* tlisi, int32_t n_win,
+                             int32_t* win, double* src) {
+  toi_status st = localise_checks(p, slot, n_win);
+  if (st != TOI_OK) return st;
+  if (!tlisi || !win || !src) return fail(p, TOI_ERR_ARG, "tlisi, win and src must be non-NULL");
+  if (!aligned(tlisi, 4) || !aligned(win, 4) || !aligned(src, 8))
+    return fail(p, TOI_ERR_ARG, "misaligned pointer (element alignment)");
+  const int nt = p->N / p->T;
+  if (nt * nt > toi::loc_seed_max_tiles(n_win))
+    return fail(p, TOI_ERR_UNSUPPORTED, "too many tLISI tiles for this many windows");
+  const int tok = toi::prof_begin(p, toi::PROF_LOCALISE, 3);
+  cudaError_t e = toi::launch_localise_seed(p, p->slots[slot], tlisi, n_win, win, src);
+  toi::prof_end(p, tok);
+  if (e != cudaSuccess) return cuda_fail(p, e, "toi_localise_seed");
+  return TOI_OK;
+}
+
+toi_status toi_localise(toi_plan_t p, int32_t slot, int32_t n_win, const int32_t* win,
+                        const double* src, float* model, double* loss, double* grad_src,
+                        float* grad_weight) {
+  toi_status st = localise_checks(p, slot, n_win);
+  if (st != TOI_OK) return st;
+  if (!win || !src) return fail(p, TOI_ERR_ARG, "win and src must be non-NULL");
+  if (!aligned(win, 4) || !aligned(src, 8) || !aligned(model, 4) || !aligned(loss, 8) ||
+      !aligned(grad_src, 8) || !aligned(grad_weight, 4))
+    return fail(p, TOI_ERR_ARG, "misaligned pointer (element alignment)");
+  Slot& s = p->slots[slot];
+  const int tok = toi::prof_begin(p, toi::PROF_LOCALISE, grad_weight ? 13 : 7);
+  cudaError_t e = toi::launch_localise(p, s, n_win, win, src, model, loss, grad_src, grad_weight);
+  toi::prof_end(p, tok);
+  if (grad_weight) {
+    s.valid = false;          // the grid memory held the adjoint (cleared again)
+    p->tilted_slot = -1;      // the tilted image held the cotangent
+  }
+  if (e != cudaSuccess) return cuda_fail(p, e, "toi_localise");
   return TOI_OK;
 }
 

@@ -220,4 +220,18 @@ cudaError_t launch_degrid_backward(toi_plan_s* p, Slot& s, const float* grad_ima
   return cudaGetLastError();
 }
 
+// The weight-gradient part of the reverse pass for a tilted-plane cotangent
+// already transformed into the slot's grid (launch_fft_adjoint): grad_weight
+// = Re(conj(g_q) V_p) - *dot / sum w on the unflagged parallel hands of
+// selected samples, 0 elsewhere; the grid rows are cleared afterwards.
+cudaError_t launch_degrid_weights(toi_plan_s* p, Slot& s, const double* dot, float* grad_weight) {
+  const dim3 grid((s.nch + kDegridThreads - 1) / kDegridThreads, s.nbl);
+  degrid_backward_kernel<<<grid, kDegridThreads, 0, p->stream>>>(
+      s.grid, p->G, s.coef, s.freq, s.vis, s.chan_scale,
+      p->cfg.vis_dtype == TOI_VIS_C16_CHANSCALE ? 1 : 0, s.weight, s.flag, s.nbl, s.nch,
+      p->cfg.n_pol, s.snap, dot, (float)p->beta_es, nullptr, nullptr, grad_weight);
+  clear_rows_kernel<<<p->G / 2, 256, 0, p->stream>>>(s.grid, p->G, s.snap);
+  return cudaGetLastError();
+}
+
 }  // namespace toi

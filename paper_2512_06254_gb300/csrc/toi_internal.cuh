@@ -118,7 +118,7 @@ struct BatchHeader {
 enum ProfStage {
   // PROF_BIN is reserved (the gridder needs no binning pass)
   PROF_PREP = 0, PROF_BIN, PROF_GRID, PROF_FFT_ROWS, PROF_FFT_COLS, PROF_REPROJECT,
-  PROF_TLISI, PROF_BACKWARD, PROF_NSTAGE
+  PROF_TLISI, PROF_BACKWARD, PROF_LOCALISE, PROF_NSTAGE
 };
 
 struct ProfState {
@@ -187,6 +187,21 @@ struct toi_plan_s {
   int grid_blocks = 0;                      // persistent gridder: resident blocks
   int tuned_run[4] = {0, 0, 0, 0};          // autotuned lane runs per channel bucket
   int batch_rows = 4;                       // window rows per lane of the batch gridder
+
+  // localisation (toi_localise*): max_windows windows
+  int tilted_slot = -1;                     // slot whose image p->tilted holds (-1: none)
+  float2* loc_k = nullptr;                  // [max_ch] k as float pairs
+  float4* loc_coef = nullptr;               // [max_windows][max_bl] P_bw (hi, lo), dl, dm factors
+  int4* loc_win = nullptr;                  // [max_windows] corner, flux bits, validity
+  float2* loc_facets = nullptr;             // [max_windows][64][64] facet grids
+  float2* loc_K = nullptr;                  // [max_windows][64][64] facet adjoints
+  float* loc_gD = nullptr;                  // [max_windows][32][32] data cotangents
+  float* loc_corr = nullptr;                // [32] 1 / psi_hat for 32 pixels on 64 cells
+  double* loc_loss2 = nullptr;              // [max_windows] 2 L_w
+  double* loc_dot = nullptr;                // [1] sum 2 L_w
+  double* loc_part = nullptr;               // reverse-pass block partials
+  unsigned long long* loc_keys = nullptr;   // [4096] window selection keys
+  int* loc_tiles = nullptr;                 // [max_windows] selected tiles
 };
 
 namespace toi {
@@ -234,6 +249,14 @@ size_t degrid_scratch_doubles();
 cudaError_t launch_degrid_backward(toi_plan_s* p, Slot& s, const float* grad_image,
                                    const float* image, float2* grad_sample, float2* grad_vis,
                                    float* grad_weight);
+
+// localise.cu
+size_t loc_part_doubles(int max_bl, int max_ch, int max_win);
+int loc_seed_max_tiles(int nwin);
+cudaError_t launch_localise_seed(toi_plan_s* p, Slot& s, const float* tlisi, int nwin, int* win,
+                                 double* src);
+cudaError_t launch_localise(toi_plan_s* p, Slot& s, int nwin, const int* win, const double* src,
+                            float* model, double* loss, double* grad_src, float* grad_weight);
 
 // host-side constant tables (api.cu)
 void es_fourier_table(int N, int G, int W, double beta_es, float* out);
