@@ -129,7 +129,7 @@ void free_plan(toi_plan_s* p) {
   cudaFree(p->adj_scratch);
   cudaFree(p->moments); cudaFree(p->m3_dev); cudaFree(p->m3_slabs); cudaFreeHost(p->m3_host);
   cudaFree(p->grid2);
-  cudaFree(p->loc_k); cudaFree(p->loc_coef); cudaFree(p->loc_win); cudaFree(p->loc_facets);
+  cudaFree(p->loc_k); cudaFree(p->loc_wq); cudaFree(p->loc_coef); cudaFree(p->loc_win); cudaFree(p->loc_facets);
   cudaFree(p->loc_K); cudaFree(p->loc_gD); cudaFree(p->loc_corr); cudaFree(p->loc_loss2);
   cudaFree(p->loc_dot); cudaFree(p->loc_part); cudaFree(p->loc_keys); cudaFree(p->loc_tiles);
   if (p->bslots) {
@@ -288,6 +288,7 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   if (c.max_windows > 0) {
     const size_t nw = (size_t)c.max_windows;
     TOI_ALLOC(p->loc_k, (size_t)c.max_channels, "localisation channel table");
+    TOI_ALLOC(p->loc_wq, (size_t)c.max_baselines * c.max_channels, "localisation sample weights");
     TOI_ALLOC(p->loc_coef, nw * c.max_baselines, "localisation coefficients");
     TOI_ALLOC(p->loc_win, nw, "localisation windows");
     TOI_ALLOC(p->loc_facets, nw * 64 * 64, "facet grids");

@@ -42,9 +42,7 @@ namespace {
 constexpr int kWin = TOI_LOC_WINDOW;   // window side (pixels)
 constexpr int kF = 2 * kWin;           // facet grid side (cells)
 constexpr int kW = 8;                  // ES kernel support
-constexpr int kGridThreads = 256;
-constexpr int kDegridThreads = 256;
-constexpr int kDegridRun = 8;          // samples per thread in the reverse pass
+constexpr int kMaxPassBlocks = 4 * 152;   // facet passes: blocks over the baselines
 constexpr int kFinThreads = 256;
 constexpr int kSortKeys = 2048;        // keys per block of the window selection
 constexpr int kMergeKeys = 4096;
@@ -53,13 +51,6 @@ __device__ __forceinline__ void hands(int npol, int& pa, int& pb) {
   if (npol == 4) { pa = 0; pb = 3; }
   else if (npol == 2) { pa = 0; pb = 1; }
   else { pa = 0; pb = 0; }
-}
-
-// psi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)) on |x| <= W/2, else 0
-__device__ __forceinline__ float psi(float x, float beta) {
-  const float z = x * (2.0f / kW);
-  const float s = 1.0f - z * z;
-  return s >= 0.f ? expf(beta * (sqrtf(s) - 1.0f)) : 0.f;
 }
 
 // Sample weight W_q = w_a + w_b of the parallel hands (0: not selected).
@@ -133,106 +124,224 @@ __global__ void loc_coef_kernel(const double* __restrict__ uvw, int nbl,
 }
 
 // ------------------------------------------------------- faceted gridding --
+//
+// Both facet passes treat a chunk of kChunk consecutive channels of one
+// baseline as a small matrix product over all windows.  For the chunk's
+// samples whose footprint starts at the same facet cell (o1, o2) (all of
+// them unless the track crosses a cell inside the chunk; then the chunk
+// takes one pass per origin)
+//   T[q][tap] = W_q psi(o2 + y - g2_q) psi(o1 + x - g1_q),   tap = 8 y + x,
+//   E[q][w]   = exp(2 pi i k_q P_bw),
+// the forward adds sum_q T[q][tap] S_w E[q][w] to facet cell o + tap of
+// window w (64 taps x 64 windows per block, accumulated in registers while
+// the origin stays and added to the facet grids in global memory when it
+// moves), and the reverse pass forms G[q][w] = sum_tap T[q][tap] K_w[o + tap]
+// from the 64 x 64 footprint of the windows' adjoints staged in shared
+// memory.  One warp evaluates each sample's 16 kernel values once for all
+// windows.
 
-// Block (window w, chunk): its threads walk runs of `run` channels of one
-// baseline each, keep the 8 x 8 footprint in registers while it stays on the
-// same cells (consecutive channels move by ~1e-3 facet cells) and add it to
-// the block's shared facet grid when it moves and at the end of the run; the
-// block's grid is then added to the window's facet grid in global memory.
-__global__ void __launch_bounds__(kGridThreads)
-loc_grid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale, const float2* __restrict__ kp,
-                const float* __restrict__ weight, const uint8_t* __restrict__ flag, int nbl,
-                int nch, int npol, int run, int runs_per_chunk, const float4* __restrict__ coef,
-                const int4* __restrict__ winfo, float beta_es, float2* __restrict__ facets) {
-  __shared__ float2 F[kF * kF];
-  const int w = blockIdx.x;
-  for (int i = threadIdx.x; i < kF * kF; i += blockDim.x) F[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-  const float S = __int_as_float(winfo[w].z);
-  if (!winfo[w].w) return;            // uniform per block
+constexpr int kChunk = 32;          // samples (channels) per chunk: one warp
+constexpr int kWG = 64;             // windows per block (blockIdx.y: window group)
+constexpr int kTaps = kW * kW;
+constexpr int kPassThreads = 256;
+
+struct PassCtl {
+  int o1, o2, active, more, flush;
+};
+
+// Sample weight table W_q = w_a + w_b (0: not selected) for both passes.
+__global__ void loc_wq_kernel(const float* __restrict__ weight, const uint8_t* __restrict__ flag,
+                              int nbl, int nch, int npol, float* __restrict__ wq) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)nbl * nch) return;
   int pa, pb;
   hands(npol, pa, pb);
-  const int nrun = (nch + run - 1) / run;
-  const long long total = (long long)nbl * nrun;
-  const long long r0 = (long long)blockIdx.y * runs_per_chunk;
-  const long long r1 = min(total, r0 + runs_per_chunk);
-  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    const int b = (int)(r / nrun);
-    const int c0 = (int)(r - (long long)b * nrun) * run;
-    const int c1 = min(nch, c0 + run);
-    const float a1 = (float)(bcoef[b].a1 * fscale), a2 = (float)(bcoef[b].a2 * fscale);
-    const float4 cf = coef[(size_t)w * nbl + b];
-    float2 acc[kW][kW];
+  wq[q] = sample_weight(weight, flag, (size_t)q * npol, pa, pb);
+}
+
+// psi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)) on |x| <= W/2, else 0, with
+// the hardware approximations of exp2 and sqrt (relative error ~1e-6, far
+// below the ES kernel's own error); beta_log2e = beta log2(e)
+__device__ __forceinline__ float psi_fast(float x, float beta_log2e) {
+  const float z = x * (2.0f / kW);
+  const float s = 1.0f - z * z;
+  if (!(s >= 0.f)) return 0.f;
+  float r, e;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(s));
+  asm("ex2.approx.f32 %0, %1;" : "=f"(e) : "f"(beta_log2e * (r - 1.0f)));
+  return e;
+}
+
+// exp(2 pi i f) for |f| <= ~0.5 (hardware sin/cos: absolute error ~5e-7)
+__device__ __forceinline__ float2 cis_turns(float f) {
+  float sn, cs;
+  __sincosf(6.283185307179586f * f, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+// Warp 0 (lane = sample of the chunk): choose the next origin among the
+// pending samples (the block's current origin first, so that a chunk that
+// continues it costs no flush), write the pass's T (0 for samples outside
+// it) and clear them from `pending` (warp-uniform).  TQ: T is [q][tap],
+// else [tap][q].
+template <bool TQ>
+__device__ __forceinline__ void build_pass(float* T, unsigned& pending, float g1, float g2,
+                                           float Wq, int cur1, int cur2, bool have,
+                                           float beta_log2e, PassCtl* ctl) {
+  const int lane = threadIdx.x;
+  const int n1 = (int)ceilf(g1 - 0.5f * kW), n2 = (int)ceilf(g2 - 0.5f * kW);
+  const bool mine = (pending >> lane) & 1u;
+  const unsigned cur = __ballot_sync(0xffffffffu, mine && n1 == cur1 && n2 == cur2);
+  int o1 = cur1, o2 = cur2;
+  unsigned in = 0;
+  if (have && cur) {
+    in = cur;
+  } else if (pending) {
+    const int first = __ffs(pending) - 1;
+    o1 = __shfl_sync(0xffffffffu, n1, first);
+    o2 = __shfl_sync(0xffffffffu, n2, first);
+    in = __ballot_sync(0xffffffffu, mine && n1 == o1 && n2 == o2);
+  }
+  const bool use = (in >> lane) & 1u;
+  float wx[kW], wy[kW];
 #pragma unroll
-    for (int y = 0; y < kW; ++y)
+  for (int a = 0; a < kW; ++a) {
+    wx[a] = use ? psi_fast((float)(o1 + a) - g1, beta_log2e) : 0.f;
+    wy[a] = use ? Wq * psi_fast((float)(o2 + a) - g2, beta_log2e) : 0.f;
+  }
 #pragma unroll
-      for (int x = 0; x < kW; ++x) acc[y][x] = make_float2(0.f, 0.f);
-    int o1 = 0, o2 = 0;
-    bool live = false;
-    for (int c = c0; c < c1; ++c) {
-      const size_t o = ((size_t)b * nch + c) * npol;
-      const float Wq = sample_weight(weight, flag, o, pa, pb);
-      if (!(Wq > 0.f)) continue;
-      const float2 k = kp[c];
-      const float g1 = fmaf(a1, k.x, fmaf(a1, k.y, 0.5f * kF));
-      const float g2 = fmaf(a2, k.x, fmaf(a2, k.y, 0.5f * kF));
-      const int n1 = (int)ceilf(g1 - 0.5f * kW), n2 = (int)ceilf(g2 - 0.5f * kW);
-      if (!live || n1 != o1 || n2 != o2) {
-        if (live) {
+  for (int y = 0; y < kW; ++y) {
+    if (TQ) {
+      float4* row = reinterpret_cast<float4*>(T + lane * kTaps + y * kW);
+      row[0] = make_float4(wy[y] * wx[0], wy[y] * wx[1], wy[y] * wx[2], wy[y] * wx[3]);
+      row[1] = make_float4(wy[y] * wx[4], wy[y] * wx[5], wy[y] * wx[6], wy[y] * wx[7]);
+    } else {
 #pragma unroll
-          for (int y = 0; y < kW; ++y)
+      for (int x = 0; x < kW; ++x) T[(y * kW + x) * kChunk + lane] = wy[y] * wx[x];
+    }
+  }
+  pending &= ~in;
+  if (lane == 0) {
+    ctl->o1 = o1;
+    ctl->o2 = o2;
+    ctl->active = in != 0;
+    ctl->more = pending != 0;
+    ctl->flush = have && in != 0 && (o1 != cur1 || o2 != cur2);
+  }
+}
+
+// Block (baselines blockIdx.x, blockIdx.x + gridDim.x, ...; window group
+// blockIdx.y).  Thread t accumulates taps 4 (t / 16) .. + 3 for windows
+// 4 (t % 16) .. + 3 of the group.
+__global__ void __launch_bounds__(kPassThreads)
+loc_grid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
+                const float2* __restrict__ kp, const float* __restrict__ wq, int nbl, int nch,
+                const float4* __restrict__ coef, const int4* __restrict__ winfo, int nwin,
+                float beta_log2e, float2* __restrict__ facets) {
+  __shared__ __align__(16) float T[kChunk * kTaps];     // [q][tap]
+  __shared__ __align__(16) float2 C[kChunk * kWG];      // [q][w]: S_w E[q][w]
+  __shared__ float2 Pw[kWG];
+  __shared__ float Sw[kWG];
+  __shared__ float2 kq[kChunk];
+  __shared__ PassCtl ctl;
+  const int t = threadIdx.x;
+  const int wg0 = blockIdx.y * kWG;
+  if (t < kWG) {
+    const int w = wg0 + t;
+    Sw[t] = (w < nwin && winfo[w].w) ? __int_as_float(winfo[w].z) : 0.f;
+  }
+  const int tb = t >> 4, wb = t & 15;
+  float2 acc[4][4];
 #pragma unroll
-            for (int x = 0; x < kW; ++x) {
-              float2* dst = &F[((o2 + y) & (kF - 1)) * kF + ((o1 + x) & (kF - 1))];
-              atomicAdd(&dst->x, acc[y][x].x);
-              atomicAdd(&dst->y, acc[y][x].y);
-              acc[y][x] = make_float2(0.f, 0.f);
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  int o1 = 0, o2 = 0;
+  bool have = false;
+
+  auto flush = [&]() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int tap = tb * 4 + i, y = tap >> 3, x = tap & 7;
+      const int cell = ((o2 + y) & (kF - 1)) * kF + ((o1 + x) & (kF - 1));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int w = wg0 + wb * 4 + j;
+        if (w < nwin && (acc[i][j].x != 0.f || acc[i][j].y != 0.f)) {
+          float2* dst = facets + (size_t)w * kF * kF + cell;
+          atomicAdd(&dst->x, acc[i][j].x);
+          atomicAdd(&dst->y, acc[i][j].y);
+        }
+        acc[i][j] = make_float2(0.f, 0.f);
+      }
+    }
+  };
+
+  for (int b = blockIdx.x; b < nbl; b += gridDim.x) {
+    __syncthreads();                  // the previous baseline's Pw readers are done
+    if (t < kWG) {
+      const int w = wg0 + t;
+      const float4 cf = w < nwin ? coef[(size_t)w * nbl + b] : make_float4(0.f, 0.f, 0.f, 0.f);
+      Pw[t] = make_float2(cf.x, cf.y);
+    }
+    float a1 = 0.f, a2 = 0.f;
+    if (t < kChunk) {
+      a1 = (float)(bcoef[b].a1 * fscale);
+      a2 = (float)(bcoef[b].a2 * fscale);
+    }
+    for (int ch0 = 0; ch0 < nch; ch0 += kChunk) {
+      float g1 = 0.f, g2 = 0.f, W = 0.f;
+      unsigned pending = 0;
+      if (t < kChunk) {
+        const int c = ch0 + t;
+        float2 k = make_float2(0.f, 0.f);
+        if (c < nch) {
+          W = wq[(size_t)b * nch + c];
+          k = kp[c];
+        }
+        g1 = fmaf(a1, k.x, fmaf(a1, k.y, 0.5f * kF));
+        g2 = fmaf(a2, k.x, fmaf(a2, k.y, 0.5f * kF));
+        kq[t] = k;
+        pending = __ballot_sync(0xffffffffu, W > 0.f);
+      }
+      __syncthreads();                // kq and Pw written; the last chunk's T, C are read
+      for (int e = t; e < kChunk * kWG; e += kPassThreads) {
+        const int q = e >> 6, w = e & (kWG - 1);
+        const float2 k = kq[q], P = Pw[w];
+        const float2 ph = cis_turns(frac_turns(k.x, k.y, P.x, P.y));
+        C[e] = make_float2(Sw[w] * ph.x, Sw[w] * ph.y);
+      }
+      while (true) {
+        if (t < kChunk) build_pass<true>(T, pending, g1, g2, W, o1, o2, have, beta_log2e, &ctl);
+        __syncthreads();
+        const PassCtl c = ctl;
+        if (!c.active) break;
+        if (c.flush) flush();
+        o1 = c.o1;
+        o2 = c.o2;
+        have = true;
+#pragma unroll 4
+        for (int q = 0; q < kChunk; ++q) {
+          const float4 tv = *reinterpret_cast<const float4*>(T + q * kTaps + tb * 4);
+          const float4 ca = *reinterpret_cast<const float4*>(C + q * kWG + wb * 4);
+          const float4 cb = *reinterpret_cast<const float4*>(C + q * kWG + wb * 4 + 2);
+          const float tt[4] = {tv.x, tv.y, tv.z, tv.w};
+          const float2 cc[4] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w),
+                                make_float2(cb.x, cb.y), make_float2(cb.z, cb.w)};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              acc[i][j].x = fmaf(tt[i], cc[j].x, acc[i][j].x);
+              acc[i][j].y = fmaf(tt[i], cc[j].y, acc[i][j].y);
             }
         }
-        o1 = n1;
-        o2 = n2;
-        live = true;
+        __syncthreads();              // T read before the next pass rewrites it
+        if (!c.more) break;
       }
-      float wx[kW], wy[kW];
-#pragma unroll
-      for (int a = 0; a < kW; ++a) {
-        wx[a] = psi((float)(n1 + a) - g1, beta_es);
-        wy[a] = psi((float)(n2 + a) - g2, beta_es);
-      }
-      float sn, cs;
-      sincospif(2.0f * frac_turns(k.x, k.y, cf.x, cf.y), &sn, &cs);
-      const float sw = S * Wq;
-      const float cr = sw * cs, ci = sw * sn;
-#pragma unroll
-      for (int y = 0; y < kW; ++y) {
-        const float yr = wy[y] * cr, yi = wy[y] * ci;
-#pragma unroll
-        for (int x = 0; x < kW; ++x) {
-          acc[y][x].x = fmaf(wx[x], yr, acc[y][x].x);
-          acc[y][x].y = fmaf(wx[x], yi, acc[y][x].y);
-        }
-      }
-    }
-    if (live) {
-#pragma unroll
-      for (int y = 0; y < kW; ++y)
-#pragma unroll
-        for (int x = 0; x < kW; ++x) {
-          float2* dst = &F[((o2 + y) & (kF - 1)) * kF + ((o1 + x) & (kF - 1))];
-          atomicAdd(&dst->x, acc[y][x].x);
-          atomicAdd(&dst->y, acc[y][x].y);
-        }
     }
   }
-  __syncthreads();
-  float2* G = facets + (size_t)w * kF * kF;
-  for (int i = threadIdx.x; i < kF * kF; i += blockDim.x) {
-    const float2 v = F[i];
-    if (v.x != 0.f || v.y != 0.f) {
-      atomicAdd(&G[i].x, v.x);
-      atomicAdd(&G[i].y, v.y);
-    }
-  }
+  if (have) flush();
 }
 
 // ------------------------------------------------------------- finish ----
@@ -378,108 +487,162 @@ __global__ void loc_dot_kernel(const double* __restrict__ loss2, int nwin, doubl
 
 // ------------------------------------------------------------- reverse ---
 
-// Thread = (baseline, run of kDegridRun channels); for each window in turn
-// it degrids K_w at its samples and accumulates the window's dS, dl, dm
-// (block partials, fixed order) and, per sample over all windows, the model
-// part of the weight gradient, added to grad_weight at the end.
-__global__ void __launch_bounds__(kDegridThreads)
+// Block as loc_grid_kernel.  Per pass, thread t forms G for samples
+// 4 (t / 32) .. + 3 and windows 2 (t % 32), + 1 of the group, then
+//   zz = conj(G) E;  dS_w += W Re zz;  dl_w += S W k fl Im zz;  dm_w alike;
+//   A_q += S_w Re zz (the models' weight gradient, summed over the windows
+//   in shared memory and added to grad_weight per chunk).
+// The window sums are float per chunk, float64 across chunks; the block's
+// totals go to part[block][w][3] in a fixed order.
+__global__ void __launch_bounds__(kPassThreads)
 loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
-                  const float2* __restrict__ kp, const float* __restrict__ weight,
+                  const float2* __restrict__ kp, const float* __restrict__ wq,
                   const uint8_t* __restrict__ flag, int nbl, int nch, int npol,
                   const float4* __restrict__ coef, const int4* __restrict__ winfo, int nwin,
-                  const float2* __restrict__ Kall, float beta_es, double* __restrict__ part,
-                  float* __restrict__ grad_weight) {
-  __shared__ float red[kDegridThreads / 32][3];
+                  const float2* __restrict__ Kall, float beta_log2e, double* __restrict__ part,
+                  int nwin_part, float* __restrict__ grad_weight) {
+  __shared__ __align__(16) float T2[kTaps * kChunk];    // [tap][q]
+  __shared__ __align__(16) float2 Kf[kTaps * kWG];      // [tap][w]; reused for the final sums
+  __shared__ float4 Cf[kWG];
+  __shared__ float Sw[kWG];
+  __shared__ float2 kq[kChunk];
+  __shared__ float Wsh[kChunk];
+  __shared__ float Ared[kChunk][33];
+  __shared__ PassCtl ctl;
+  const int t = threadIdx.x;
+  const int wg0 = blockIdx.y * kWG;
+  if (t < kWG) {
+    const int w = wg0 + t;
+    Sw[t] = (w < nwin && winfo[w].w) ? __int_as_float(winfo[w].z) : 0.f;
+  }
   int pa, pb;
   hands(npol, pa, pb);
-  const int nrun = (nch + kDegridRun - 1) / kDegridRun;
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = r < (long long)nbl * nrun;
-  const int b = active ? (int)(r / nrun) : 0;
-  const int c0 = active ? (int)(r - (long long)b * nrun) * kDegridRun : 0;
-  float Wq[kDegridRun], Aq[kDegridRun];
-  float a1 = 0.f, a2 = 0.f;
-  if (active) {
-    a1 = (float)(bcoef[b].a1 * fscale);
-    a2 = (float)(bcoef[b].a2 * fscale);
-  }
-#pragma unroll
-  for (int j = 0; j < kDegridRun; ++j) {
-    const int c = c0 + j;
-    Wq[j] = (active && c < nch)
-                ? sample_weight(weight, flag, ((size_t)b * nch + c) * npol, pa, pb) : 0.f;
-    Aq[j] = 0.f;
-  }
-  for (int w = 0; w < nwin; ++w) {
-    float dS = 0.f, dl = 0.f, dm = 0.f;
-    if (active && winfo[w].w) {
-      const float S = __int_as_float(winfo[w].z);
-      const float4 cf = coef[(size_t)w * nbl + b];
-      const float2* K = Kall + (size_t)w * kF * kF;
-#pragma unroll 1
-      for (int j = 0; j < kDegridRun; ++j) {
-        if (!(Wq[j] > 0.f)) continue;
-        const float2 k = kp[c0 + j];
-        const float g1 = fmaf(a1, k.x, fmaf(a1, k.y, 0.5f * kF));
-        const float g2 = fmaf(a2, k.x, fmaf(a2, k.y, 0.5f * kF));
-        const int n1 = (int)ceilf(g1 - 0.5f * kW), n2 = (int)ceilf(g2 - 0.5f * kW);
-        float wx[kW];
-#pragma unroll
-        for (int a = 0; a < kW; ++a) wx[a] = psi((float)(n1 + a) - g1, beta_es);
-        float gr = 0.f, gi = 0.f;
-#pragma unroll
-        for (int y = 0; y < kW; ++y) {
-          const float wy = psi((float)(n2 + y) - g2, beta_es);
-          const float2* row = K + ((n2 + y) & (kF - 1)) * kF;
-          float rr = 0.f, ri = 0.f;
-#pragma unroll
-          for (int x = 0; x < kW; ++x) {
-            const float2 v = __ldg(row + ((n1 + x) & (kF - 1)));
-            rr = fmaf(wx[x], v.x, rr);
-            ri = fmaf(wx[x], v.y, ri);
-          }
-          gr = fmaf(wy, rr, gr);
-          gi = fmaf(wy, ri, gi);
+  const int qb = t >> 5, wb = t & 31;
+  double sums[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  int o1 = 0, o2 = 0, k1 = -1 << 30, k2 = 0;     // pass origin, origin of the staged footprint
+  bool have = false;
+  for (int b = blockIdx.x; b < nbl; b += gridDim.x) {
+    __syncthreads();
+    if (t < kWG) {
+      const int w = wg0 + t;
+      Cf[t] = w < nwin ? coef[(size_t)w * nbl + b] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float a1 = 0.f, a2 = 0.f;
+    if (t < kChunk) {
+      a1 = (float)(bcoef[b].a1 * fscale);
+      a2 = (float)(bcoef[b].a2 * fscale);
+    }
+    for (int ch0 = 0; ch0 < nch; ch0 += kChunk) {
+      float g1 = 0.f, g2 = 0.f, W = 0.f;
+      unsigned pending = 0;
+      if (t < kChunk) {
+        const int c = ch0 + t;
+        float2 k = make_float2(0.f, 0.f);
+        if (c < nch) {
+          W = wq[(size_t)b * nch + c];
+          k = kp[c];
         }
-        float sn, cs;
-        sincospif(2.0f * frac_turns(k.x, k.y, cf.x, cf.y), &sn, &cs);
-        // zz = conj(g) e^{2 pi i k P}
-        const float zr = gr * cs + gi * sn, zi = gr * sn - gi * cs;
-        dS = fmaf(Wq[j], zr, dS);
-        const float swk = S * Wq[j] * k.x;
-        dl = fmaf(swk * cf.z, zi, dl);
-        dm = fmaf(swk * cf.w, zi, dm);
-        Aq[j] = fmaf(S, zr, Aq[j]);
+        g1 = fmaf(a1, k.x, fmaf(a1, k.y, 0.5f * kF));
+        g2 = fmaf(a2, k.x, fmaf(a2, k.y, 0.5f * kF));
+        kq[t] = k;
+        Wsh[t] = W;
+        for (int j = 0; j < 33; ++j) Ared[t][j] = 0.f;
+        pending = __ballot_sync(0xffffffffu, W > 0.f);
+      }
+      float cs[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      while (true) {
+        // T without the sample weight: the epilogue applies W itself
+        if (t < kChunk) build_pass<false>(T2, pending, g1, g2, 1.0f, o1, o2, have, beta_log2e, &ctl);
+        __syncthreads();
+        const PassCtl c = ctl;
+        if (!c.active) break;
+        o1 = c.o1;
+        o2 = c.o2;
+        have = true;
+        if (o1 != k1 || o2 != k2) {     // stage the windows' footprints at this origin
+          for (int e = t; e < kTaps * kWG; e += kPassThreads) {
+            const int tap = e >> 6, w = wg0 + (e & (kWG - 1));
+            const int y = tap >> 3, x = tap & 7;
+            Kf[e] = w < nwin ? __ldg(Kall + (size_t)w * kF * kF +
+                                     ((o2 + y) & (kF - 1)) * kF + ((o1 + x) & (kF - 1)))
+                             : make_float2(0.f, 0.f);
+          }
+          k1 = o1;
+          k2 = o2;
+          __syncthreads();
+        }
+        float2 g[4][2];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) g[i][0] = g[i][1] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int tap = 0; tap < kTaps; ++tap) {
+          const float4 tv = *reinterpret_cast<const float4*>(T2 + tap * kChunk + qb * 4);
+          const float4 kv = *reinterpret_cast<const float4*>(Kf + tap * kWG + wb * 2);
+          const float tt[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            g[i][0].x = fmaf(tt[i], kv.x, g[i][0].x);
+            g[i][0].y = fmaf(tt[i], kv.y, g[i][0].y);
+            g[i][1].x = fmaf(tt[i], kv.z, g[i][1].x);
+            g[i][1].y = fmaf(tt[i], kv.w, g[i][1].y);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int q = qb * 4 + i;
+          const float2 k = kq[q];
+          const float Wq = Wsh[q];
+          float ap = 0.f;
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const float4 cf = Cf[wb * 2 + j];
+            const float S = Sw[wb * 2 + j];
+            const float2 e = cis_turns(frac_turns(k.x, k.y, cf.x, cf.y));
+            // zz = conj(g) e
+            const float zr = g[i][j].x * e.x + g[i][j].y * e.y;
+            const float zi = g[i][j].x * e.y - g[i][j].y * e.x;
+            cs[j][2] = fmaf(Wq, zr, cs[j][2]);
+            const float swk = S * Wq * k.x;
+            cs[j][0] = fmaf(swk * cf.z, zi, cs[j][0]);
+            cs[j][1] = fmaf(swk * cf.w, zi, cs[j][1]);
+            ap = fmaf(S, zr, ap);
+          }
+          Ared[q][wb] += ap;
+        }
+        __syncthreads();              // T2, Kf read before the next pass
+        if (!c.more) break;
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) sums[j][m] += (double)cs[j][m];
+      __syncthreads();                // Ared complete
+      if (t < kChunk && grad_weight) {
+        const int c = ch0 + t;
+        if (c < nch && W > 0.f) {
+          float A = 0.f;
+          for (int j = 0; j < 32; ++j) A += Ared[t][j];
+          const size_t o = ((size_t)b * nch + c) * npol;
+          if (!(flag && flag[o + pa])) grad_weight[o + pa] += A;
+          if (pb != pa && !(flag && flag[o + pb])) grad_weight[o + pb] += A;
+        }
       }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      dS += __shfl_down_sync(0xffffffffu, dS, off);
-      dl += __shfl_down_sync(0xffffffffu, dl, off);
-      dm += __shfl_down_sync(0xffffffffu, dm, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red[threadIdx.x >> 5][0] = dl;      // grad_src order: l, m, S
-      red[threadIdx.x >> 5][1] = dm;
-      red[threadIdx.x >> 5][2] = dS;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-      double t = 0.0;
-      for (int i = 0; i < kDegridThreads / 32; ++i) t += (double)red[i][threadIdx.x];
-      part[((size_t)blockIdx.x * nwin + w) * 3 + threadIdx.x] = t;
-    }
-    __syncthreads();
   }
-  if (grad_weight && active) {
-    const bool fl = flag != nullptr;
+  // block totals per window: sum over the 8 sample blocks in a fixed order
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(Kf);        // [8][64][3]
 #pragma unroll
-    for (int j = 0; j < kDegridRun; ++j) {
-      const int c = c0 + j;
-      if (c >= nch || !(Wq[j] > 0.f)) continue;
-      const size_t o = ((size_t)b * nch + c) * npol;
-      if (!(fl && flag[o + pa])) grad_weight[o + pa] += Aq[j];
-      if (pb != pa && !(fl && flag[o + pb])) grad_weight[o + pb] += Aq[j];
-    }
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) red[(qb * kWG + wb * 2 + j) * 3 + m] = sums[j][m];
+  __syncthreads();
+  for (int e = t; e < kWG * 3; e += kPassThreads) {
+    const int w = wg0 + e / 3;
+    if (w >= nwin) continue;
+    double acc = 0.0;
+    for (int i = 0; i < kPassThreads / 32; ++i) acc += red[i * kWG * 3 + e];
+    part[((size_t)blockIdx.x * nwin_part + w) * 3 + e % 3] = acc;
   }
 }
 
@@ -597,8 +760,8 @@ __global__ void seed_window_kernel(const int* __restrict__ tiles, int ntx, int T
 }  // namespace
 
 size_t loc_part_doubles(int max_bl, int max_ch, int max_win) {
-  const long long runs = (long long)max_bl * ((max_ch + kDegridRun - 1) / kDegridRun);
-  const long long blocks = (runs + kDegridThreads - 1) / kDegridThreads;
+  (void)max_ch;
+  const int blocks = max_bl < kMaxPassBlocks ? max_bl : kMaxPassBlocks;
   return (size_t)blocks * max_win * 3;
 }
 
@@ -622,23 +785,20 @@ cudaError_t launch_localise(toi_plan_s* p, Slot& s, int nwin, const int* win, co
                             float* model, double* loss, double* grad_src, float* grad_weight) {
   const int nbl = s.nbl, nch = s.nch, npol = p->cfg.n_pol;
   const double fscale = (double)kF / (double)p->G;
-  const float beta_es = (float)p->beta_es;
   cudaError_t e = cudaMemsetAsync(p->loc_facets, 0, sizeof(float2) * kF * kF * nwin, p->stream);
   if (e != cudaSuccess) return e;
   loc_k_kernel<<<(nch + 255) / 256, 256, 0, p->stream>>>(s.freq, nch, p->loc_k);
+  const long long nq = (long long)nbl * nch;
+  loc_wq_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, p->stream>>>(s.weight, s.flag, nbl, nch,
+                                                                     npol, p->loc_wq);
   loc_coef_kernel<<<dim3((nbl + 127) / 128, nwin), 128, 0, p->stream>>>(
       s.uvw, nbl, s.snap, win, src, nwin, p->N, p->beta_rad, p->loc_coef, p->loc_win, p->d_status);
-  // faceted gridding: about 8 blocks per SM over all windows
-  const int run = nch < 128 ? nch : 128;
-  const long long total = (long long)nbl * ((nch + run - 1) / run);
-  int chunks = (8 * 152 + nwin - 1) / nwin;
-  const long long maxchunks = (total + kGridThreads - 1) / kGridThreads;
-  if (chunks > maxchunks) chunks = (int)maxchunks;
-  if (chunks < 1) chunks = 1;
-  const int per_chunk = (int)((total + chunks - 1) / chunks);
-  loc_grid_kernel<<<dim3(nwin, chunks), kGridThreads, 0, p->stream>>>(
-      s.coef, fscale, p->loc_k, s.weight, s.flag, nbl, nch, npol, run, per_chunk, p->loc_coef,
-      p->loc_win, beta_es, p->loc_facets);
+  const float beta_log2e = (float)(p->beta_es * 1.4426950408889634);
+  const int nblk = nbl < kMaxPassBlocks ? nbl : kMaxPassBlocks;
+  const dim3 pgrid(nblk, (nwin + kWG - 1) / kWG);
+  loc_grid_kernel<<<pgrid, kPassThreads, 0, p->stream>>>(
+      s.coef, fscale, p->loc_k, p->loc_wq, nbl, nch, p->loc_coef, p->loc_win, nwin, beta_log2e,
+      p->loc_facets);
   loc_finish_kernel<<<nwin, kFinThreads, 0, p->stream>>>(
       p->loc_facets, p->loc_win, p->tilted, p->N, p->loc_corr, s.snap, model, loss, p->loc_gD,
       p->loc_K, p->loc_loss2);
@@ -654,11 +814,9 @@ cudaError_t launch_localise(toi_plan_s* p, Slot& s, int nwin, const int* win, co
     if ((e = launch_degrid_weights(p, s, p->loc_dot, grad_weight)) != cudaSuccess) return e;
   }
   if (grad_src || grad_weight) {
-    const long long runs = (long long)nbl * ((nch + kDegridRun - 1) / kDegridRun);
-    const int nblk = (int)((runs + kDegridThreads - 1) / kDegridThreads);
-    loc_degrid_kernel<<<nblk, kDegridThreads, 0, p->stream>>>(
-        s.coef, fscale, p->loc_k, s.weight, s.flag, nbl, nch, npol, p->loc_coef, p->loc_win,
-        nwin, p->loc_K, beta_es, p->loc_part, grad_weight);
+    loc_degrid_kernel<<<pgrid, kPassThreads, 0, p->stream>>>(
+        s.coef, fscale, p->loc_k, p->loc_wq, s.flag, nbl, nch, npol, p->loc_coef, p->loc_win,
+        nwin, p->loc_K, beta_log2e, p->loc_part, nwin, grad_weight);
     if (grad_src)
       loc_reduce_kernel<<<(3 * nwin + 127) / 128, 128, 0, p->stream>>>(p->loc_part, nblk, nwin,
                                                                         grad_src);

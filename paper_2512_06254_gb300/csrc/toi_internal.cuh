@@ -191,6 +191,7 @@ struct toi_plan_s {
   // localisation (toi_localise*): max_windows windows
   int tilted_slot = -1;                     // slot whose image p->tilted holds (-1: none)
   float2* loc_k = nullptr;                  // [max_ch] k as float pairs
+  float* loc_wq = nullptr;                  // [max_bl][max_ch] sample weights w_a + w_b
   float4* loc_coef = nullptr;               // [max_windows][max_bl] P_bw (hi, lo), dl, dm factors
   int4* loc_win = nullptr;                  // [max_windows] corner, flux bits, validity
   float2* loc_facets = nullptr;             // [max_windows][64][64] facet grids
