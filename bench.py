@@ -270,8 +270,11 @@ def run_ours(args):
               for k, v in prof.items()}
 
     # end to end through the streaming API from pinned host memory
+    # the Python batch pipeline (pipeline.StreamingImager): the end-to-end
+    # number when sharded or asked for with --e2e-engine batch
     e2e = None
-    if not args.no_e2e:
+    use_native = args.e2e_engine == "native" and not sharded
+    if not args.no_e2e and not use_native:
         hpool = []
         for p in pool[:args.host_pool]:
             hpool.append({k: v.cpu().pin_memory() for k, v in p.items()})
@@ -297,6 +300,56 @@ def run_ours(args):
                "host_pool_snapshots": args.host_pool, "copy_streams": args.copy_streams,
                "staging_depth": args.e2e_depth,
                "engine": args.engine + (f"{B}" if B else "")}
+
+    # end to end through the native multi-stream runtime (toi_stream_*)
+    if not args.no_e2e and use_native:
+        nplan = toi.Plan(w.image_size, w.cell_arcsec, w.n_bl, w.n_chan, w.n_pol, tlisi_tile=T,
+                         grid_slots=3)
+        hpool_n = []
+        for p in pool[:args.host_pool]:
+            hpool_n.append({k: v.cpu().pin_memory() for k, v in p.items()})
+        sn = toi.Stream(nplan, host_depth=16, n_copy=args.copy_streams)
+        row_host = torch.empty(nt, nt, dtype=torch.float32)
+
+        def native_obs():
+            h2d = d2h = 0
+            for s_ in range(S):
+                # the host row ring holds 16 rows: the oldest is popped when full
+                while sn.pending_rows >= 15:
+                    sn.pop(wait=True, out=row_host)
+                    d2h += row_bytes
+                hp = hpool_n[s_ % len(hpool_n)]
+                sn.push(hp)
+                h2d += sum(v.numel() * v.element_size() for v in hp.values())
+                while sn.pop(wait=False, out=row_host) is not None:
+                    d2h += row_bytes
+            while sn.pop(wait=True, out=row_host) is not None:
+                d2h += row_bytes
+            return h2d, d2h
+
+        for _ in range(args.e2e_warmup):
+            native_obs()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0 = time.perf_counter()
+        h2d = d2h = 0
+        for _ in range(args.e2e_steps):
+            a_, b_ = native_obs()
+            h2d += a_
+            d2h += b_
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        es = time.perf_counter() - e0
+        sn.close()
+        nplan.close()
+        e2e = {"value": round(S * args.e2e_steps * world / es, 2), "unit": "snapshots/s",
+               "h2d_bytes_per_step": h2d // args.e2e_steps,
+               "d2h_bytes_per_step": d2h // args.e2e_steps,
+               "host_pool_snapshots": args.host_pool, "copy_streams": args.copy_streams,
+               "engine": "toi_stream (pipeline stages on their own CUDA streams, depth-3 "
+                         "grid ring, depth-5 image ring)"}
 
     mode3_plan = plan.mode3_info() if args.mode == 3 else None
     cpu = None
@@ -745,6 +798,9 @@ def main():
                     help="field of view in degrees (cell = fov / N; default 2 arcsec cells)")
     ap.add_argument("--channels", type=int, default=N_CH,
                     help="channels per snapshot (the paper's MeerKAT set has 1024)")
+    ap.add_argument("--e2e-engine", default="native", choices=["native", "batch"],
+                    help="end-to-end path: toi_stream_* (native stage streams, default) or the "
+                         "Python batch pipeline")
     ap.add_argument("--e2e-depth", type=int, default=2,
                     help="e2e: staging slots (of a batch each with the batch engine)")
     ap.add_argument("--copy-streams", type=int, default=4,

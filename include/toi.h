@@ -332,6 +332,51 @@ toi_status toi_degrid_backward(toi_plan_t plan, int32_t slot, const float* grad_
                                const float* image, void* grad_sample, void* grad_vis,
                                float* grad_weight);
 
+/* Streaming runtime: the snapshot pipeline of Sections 4.1-4.4 with one
+ * CUDA stream per device stage (copy_gpu over n_copy copy streams, gridding,
+ * fft, interpolate fused with the tLISI tile moments, tlisi, copy_cpu),
+ * interlocked by events; the caller is data_read (filling pinned host
+ * buffers) and data_write (toi_stream_pop).  Rings: a depth-2 device staging
+ * ring, the depth-3 grid ring (grid slots 0-2 and three tilted images), the
+ * depth-5 image ring, two device tLISI rows and host_depth pinned host rows.
+ * A ring slot is reused after an event of its last reader (a stream wait):
+ * toi_stream_push never waits on the host.  Row r of the output is the
+ * tLISI of snapshots (r, r + 1, r + 2) (float32 [N/T][N/T]).
+ * The plan needs grid_slots >= 3 and 2-D mode; while a stream is open the
+ * plan's grid slots 0-2 belong to it (no toi_grid/toi_image/toi_batch on
+ * this plan until toi_stream_close).  Errors: TOI_ERR_ARG,
+ * TOI_ERR_UNSUPPORTED, TOI_ERR_OOM, TOI_ERR_CUDA (plan-reported). */
+typedef struct toi_stream_s* toi_stream_t;
+
+/* Allocate the rings and streams.  host_depth in [1, 4096] pinned host tLISI
+ * rows; n_copy in [1, 16] copy streams for the visibilities (and flags and
+ * weights), split by baseline; with_weights: whether snapshots may carry
+ * WEIGHT_SPECTRUM (staging for it is allocated). */
+toi_status toi_stream_open(toi_plan_t plan, int32_t host_depth, int32_t n_copy,
+                           int32_t with_weights, toi_stream_t* out);
+
+/* Enqueue one snapshot through every device stage.  snap holds HOST
+ * pointers (pinned memory, else the copies are not asynchronous), layouts
+ * as toi_grid; snap->image is ignored.  The buffers must stay unchanged until
+ * toi_stream_input_free reports them free.  *index (may be NULL) receives the
+ * snapshot's position in the stream.  Fails with TOI_ERR_ARG when the host
+ * row ring is full (pop first). */
+toi_status toi_stream_push(toi_stream_t stream, const toi_snapshot* snap, int64_t* index);
+
+/* *is_free = 1 once the host->device copies of snapshot `index` are done
+ * (its host buffers may be refilled); wait != 0 blocks until then. */
+toi_status toi_stream_input_free(toi_stream_t stream, int64_t index, int32_t wait,
+                                 int32_t* is_free);
+
+/* The oldest tLISI row not yet popped: copied to row (host float32
+ * [N/T][N/T]) with *got = 1 and *row_index = r, or *got = 0 when none is
+ * ready (none pushed yet, or wait == 0 and its copy is still running). */
+toi_status toi_stream_pop(toi_stream_t stream, float* row, int64_t* row_index, int32_t wait,
+                          int32_t* got);
+
+/* Wait for the stages and free the stream's buffers, streams and events. */
+toi_status toi_stream_close(toi_stream_t stream);
+
 /* Side of a localisation window (pixels of the tilted-plane image). */
 #define TOI_LOC_WINDOW 32
 

@@ -7,7 +7,7 @@ computation lives in the CUDA library libtoi (C ABI, include/toi.h); this
 package holds its ctypes binding, the build script and the seeded input
 generator.
 """
-from .binding import (Plan, ToiError, tlisi_candidates, lib, config_default,  # noqa: F401
+from .binding import (Plan, Stream, ToiError, tlisi_candidates, lib, config_default,  # noqa: F401
                       TOI_OK, TOI_ERR_ARG, TOI_ERR_CUDA, TOI_ERR_OOM, TOI_ERR_EMPTY,
                       TOI_ERR_TIMEOUT, TOI_ERR_UNSUPPORTED, TOI_ERR_RANGE, TOI_VIS_C64,
                       TOI_VIS_C16_CHANSCALE, TOI_CAND_PERIODIC, TOI_CAND_NONPERIODIC,

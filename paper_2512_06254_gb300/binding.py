@@ -33,6 +33,8 @@ EXPORTS = ("toi_config_default", "toi_plan", "toi_plan_destroy", "toi_set_stream
            "tlisi_candidates_noalloc",
            "toi_degrid_backward", "toi_batch_prepare", "toi_batch_run", "toi_batch",
            "toi_autotune", "toi_mode3_info", "toi_localise_seed", "toi_localise",
+           "toi_stream_open", "toi_stream_push", "toi_stream_input_free", "toi_stream_pop",
+           "toi_stream_close",
            "toi_plan_buffer", "toi_profile_enable", "toi_profile_read",
            "toi_sync_status", "toi_last_error", "toi_status_string")
 PROF_STAGES = ("prep", "bin", "grid", "fft_rows", "fft_cols", "reproject", "tlisi", "backward",
@@ -94,6 +96,11 @@ def lib():
         "toi_mode3_info": [P, I, P],
         "toi_localise_seed": [P, I, P, I, P, P],
         "toi_localise": [P, I, I, P, P, P, P, P, P],
+        "toi_stream_open": [P, I, I, I, C.POINTER(C.c_void_p)],
+        "toi_stream_push": [P, P, C.POINTER(C.c_int64)],
+        "toi_stream_input_free": [P, C.c_int64, I, C.POINTER(I)],
+        "toi_stream_pop": [P, P, C.POINTER(C.c_int64), I, C.POINTER(I)],
+        "toi_stream_close": [P],
         "toi_plan_buffer": [P, I, I, P, C.c_int64, C.POINTER(C.c_int64)],
         "toi_profile_enable": [P, I],
         "toi_profile_read": [P, P, P, I],
@@ -390,3 +397,79 @@ def tlisi_candidates_noalloc(cube, tile: int, mode: int, max_boxes: int = 256, s
     n = min(nb.value, max_boxes)
     out = [[boxes[4 * i + j] for j in range(4)] for i in range(n)]
     return thr.value, out, nb.value
+
+
+class Stream:
+    """toi_stream_*: the native multi-stream snapshot pipeline of a plan
+    (grid_slots >= 3).  push() takes a dict of PINNED host tensors (uvw,
+    freq, vis, flag, weight, chan_scale); pop() returns (row index, float32
+    tensor [N/T, N/T]) of the oldest finished tLISI row, or None."""
+
+    def __init__(self, plan: Plan, host_depth: int = 8, n_copy: int = 4, with_weights: bool = False):
+        import torch
+        self._torch = torch
+        self.plan = plan
+        self.nt = plan.N // plan.T
+        h = C.c_void_p()
+        _check(lib().toi_stream_open(plan.handle, host_depth, n_copy, 1 if with_weights else 0,
+                                     C.byref(h)), plan.handle)
+        self.handle = h.value
+        self.host_depth = host_depth
+        self._inputs = {}
+        self.pushed = 0
+        self.popped = 0
+
+    @property
+    def pending_rows(self) -> int:
+        """tLISI rows produced (or in flight) and not yet popped."""
+        return max(0, self.pushed - 2) - self.popped
+
+    def push(self, snap) -> int:
+        t = self._torch
+        s = toi_snapshot()
+        for k in ("uvw", "freq", "vis", "flag", "weight", "chan_scale"):
+            x = snap.get(k)
+            if x is not None and (x.is_cuda or not x.is_pinned()):
+                raise ValueError(f"{k} must be a pinned host tensor")
+        s.uvw = _ptr(snap["uvw"])
+        s.freq = _ptr(snap["freq"])
+        s.vis = _ptr(snap["vis"])
+        s.flag = _ptr(snap.get("flag"))
+        s.weight = _ptr(snap.get("weight"))
+        s.chan_scale = _ptr(snap.get("chan_scale"))
+        s.n_bl = snap["uvw"].shape[0]
+        s.n_ch = snap["freq"].shape[0]
+        idx = C.c_int64(0)
+        _check(lib().toi_stream_push(self.handle, C.byref(s), C.byref(idx)), self.plan.handle)
+        self.pushed = idx.value + 1
+        # the host tensors stay referenced until their copies are done
+        self._inputs[idx.value] = snap
+        for k in [k for k in self._inputs if k < idx.value]:
+            if self.input_free(k):
+                del self._inputs[k]
+        del t
+        return idx.value
+
+    def input_free(self, index: int, wait: bool = False) -> bool:
+        f = C.c_int32(0)
+        _check(lib().toi_stream_input_free(self.handle, index, 1 if wait else 0, C.byref(f)),
+               self.plan.handle)
+        return bool(f.value)
+
+    def pop(self, wait: bool = True, out=None):
+        t = self._torch
+        row = t.empty(self.nt, self.nt, dtype=t.float32) if out is None else out
+        r = C.c_int64(0)
+        got = C.c_int32(0)
+        _check(lib().toi_stream_pop(self.handle, row.data_ptr(), C.byref(r), 1 if wait else 0,
+                                    C.byref(got)), self.plan.handle)
+        if got.value:
+            self.popped = r.value + 1
+            return r.value, row
+        return None
+
+    def close(self):
+        if self.handle:
+            _check(lib().toi_stream_close(self.handle), self.plan.handle)
+            self.handle = None
+            self._inputs.clear()

@@ -404,6 +404,17 @@ static toi_status check_snapshot(toi_plan_t p, const double* uvw_m, const double
   return TOI_OK;
 }
 
+}  // extern "C"
+
+namespace toi {
+toi_status validate_snapshot(toi_plan_s* p, const toi_snapshot& sn) {
+  return check_snapshot(p, sn.uvw, sn.freq, sn.vis, sn.chan_scale, sn.weight, sn.flag, sn.n_bl,
+                        sn.n_ch);
+}
+}  // namespace toi
+
+extern "C" {
+
 toi_status toi_grid(toi_plan_t p, const double* uvw_m, const double* freq_hz, const void* vis,
                     const float* chan_scale, const float* weight, const uint8_t* flag,
                     int32_t n_bl, int32_t n_ch, int32_t slot) {

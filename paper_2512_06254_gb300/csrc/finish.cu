@@ -377,6 +377,35 @@ cudaError_t launch_ring_moments(toi_plan_s* p, const float* image, int cur, int 
   return cudaGetLastError();
 }
 
+// Re-projection (+ tile moments) with explicit buffers, for the streaming
+// runtime's rings: tilted source, the new ring image and the two before it,
+// its maximum word and the tile moments of this window.
+cudaError_t launch_reproject_ring(toi_plan_s* p, Slot& s, const float* tilted, float* cur,
+                                  const float* prev1, const float* prev2, bool with_moments,
+                                  double* tile_mom, unsigned int* max_cur) {
+  cudaError_t e = cudaMemsetAsync(max_cur, 0, sizeof(unsigned int), p->stream);
+  if (e != cudaSuccess) return e;
+  const int ntl = (p->N / p->T) * (p->N / p->T);
+  const int tok = prof_begin(p, PROF_REPROJECT, 1);
+  image_tile_kernel<true><<<ntl, kFinThreads, 0, p->stream>>>(
+      tilted, p->N, p->T, s.snap, p->beta_rad, cur, prev1, prev2, nullptr, with_moments ? 1 : 0,
+      tile_mom, max_cur);
+  prof_end(p, tok);
+  return cudaGetLastError();
+}
+
+// tLISI of the window whose moments are in tile_mom and whose image maxima
+// are ring_max[cur], [prev1], [prev2].
+cudaError_t launch_tlisi_rows(toi_plan_s* p, const double* tile_mom, const unsigned int* ring_max,
+                              int cur, int prev1, int prev2, float* out) {
+  const int ntl = (p->N / p->T) * (p->N / p->T);
+  const int tok = prof_begin(p, PROF_TLISI, 1);
+  tlisi_finish_kernel<<<(ntl + 255) / 256, 256, 0, p->stream>>>(tile_mom, ntl, p->T, ring_max,
+                                                                cur, prev1, prev2, out);
+  prof_end(p, tok);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finish_batch(toi_plan_s* p) {
   const int ntl = (p->N / p->T) * (p->N / p->T);
   const int B = p->batch_max;
