@@ -177,7 +177,7 @@ def test_autograd_wrapper_and_argument_errors():
     plan.image(0, None)
     L = localise_loss(plan, win, s, weight=wt)
     (3.0 * L).backward()
-    assert float(L) == pytest.approx(direct["loss"].sum(), rel=1e-6)
+    assert float(L.detach()) == pytest.approx(direct["loss"].sum(), rel=1e-6)
     assert np.abs(s.grad.cpu().numpy() - 3.0 * direct["grad_src"]).max() <= \
         1e-5 * np.abs(direct["grad_src"]).max()
     assert wt.grad is not None and torch.isfinite(wt.grad).all()
