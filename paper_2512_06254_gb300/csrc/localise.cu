@@ -143,7 +143,9 @@ __global__ void loc_coef_kernel(const double* __restrict__ uvw, int nbl,
 constexpr int kChunk = 32;          // samples (channels) per chunk: one warp
 constexpr int kWG = 64;             // windows per block (blockIdx.y: window group)
 constexpr int kTaps = kW * kW;
-constexpr int kPassThreads = 256;
+constexpr int kPassThreads = 256;     // forward pass block
+constexpr int kRevThreads = 128;      // reverse pass block
+constexpr int kTRow = kTaps + 4;      // padded row of T [q][tap]: rows start 4 banks apart
 
 struct PassCtl {
   int o1, o2, active, more, flush;
@@ -212,7 +214,7 @@ __device__ __forceinline__ void build_pass(float* T, unsigned& pending, float g1
 #pragma unroll
   for (int y = 0; y < kW; ++y) {
     if (TQ) {
-      float4* row = reinterpret_cast<float4*>(T + lane * kTaps + y * kW);
+      float4* row = reinterpret_cast<float4*>(T + lane * kTRow + y * kW);
       row[0] = make_float4(wy[y] * wx[0], wy[y] * wx[1], wy[y] * wx[2], wy[y] * wx[3]);
       row[1] = make_float4(wy[y] * wx[4], wy[y] * wx[5], wy[y] * wx[6], wy[y] * wx[7]);
     } else {
@@ -233,13 +235,15 @@ __device__ __forceinline__ void build_pass(float* T, unsigned& pending, float g1
 // Block (baselines blockIdx.x, blockIdx.x + gridDim.x, ...; window group
 // blockIdx.y).  Thread t accumulates taps 4 (t / 16) .. + 3 for windows
 // 4 (t % 16) .. + 3 of the group.
-__global__ void __launch_bounds__(kPassThreads)
+__global__ void __launch_bounds__(kPassThreads, 3)
 loc_grid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
                 const float2* __restrict__ kp, const float* __restrict__ wq, int nbl, int nch,
                 const float4* __restrict__ coef, const int4* __restrict__ winfo, int nwin,
                 float beta_log2e, float2* __restrict__ facets) {
-  __shared__ __align__(16) float T[kChunk * kTaps];     // [q][tap]
-  __shared__ __align__(16) float2 C[kChunk * kWG];      // [q][w]: S_w E[q][w]
+  __shared__ __align__(16) float T[kChunk * kTRow];     // [q][tap], padded rows
+  // C[q] holds S_w E[q][w] for w = 4 b + j at [(j / 2) 32 + 2 b + j % 2]: the
+  // two float4 loads of a thread's four windows each cover 256 contiguous bytes
+  __shared__ __align__(16) float2 C[kChunk * kWG];
   __shared__ float2 Pw[kWG];
   __shared__ float Sw[kWG];
   __shared__ float2 kq[kChunk];
@@ -309,7 +313,8 @@ loc_grid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
         const int q = e >> 6, w = e & (kWG - 1);
         const float2 k = kq[q], P = Pw[w];
         const float2 ph = cis_turns(frac_turns(k.x, k.y, P.x, P.y));
-        C[e] = make_float2(Sw[w] * ph.x, Sw[w] * ph.y);
+        const int j = w & 3;
+        C[q * kWG + (j >> 1) * 32 + (w >> 2) * 2 + (j & 1)] = make_float2(Sw[w] * ph.x, Sw[w] * ph.y);
       }
       while (true) {
         if (t < kChunk) build_pass<true>(T, pending, g1, g2, W, o1, o2, have, beta_log2e, &ctl);
@@ -322,9 +327,9 @@ loc_grid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
         have = true;
 #pragma unroll 4
         for (int q = 0; q < kChunk; ++q) {
-          const float4 tv = *reinterpret_cast<const float4*>(T + q * kTaps + tb * 4);
-          const float4 ca = *reinterpret_cast<const float4*>(C + q * kWG + wb * 4);
-          const float4 cb = *reinterpret_cast<const float4*>(C + q * kWG + wb * 4 + 2);
+          const float4 tv = *reinterpret_cast<const float4*>(T + q * kTRow + tb * 4);
+          const float4 ca = *reinterpret_cast<const float4*>(C + q * kWG + wb * 2);
+          const float4 cb = *reinterpret_cast<const float4*>(C + q * kWG + 32 + wb * 2);
           const float tt[4] = {tv.x, tv.y, tv.z, tv.w};
           const float2 cc[4] = {make_float2(ca.x, ca.y), make_float2(ca.z, ca.w),
                                 make_float2(cb.x, cb.y), make_float2(cb.z, cb.w)};
@@ -487,14 +492,17 @@ __global__ void loc_dot_kernel(const double* __restrict__ loss2, int nwin, doubl
 
 // ------------------------------------------------------------- reverse ---
 
-// Block as loc_grid_kernel.  Per pass, thread t forms G for samples
-// 4 (t / 32) .. + 3 and windows 2 (t % 32), + 1 of the group, then
+// Block as loc_grid_kernel (kRevThreads threads).  Per pass, thread t forms G
+// for samples 4 (t / 16) .. + 3 and windows 4 (t % 16) .. + 3 of the group,
+// then
 //   zz = conj(G) E;  dS_w += W Re zz;  dl_w += S W k fl Im zz;  dm_w alike;
 //   A_q += S_w Re zz (the models' weight gradient, summed over the windows
 //   in shared memory and added to grad_weight per chunk).
 // The window sums are float per chunk, float64 across chunks; the block's
-// totals go to part[block][w][3] in a fixed order.
-__global__ void __launch_bounds__(kPassThreads)
+// totals go to part[block][w][3] in a fixed order.  Kf holds the footprint of
+// windows 4 b + j at [tap][(j / 2) 32 + 2 b + j % 2], so that a thread's two
+// float4 loads each read 256 contiguous bytes.
+__global__ void __launch_bounds__(kRevThreads, 4)
 loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
                   const float2* __restrict__ kp, const float* __restrict__ wq,
                   const uint8_t* __restrict__ flag, int nbl, int nch, int npol,
@@ -502,12 +510,12 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
                   const float2* __restrict__ Kall, float beta_log2e, double* __restrict__ part,
                   int nwin_part, float* __restrict__ grad_weight) {
   __shared__ __align__(16) float T2[kTaps * kChunk];    // [tap][q]
-  __shared__ __align__(16) float2 Kf[kTaps * kWG];      // [tap][w]; reused for the final sums
+  __shared__ __align__(16) float2 Kf[kTaps * kWG];      // see above; reused for the final sums
   __shared__ float4 Cf[kWG];
   __shared__ float Sw[kWG];
   __shared__ float2 kq[kChunk];
   __shared__ float Wsh[kChunk];
-  __shared__ float Ared[kChunk][33];
+  __shared__ float Ared[kChunk][17];
   __shared__ PassCtl ctl;
   const int t = threadIdx.x;
   const int wg0 = blockIdx.y * kWG;
@@ -517,8 +525,10 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
   }
   int pa, pb;
   hands(npol, pa, pb);
-  const int qb = t >> 5, wb = t & 31;
-  double sums[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  const int qb = t >> 4, wb = t & 15;
+  double sums[4][3];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sums[j][0] = sums[j][1] = sums[j][2] = 0.0;
   int o1 = 0, o2 = 0, k1 = -1 << 30, k2 = 0;     // pass origin, origin of the staged footprint
   bool have = false;
   for (int b = blockIdx.x; b < nbl; b += gridDim.x) {
@@ -546,10 +556,12 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
         g2 = fmaf(a2, k.x, fmaf(a2, k.y, 0.5f * kF));
         kq[t] = k;
         Wsh[t] = W;
-        for (int j = 0; j < 33; ++j) Ared[t][j] = 0.f;
+        for (int j = 0; j < 17; ++j) Ared[t][j] = 0.f;
         pending = __ballot_sync(0xffffffffu, W > 0.f);
       }
-      float cs[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      float cs[4][3];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cs[j][0] = cs[j][1] = cs[j][2] = 0.f;
       while (true) {
         // T without the sample weight: the epilogue applies W itself
         if (t < kChunk) build_pass<false>(T2, pending, g1, g2, 1.0f, o1, o2, have, beta_log2e, &ctl);
@@ -560,32 +572,39 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
         o2 = c.o2;
         have = true;
         if (o1 != k1 || o2 != k2) {     // stage the windows' footprints at this origin
-          for (int e = t; e < kTaps * kWG; e += kPassThreads) {
-            const int tap = e >> 6, w = wg0 + (e & (kWG - 1));
+          for (int e = t; e < kTaps * kWG; e += kRevThreads) {
+            const int tap = e >> 6, wl = e & (kWG - 1), w = wg0 + wl;
             const int y = tap >> 3, x = tap & 7;
-            Kf[e] = w < nwin ? __ldg(Kall + (size_t)w * kF * kF +
-                                     ((o2 + y) & (kF - 1)) * kF + ((o1 + x) & (kF - 1)))
-                             : make_float2(0.f, 0.f);
+            const int j = wl & 3;
+            Kf[tap * kWG + (j >> 1) * 32 + (wl >> 2) * 2 + (j & 1)] =
+                w < nwin ? __ldg(Kall + (size_t)w * kF * kF + ((o2 + y) & (kF - 1)) * kF +
+                                 ((o1 + x) & (kF - 1)))
+                         : make_float2(0.f, 0.f);
           }
           k1 = o1;
           k2 = o2;
           __syncthreads();
         }
-        float2 g[4][2];
+        float2 g[4][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) g[i][0] = g[i][1] = make_float2(0.f, 0.f);
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) g[i][j] = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int tap = 0; tap < kTaps; ++tap) {
           const float4 tv = *reinterpret_cast<const float4*>(T2 + tap * kChunk + qb * 4);
-          const float4 kv = *reinterpret_cast<const float4*>(Kf + tap * kWG + wb * 2);
+          const float4 ka = *reinterpret_cast<const float4*>(Kf + tap * kWG + wb * 2);
+          const float4 kb = *reinterpret_cast<const float4*>(Kf + tap * kWG + 32 + wb * 2);
           const float tt[4] = {tv.x, tv.y, tv.z, tv.w};
+          const float2 kk[4] = {make_float2(ka.x, ka.y), make_float2(ka.z, ka.w),
+                                make_float2(kb.x, kb.y), make_float2(kb.z, kb.w)};
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            g[i][0].x = fmaf(tt[i], kv.x, g[i][0].x);
-            g[i][0].y = fmaf(tt[i], kv.y, g[i][0].y);
-            g[i][1].x = fmaf(tt[i], kv.z, g[i][1].x);
-            g[i][1].y = fmaf(tt[i], kv.w, g[i][1].y);
-          }
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              g[i][j].x = fmaf(tt[i], kk[j].x, g[i][j].x);
+              g[i][j].y = fmaf(tt[i], kk[j].y, g[i][j].y);
+            }
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -594,9 +613,9 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
           const float Wq = Wsh[q];
           float ap = 0.f;
 #pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            const float4 cf = Cf[wb * 2 + j];
-            const float S = Sw[wb * 2 + j];
+          for (int j = 0; j < 4; ++j) {
+            const float4 cf = Cf[wb * 4 + j];
+            const float S = Sw[wb * 4 + j];
             const float2 e = cis_turns(frac_turns(k.x, k.y, cf.x, cf.y));
             // zz = conj(g) e
             const float zr = g[i][j].x * e.x + g[i][j].y * e.y;
@@ -613,7 +632,7 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
         if (!c.more) break;
       }
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
+      for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int m = 0; m < 3; ++m) sums[j][m] += (double)cs[j][m];
       __syncthreads();                // Ared complete
@@ -621,7 +640,7 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
         const int c = ch0 + t;
         if (c < nch && W > 0.f) {
           float A = 0.f;
-          for (int j = 0; j < 32; ++j) A += Ared[t][j];
+          for (int j = 0; j < 16; ++j) A += Ared[t][j];
           const size_t o = ((size_t)b * nch + c) * npol;
           if (!(flag && flag[o + pa])) grad_weight[o + pa] += A;
           if (pb != pa && !(flag && flag[o + pb])) grad_weight[o + pb] += A;
@@ -633,15 +652,15 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
   __syncthreads();
   double* red = reinterpret_cast<double*>(Kf);        // [8][64][3]
 #pragma unroll
-  for (int j = 0; j < 2; ++j)
+  for (int j = 0; j < 4; ++j)
 #pragma unroll
-    for (int m = 0; m < 3; ++m) red[(qb * kWG + wb * 2 + j) * 3 + m] = sums[j][m];
+    for (int m = 0; m < 3; ++m) red[(qb * kWG + wb * 4 + j) * 3 + m] = sums[j][m];
   __syncthreads();
-  for (int e = t; e < kWG * 3; e += kPassThreads) {
+  for (int e = t; e < kWG * 3; e += kRevThreads) {
     const int w = wg0 + e / 3;
     if (w >= nwin) continue;
     double acc = 0.0;
-    for (int i = 0; i < kPassThreads / 32; ++i) acc += red[i * kWG * 3 + e];
+    for (int i = 0; i < kChunk / 4; ++i) acc += red[i * kWG * 3 + e];
     part[((size_t)blockIdx.x * nwin_part + w) * 3 + e % 3] = acc;
   }
 }
@@ -814,7 +833,7 @@ cudaError_t launch_localise(toi_plan_s* p, Slot& s, int nwin, const int* win, co
     if ((e = launch_degrid_weights(p, s, p->loc_dot, grad_weight)) != cudaSuccess) return e;
   }
   if (grad_src || grad_weight) {
-    loc_degrid_kernel<<<pgrid, kPassThreads, 0, p->stream>>>(
+    loc_degrid_kernel<<<pgrid, kRevThreads, 0, p->stream>>>(
         s.coef, fscale, p->loc_k, p->loc_wq, s.flag, nbl, nch, npol, p->loc_coef, p->loc_win,
         nwin, p->loc_K, beta_log2e, p->loc_part, nwin, grad_weight);
     if (grad_src)
