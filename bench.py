@@ -749,7 +749,8 @@ def profile_case(args):
 
     import paper_2512_06254_gb300 as toi
     from paper_2512_06254_gb300 import synth
-    w = synth.meerkat_workload()
+    cell = args.fov_deg * 3600.0 / args.image_size if args.fov_deg else 2.0
+    w = synth.meerkat_workload(n_chan=args.channels, image_size=args.image_size, cell_arcsec=cell)
     p = synth.make_snapshot(w, 3, device="cuda", uvw_index=3)
     batch = args.engine == "batch"
     B = args.batch if batch else 0
