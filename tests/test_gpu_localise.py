@@ -240,3 +240,30 @@ def test_meerkat_windows_from_tlisi():
     eg = np.abs(gsrc[0].cpu().numpy() - ref["grad_src"][0]) / np.abs(ref["grad_src"][0])
     print(f"MeerKAT window 0: model {em:.2e} loss {el:.2e} grad_src {eg}")
     assert em < 1e-5 and el < 1e-4 and eg.max() < 1e-4
+
+
+def test_more_windows_than_one_group():
+    """70 windows (two window groups of the facet passes), two pols, no
+    weights: losses and source gradients of every window against the
+    oracle."""
+    w = _workload(n_ant=10, n_chan=40, N=256, n_pol=2, flag_frac=0.05)
+    sn = synth.make_snapshot(w, 4)
+    h = to_np(sn)
+    rng = np.random.default_rng(11)
+    windows = rng.integers(0, w.image_size - WIN + 1, size=(70, 2))
+    offs = [(float(a), float(b), float(S)) for a, b, S in
+            zip(rng.uniform(-3, 3, 70), rng.uniform(-3, 3, 70), rng.uniform(0.5, 2.0, 70))]
+    src = _sources(h, w, windows, offs)
+    plan = plan_for(w, max_windows=80)
+    d = to_dev(sn)
+    gpu_image(plan, d, out=False)
+    got = _run(plan, windows, src, weight_like=torch.empty(w.n_bl, w.n_chan, w.n_pol,
+                                                           device="cuda"))
+    plan.close()
+    ref = O.localise(h["uvw"], h["freq"], h["vis"], h["flag"], None, w.image_size,
+                     w.cell_arcsec, windows, src, WIN)
+    el = np.abs(got["loss"] - ref["loss"]).max() / np.abs(ref["loss"]).max()
+    eg = np.abs(got["grad_src"] - ref["grad_src"]) / np.abs(ref["grad_src"]).max(axis=0)
+    ew = rel_err(got["grad_weight"], ref["grad_weight"])
+    print(f"70 windows: loss {el:.2e} grad_src {eg.max():.2e} grad_weight {ew:.2e}")
+    assert el < 1e-4 and eg.max() < 1e-4 and ew < 1e-4
