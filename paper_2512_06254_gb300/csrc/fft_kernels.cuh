@@ -23,8 +23,9 @@
 // or radix-5 pass) whose butterflies run in registers,
 // twiddles from a float32 table e^{+2 pi i m / G} made in float64 at plan time
 // (three table reads per radix-8 butterfly, the other powers by products).
-// Shared memory is padded by one slot per eight to avoid bank conflicts of
-// the strided Stockham stores.
+// Shared memory is padded by one slot per sixteen: a half warp's run of 16
+// consecutive complex values then fills the 32 banks exactly, which keeps
+// every pass's loads and all but one radix-8 span's stores conflict-free.
 #pragma once
 #include "toi_internal.cuh"
 
@@ -34,7 +35,7 @@ enum FftOp { FFT_FORWARD, FFT_BATCH, FFT_ADJOINT };
 
 namespace {
 
-__device__ __forceinline__ int pad(int a) { return a + (a >> 3); }
+__device__ __forceinline__ int pad(int a) { return a + (a >> 4); }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -150,7 +151,7 @@ __device__ __forceinline__ void twiddles(const float2* __restrict__ tw, int step
 template <int G, int R, int BPT>
 __device__ __forceinline__ void stockham_pass(float2* x, int nseq, int Ns, const float2* __restrict__ tw) {
   constexpr int NB = G / R;       // butterflies per sequence
-  constexpr int LEN = G + G / 8;  // padded sequence length
+  constexpr int LEN = G + G / 16;  // padded sequence length
   float2 v[BPT][R];
   int jj[BPT], ss[BPT];
 #pragma unroll
@@ -294,7 +295,7 @@ struct ColCfg {
   static constexpr int NSEQ = G <= 8192 ? 2 : 1;
   static constexpr int CW = 2 * NSEQ;     // columns per block
   static constexpr int NT = 512;
-  static constexpr int LEN = G + G / 8;
+  static constexpr int LEN = G + G / 16;
 };
 
 template <int G>
@@ -451,7 +452,7 @@ fft_adj_rows_kernel(const float2* __restrict__ Y, int N, const float2* __restric
 
 template <int G>
 cudaError_t configure_g() {
-  const int row_smem = (G + G / 8) * (int)sizeof(float2);
+  const int row_smem = (G + G / 16) * (int)sizeof(float2);
   const int col_smem = ColCfg<G>::NSEQ * ColCfg<G>::LEN * (int)sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        row_smem);
@@ -475,7 +476,7 @@ void launch_batch_g(toi_plan_s* p) {
   const int N = p->N, B = p->batch_max;
   constexpr int CW = ColCfg<G>::CW;
   int tok = prof_begin(p, PROF_FFT_ROWS, 1);
-  fft_rows_batch<G><<<dim3(G / 2, B), RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
+  fft_rows_batch<G><<<dim3(G / 2, B), RowCfg<G>::NT, (G + G / 16) * sizeof(float2), p->stream>>>(
       p->bentry_dev, p->bheader_dev, N, p->twiddle);
   prof_end(p, tok);
   tok = prof_begin(p, PROF_FFT_COLS, 1);
@@ -490,7 +491,7 @@ void launch_adj_g(toi_plan_s* p, Slot& s) {
   constexpr int CW = ColCfg<G>::CW;
   fft_adj_cols_kernel<G><<<N / CW, ColCfg<G>::NT, ColCfg<G>::NSEQ * ColCfg<G>::LEN * sizeof(float2), p->stream>>>(
       p->tilted, N, p->twiddle, s.snap, p->fft_tmp);
-  fft_adj_rows_kernel<G><<<G / 2, RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
+  fft_adj_rows_kernel<G><<<G / 2, RowCfg<G>::NT, (G + G / 16) * sizeof(float2), p->stream>>>(
       p->fft_tmp, N, p->twiddle, s.snap, s.grid);
 }
 
@@ -498,7 +499,7 @@ template <int G>
 void launch_g(toi_plan_s* p, Slot& s, float* out) {
   const int N = p->N;
   int tok = prof_begin(p, PROF_FFT_ROWS, 1);
-  fft_rows_kernel<G><<<G / 2, RowCfg<G>::NT, (G + G / 8) * sizeof(float2), p->stream>>>(
+  fft_rows_kernel<G><<<G / 2, RowCfg<G>::NT, (G + G / 16) * sizeof(float2), p->stream>>>(
       s.grid, N, p->twiddle, s.snap, p->fft_tmp);
   prof_end(p, tok);
   tok = prof_begin(p, PROF_FFT_COLS, 1);
