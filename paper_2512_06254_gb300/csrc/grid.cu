@@ -64,9 +64,8 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // Exponential of semicircle psi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)) with
 // bl2 = beta * log2(e).
 __device__ __forceinline__ float es_kernel(float x, float bl2) {
-  const float z = x * (2.0f / kW);
-  const float t = fmaxf(1.0f - z * z, 0.0f);
-  return ex2_approx(bl2 * (sqrt_approx(t) - 1.0f));
+  const float t = fmaxf(fmaf(x * x, -4.0f / (kW * kW), 1.0f), 0.0f);   // 1 - (2x/W)^2
+  return ex2_approx(fmaf(bl2, sqrt_approx(t), -bl2));                  // bl2 (sqrt - 1)
 }
 
 __device__ __forceinline__ void red_add(float2* p, float2 v) {
