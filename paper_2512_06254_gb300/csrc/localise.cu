@@ -165,12 +165,11 @@ __global__ void loc_wq_kernel(const float* __restrict__ weight, const uint8_t* _
 // the hardware approximations of exp2 and sqrt (relative error ~1e-6, far
 // below the ES kernel's own error); beta_log2e = beta log2(e)
 __device__ __forceinline__ float psi_fast(float x, float beta_log2e) {
-  const float z = x * (2.0f / kW);
-  const float s = 1.0f - z * z;
+  const float s = fmaf(x * x, -4.0f / (kW * kW), 1.0f);   // 1 - (2x/W)^2
   if (!(s >= 0.f)) return 0.f;
   float r, e;
   asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(s));
-  asm("ex2.approx.f32 %0, %1;" : "=f"(e) : "f"(beta_log2e * (r - 1.0f)));
+  asm("ex2.approx.f32 %0, %1;" : "=f"(e) : "f"(fmaf(beta_log2e, r, -beta_log2e)));
   return e;
 }
 
