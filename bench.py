@@ -344,9 +344,26 @@ def run_ours(args):
         es = time.perf_counter() - e0
         sn.close()
         nplan.close()
+        # the host link alone: pinned host -> device copies of one snapshot's bytes
+        src_h = hpool_n[0]["vis"]
+        dst_d = torch.empty_like(src_h, device=dev)
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            dst_d.copy_(src_h, non_blocking=True)
+        l0.record()
+        for _ in range(5):
+            dst_d.copy_(src_h, non_blocking=True)
+        l1.record()
+        torch.cuda.synchronize()
+        link_gbs = 5 * src_h.numel() * src_h.element_size() / (l0.elapsed_time(l1) / 1e3) / 1e9
+        del dst_d
+        e2e_gbs = h2d / es / 1e9          # all timed observations' host -> device bytes
         e2e = {"value": round(S * args.e2e_steps * world / es, 2), "unit": "snapshots/s",
                "h2d_bytes_per_step": h2d // args.e2e_steps,
                "d2h_bytes_per_step": d2h // args.e2e_steps,
+               "h2d_gbs": round(e2e_gbs, 1), "link_h2d_gbs": round(link_gbs, 1),
+               "link_frac": round(e2e_gbs / link_gbs, 3),
                "host_pool_snapshots": args.host_pool, "copy_streams": args.copy_streams,
                "engine": "toi_stream (pipeline stages on their own CUDA streams, depth-3 "
                          "grid ring, depth-5 image ring)"}
