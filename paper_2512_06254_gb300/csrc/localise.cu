@@ -180,6 +180,37 @@ __device__ __forceinline__ float2 cis_turns(float f) {
   return make_float2(cs, sn);
 }
 
+// exp(2 pi i k_q P) for m consecutive samples q0 .. q0 + m - 1 of a chunk:
+// the first exactly (compensated k P), the others by the ratio
+// exp(2 pi i dk P) when the channels are equally spaced (to the float
+// resolution of dk P), else each one exactly.
+template <int M>
+__device__ __forceinline__ void phases(const float2* kq, int q0, float2 P, float2* e) {
+  const float2 k0 = kq[q0];
+  e[0] = cis_turns(frac_turns(k0.x, k0.y, P.x, P.y));
+  const float2 k1 = kq[q0 + 1];
+  const float dk = (k1.x - k0.x) + (k1.y - k0.y);
+  bool uniform = dk != 0.f;
+#pragma unroll
+  for (int i = 2; i < M; ++i) {
+    const float2 a = kq[q0 + i], b = kq[q0 + i - 1];
+    const float d = (a.x - b.x) + (a.y - b.y);
+    uniform = uniform && fabsf(d - dk) * fabsf(P.x) < 1e-7f;
+  }
+  if (uniform) {
+    const float2 z = cis_turns(frac_turns(dk, 0.f, P.x, P.y));
+#pragma unroll
+    for (int i = 1; i < M; ++i)
+      e[i] = make_float2(e[i - 1].x * z.x - e[i - 1].y * z.y, e[i - 1].x * z.y + e[i - 1].y * z.x);
+  } else {
+#pragma unroll
+    for (int i = 1; i < M; ++i) {
+      const float2 k = kq[q0 + i];
+      e[i] = cis_turns(frac_turns(k.x, k.y, P.x, P.y));
+    }
+  }
+}
+
 // Warp 0 (lane = sample of the chunk): choose the next origin among the
 // pending samples (the block's current origin first, so that a chunk that
 // continues it costs no flush), write the pass's T (0 for samples outside
@@ -308,12 +339,15 @@ loc_grid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
         pending = __ballot_sync(0xffffffffu, W > 0.f);
       }
       __syncthreads();                // kq and Pw written; the last chunk's T, C are read
-      for (int e = t; e < kChunk * kWG; e += kPassThreads) {
-        const int q = e >> 6, w = e & (kWG - 1);
-        const float2 k = kq[q], P = Pw[w];
-        const float2 ph = cis_turns(frac_turns(k.x, k.y, P.x, P.y));
-        const int j = w & 3;
-        C[q * kWG + (j >> 1) * 32 + (w >> 2) * 2 + (j & 1)] = make_float2(Sw[w] * ph.x, Sw[w] * ph.y);
+      {
+        // thread t: window t % 64, samples 8 (t / 64) .. + 7
+        const int w = t & (kWG - 1), q0 = (t >> 6) * 8;
+        float2 ph[8];
+        phases<8>(kq, q0, Pw[w], ph);
+        const int j = w & 3, col = (j >> 1) * 32 + (w >> 2) * 2 + (j & 1);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          C[(q0 + i) * kWG + col] = make_float2(Sw[w] * ph[i].x, Sw[w] * ph[i].y);
       }
       while (true) {
         if (t < kChunk) build_pass<true>(T, pending, g1, g2, W, o1, o2, have, beta_log2e, &ctl);
@@ -605,6 +639,12 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
               g[i][j].y = fmaf(tt[i], kk[j].y, g[i][j].y);
             }
         }
+        float2 eph[4][4];             // [window][sample]
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 cf = Cf[wb * 4 + j];
+          phases<4>(kq, qb * 4, make_float2(cf.x, cf.y), eph[j]);
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int q = qb * 4 + i;
@@ -615,7 +655,7 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
           for (int j = 0; j < 4; ++j) {
             const float4 cf = Cf[wb * 4 + j];
             const float S = Sw[wb * 4 + j];
-            const float2 e = cis_turns(frac_turns(k.x, k.y, cf.x, cf.y));
+            const float2 e = eph[j][i];
             // zz = conj(g) e
             const float zr = g[i][j].x * e.x + g[i][j].y * e.y;
             const float zi = g[i][j].x * e.y - g[i][j].y * e.x;
@@ -641,8 +681,17 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
           float A = 0.f;
           for (int j = 0; j < 16; ++j) A += Ared[t][j];
           const size_t o = ((size_t)b * nch + c) * npol;
-          if (!(flag && flag[o + pa])) grad_weight[o + pa] += A;
-          if (pb != pa && !(flag && flag[o + pb])) grad_weight[o + pb] += A;
+          // with several window groups, blocks of the same baseline add to the
+          // same records: atomically then (one group: plain, deterministic)
+          const bool shared = gridDim.y > 1;
+          if (!(flag && flag[o + pa])) {
+            if (shared) atomicAdd(grad_weight + o + pa, A);
+            else grad_weight[o + pa] += A;
+          }
+          if (pb != pa && !(flag && flag[o + pb])) {
+            if (shared) atomicAdd(grad_weight + o + pb, A);
+            else grad_weight[o + pb] += A;
+          }
         }
       }
     }
