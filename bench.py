@@ -139,6 +139,38 @@ def make_pool(w, P, device):
     return pool
 
 
+def parse_cpulist(text):
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        lo, _, hi = part.partition("-")
+        cpus.update(range(int(lo), int(hi or lo) + 1))
+    return cpus
+
+
+def bind_host_to_gpu(index):
+    """Run this process (and the threads it starts) on the CPU cores local to
+    GPU `index`, so that pinned host buffers are first touched on the GPU's own
+    memory node; returns the core list, or None when the topology is not
+    exposed."""
+    import torch
+    try:
+        prop = torch.cuda.get_device_properties(index)
+        dom = getattr(prop, "pci_domain_id", 0)
+        path = (f"/sys/bus/pci/devices/{dom:04x}:{prop.pci_bus_id:02x}:"
+                f"{prop.pci_device_id:02x}.0/local_cpulist")
+        with open(path) as f:
+            text = f.read()
+        cpus = parse_cpulist(text) & os.sched_getaffinity(0)
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+            return text.strip()
+    except (OSError, AttributeError, ValueError):
+        pass
+    return None
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -155,6 +187,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    host_cpus = bind_host_to_gpu(local)
     cell = args.fov_deg * 3600.0 / args.image_size if args.fov_deg else 2.0
     w = synth.meerkat_workload(n_snap=args.snapshots, n_chan=args.channels,
                                image_size=args.image_size, cell_arcsec=cell)
@@ -365,6 +398,7 @@ def run_ours(args):
                "h2d_gbs": round(e2e_gbs, 1), "link_h2d_gbs": round(link_gbs, 1),
                "link_frac": round(e2e_gbs / link_gbs, 3),
                "host_pool_snapshots": args.host_pool, "copy_streams": args.copy_streams,
+               "host_cpus": host_cpus,
                "engine": "toi_stream (pipeline stages on their own CUDA streams, depth-3 "
                          "grid ring, depth-5 image ring)"}
 
