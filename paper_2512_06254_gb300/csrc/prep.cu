@@ -15,8 +15,6 @@
 namespace toi {
 namespace {
 
-constexpr int kPrepThreads = 128;
-
 __device__ __forceinline__ void parallel_hands(int npol, int& pa, int& pb) {
   if (npol == 4) { pa = 0; pb = 3; }
   else if (npol == 2) { pa = 0; pb = 1; }
