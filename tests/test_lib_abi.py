@@ -60,6 +60,18 @@ def test_host_validation_without_gpu(libtoi):
     cfg = b.config_default(128, 2.0, 10, 10, 4)
     cfg.reserved[0] = 1
     assert L.toi_plan(C.byref(cfg), None, C.byref(h)) == libtoi.TOI_ERR_ARG
+    cfg = b.config_default(128, 2.0, 10, 10, 4)
+    cfg.max_windows = 257                                  # above 256
+    assert L.toi_plan(C.byref(cfg), None, C.byref(h)) == libtoi.TOI_ERR_ARG
     assert L.toi_grid(None, None, None, None, None, None, None, 1, 1, 0) == libtoi.TOI_ERR_ARG
+    assert L.toi_localise(None, 0, 1, None, None, None, None, None, None) == libtoi.TOI_ERR_ARG
+    assert L.toi_localise_seed(None, 0, None, 1, None, None) == libtoi.TOI_ERR_ARG
+    out = C.c_void_p()
+    assert L.toi_stream_open(None, 2, 1, 0, C.byref(out)) == libtoi.TOI_ERR_ARG
+    assert L.toi_stream_push(None, None, None) == libtoi.TOI_ERR_ARG
+    got = C.c_int32(0)
+    assert L.toi_stream_pop(None, None, None, 0, C.byref(got)) == libtoi.TOI_ERR_ARG
+    assert L.toi_stream_input_free(None, 0, 0, C.byref(got)) == libtoi.TOI_ERR_ARG
+    assert L.toi_stream_close(None) == libtoi.TOI_ERR_ARG
     assert L.tlisi_candidates(None, 1, 1, 1, 1, 0, None, None, None, None, 0, None) == libtoi.TOI_ERR_ARG
     assert L.toi_status_string(libtoi.TOI_ERR_RANGE)
