@@ -7,9 +7,14 @@ gridding, inverse FFT, grid correction, re-projection and tLISI (S1-S7),
 then the periodic candidate search over the 1498-slice tLISI cube (S8).
 Inputs are seeded synthetic snapshots resident in HBM (a pool of 40
 distinct snapshots = one pulsar period, each 297 MB, larger than L2); the
-metric is snapshots/s.  See the design doc for the roofline model.
+metric is snapshots/s.  The roofline of the dominant stage divides its
+algorithmic bytes (every input byte read once, every output byte written
+once) by its CUDA-event time.  The end-to-end number streams the same
+observation from pinned host memory through toi_stream_*.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  other workloads: --workload uneven | adjoint | localise; --mode 3;
+  --image-size N --fov-deg F --channels C
 """
 from __future__ import annotations
 
