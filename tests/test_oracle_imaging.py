@@ -170,7 +170,7 @@ def test_es_fourier_quadrature_vs_adaptive():
     for f in (0.0, 0.1, 0.23, 0.25):
         ref, _ = scipy.integrate.quad(lambda x: float(O.es_kernel(x, W, beta)) *
                                       math.cos(2 * math.pi * x * f), -W / 2, W / 2,
-                                      epsabs=1e-15, epsrel=1e-14, limit=400)
+                                      epsabs=0.0, epsrel=1e-13, limit=400)
         assert O.es_fourier([f], W, beta)[0] == pytest.approx(ref, rel=1e-12)
 
 
