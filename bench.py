@@ -65,11 +65,11 @@ ALG_BYTES = alg_bytes()
 
 # DRAM bytes (read + write) per snapshot of the gridder, from an ncu capture
 # of the profile case (dram__bytes_read.sum + dram__bytes_write.sum): the
-# batched kernel over 16 references to one MeerKAT-shaped snapshot (4987 +
+# batched kernel over 16 references to one MeerKAT-shaped snapshot (4988 +
 # 186 MB; each reference streams its visibilities again, L2 being smaller
 # than them).  A launch's traffic is this times the snapshots it grids.  The
 # single-snapshot kernel has not been captured in its current form.
-GRID_DRAM_BYTES_PER_SNAPSHOT = {"batch": 5173.7e6 / 16, "single": None}
+GRID_DRAM_BYTES_PER_SNAPSHOT = {"batch": 5174.2e6 / 16, "single": None}
 
 
 def load_peaks():
