@@ -253,6 +253,16 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
   toi_status st = TOI_OK;
   cudaError_t e = toi::fft_configure(G);
   if (e != cudaSuccess) { toi_status r = cuda_fail(nullptr, e, "configuring FFT kernels"); free_plan(p); return r; }
+  {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || p->nsm < 1) {
+      toi_status r = cuda_fail(nullptr, e == cudaSuccess ? cudaErrorInvalidDevice : e, "device query");
+      free_plan(p);
+      return r;
+    }
+  }
   p->slots = new (std::nothrow) Slot[p->nslot];
   if (!p->slots) { free_plan(p); return fail(nullptr, TOI_ERR_OOM, "host allocation failed"); }
 #define TOI_ALLOC(ptr, n, what) \
@@ -297,7 +307,7 @@ toi_status toi_plan(const toi_config* cfg, void* cuda_stream, toi_plan_t* out) {
     TOI_ALLOC(p->loc_corr, (size_t)TOI_LOC_WINDOW, "facet correction");
     TOI_ALLOC(p->loc_loss2, nw, "window losses");
     TOI_ALLOC(p->loc_dot, 1, "localisation dot");
-    TOI_ALLOC(p->loc_part, toi::loc_part_doubles(c.max_baselines, c.max_channels, c.max_windows),
+    TOI_ALLOC(p->loc_part, toi::loc_part_doubles(c.max_baselines, c.max_windows, p->nsm),
               "localisation partial sums");
     TOI_ALLOC(p->loc_keys, (size_t)4096, "window selection keys");
     TOI_ALLOC(p->loc_tiles, nw, "selected tiles");

@@ -57,12 +57,6 @@ __global__ void dot_final_kernel(const double* __restrict__ part, int nb, double
   if (threadIdx.x == 0) *out = acc;
 }
 
-__device__ __forceinline__ void parallel_hands(int npol, int& pa, int& pb) {
-  if (npol == 4) { pa = 0; pb = 3; }
-  else if (npol == 2) { pa = 0; pb = 1; }
-  else { pa = 0; pb = 0; }
-}
-
 // psi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)) for |x| <= W/2, else 0
 __device__ __forceinline__ float es_psi(float x, float beta) {
   const float z = x * (2.0f / kW);

@@ -72,12 +72,6 @@ __device__ __forceinline__ void red_add(float2* p, float2 v) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y));
 }
 
-__device__ __forceinline__ void parallel_hands(int npol, int& pa, int& pb) {
-  if (npol == 4) { pa = 0; pb = 3; }
-  else if (npol == 2) { pa = 0; pb = 1; }
-  else { pa = 0; pb = 0; }
-}
-
 template <bool HALF>
 __device__ __forceinline__ float2 load_vis(const void* vis, size_t idx, float scale) {
   if (HALF) {

@@ -42,16 +42,10 @@ namespace {
 constexpr int kWin = TOI_LOC_WINDOW;   // window side (pixels)
 constexpr int kF = 2 * kWin;           // facet grid side (cells)
 constexpr int kW = 8;                  // ES kernel support
-constexpr int kMaxPassBlocks = 4 * 152;   // facet passes: blocks over the baselines
+constexpr int kPassBlocksPerSM = 4;       // facet passes: blocks over the baselines
 constexpr int kFinThreads = 256;
 constexpr int kSortKeys = 2048;        // keys per block of the window selection
 constexpr int kMergeKeys = 4096;
-
-__device__ __forceinline__ void hands(int npol, int& pa, int& pb) {
-  if (npol == 4) { pa = 0; pb = 3; }
-  else if (npol == 2) { pa = 0; pb = 1; }
-  else { pa = 0; pb = 0; }
-}
 
 // Sample weight W_q = w_a + w_b of the parallel hands (0: not selected).
 __device__ __forceinline__ float sample_weight(const float* __restrict__ weight,
@@ -157,7 +151,7 @@ __global__ void loc_wq_kernel(const float* __restrict__ weight, const uint8_t* _
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long long)nbl * nch) return;
   int pa, pb;
-  hands(npol, pa, pb);
+  parallel_hands(npol, pa, pb);
   wq[q] = sample_weight(weight, flag, (size_t)q * npol, pa, pb);
 }
 
@@ -557,7 +551,7 @@ loc_degrid_kernel(const BaselineCoef* __restrict__ bcoef, double fscale,
     Sw[t] = (w < nwin && winfo[w].w) ? __int_as_float(winfo[w].z) : 0.f;
   }
   int pa, pb;
-  hands(npol, pa, pb);
+  parallel_hands(npol, pa, pb);
   const int qb = t >> 4, wb = t & 15;
   double sums[4][3];
 #pragma unroll
@@ -826,9 +820,9 @@ __global__ void seed_window_kernel(const int* __restrict__ tiles, int ntx, int T
 
 }  // namespace
 
-size_t loc_part_doubles(int max_bl, int max_ch, int max_win) {
-  (void)max_ch;
-  const int blocks = max_bl < kMaxPassBlocks ? max_bl : kMaxPassBlocks;
+size_t loc_part_doubles(int max_bl, int max_win, int nsm) {
+  const int cap = kPassBlocksPerSM * nsm;
+  const int blocks = max_bl < cap ? max_bl : cap;
   return (size_t)blocks * max_win * 3;
 }
 
@@ -861,7 +855,8 @@ cudaError_t launch_localise(toi_plan_s* p, Slot& s, int nwin, const int* win, co
   loc_coef_kernel<<<dim3((nbl + 127) / 128, nwin), 128, 0, p->stream>>>(
       s.uvw, nbl, s.snap, win, src, nwin, p->N, p->beta_rad, p->loc_coef, p->loc_win, p->d_status);
   const float beta_log2e = (float)(p->beta_es * 1.4426950408889634);
-  const int nblk = nbl < kMaxPassBlocks ? nbl : kMaxPassBlocks;
+  const int cap = kPassBlocksPerSM * p->nsm;
+  const int nblk = nbl < cap ? nbl : cap;
   const dim3 pgrid(nblk, (nwin + kWG - 1) / kWG);
   loc_grid_kernel<<<pgrid, kPassThreads, 0, p->stream>>>(
       s.coef, fscale, p->loc_k, p->loc_wq, nbl, nch, p->loc_coef, p->loc_win, nwin, beta_log2e,

@@ -65,12 +65,6 @@ __global__ void m3_init_kernel(double* m3) {
   for (int i = 0; i < 4; ++i) reinterpret_cast<unsigned long long*>(m3)[M3_ERRK + i] = 0ull;
 }
 
-__device__ __forceinline__ void parallel_hands(int npol, int& pa, int& pb) {
-  if (npol == 4) { pa = 0; pb = 3; }
-  else if (npol == 2) { pa = 0; pb = 1; }
-  else { pa = 0; pb = 0; }
-}
-
 // r3 (wavelengths) range over the selected samples (w_q > 0, as the plane fit)
 __global__ void m3_r3_range_kernel(const BaselineCoef* __restrict__ coef,
                                    const double* __restrict__ kch, const uint8_t* __restrict__ flag,
@@ -310,7 +304,7 @@ cudaError_t mode3_select(toi_plan_s* p, Slot& s, const float* weight, const uint
                          int nbl, int nch) {
   double* m3 = p->m3_dev;
   m3_init_kernel<<<1, 1, 0, p->stream>>>(m3);
-  m3_r3_range_kernel<<<2 * 152 * 4, 256, 0, p->stream>>>(s.coef, p->kch, flag, weight, nbl, nch,
+  m3_r3_range_kernel<<<8 * p->nsm, 256, 0, p->stream>>>(s.coef, p->kch, flag, weight, nbl, nch,
                                                          p->cfg.n_pol, m3);
   const dim3 g((p->N + 15) / 16, (p->N + 15) / 16);
   m3_t3max_kernel<<<g, 256, 0, p->stream>>>(s.snap, p->N, p->beta_rad, m3);

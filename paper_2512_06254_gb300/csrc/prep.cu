@@ -15,12 +15,6 @@
 namespace toi {
 namespace {
 
-__device__ __forceinline__ void parallel_hands(int npol, int& pa, int& pb) {
-  if (npol == 4) { pa = 0; pb = 3; }
-  else if (npol == 2) { pa = 0; pb = 1; }
-  else { pa = 0; pb = 0; }
-}
-
 // Fixed-order block reduction of `n` doubles per thread (tree over threads).
 template <int NT, int NV>
 __device__ void block_reduce(double (&v)[NV], double* sh) {

@@ -187,6 +187,7 @@ struct toi_plan_s {
   int grid_blocks = 0;                      // persistent gridder: resident blocks
   int tuned_run[4] = {0, 0, 0, 0};          // autotuned lane runs per channel bucket
   int batch_rows = 4;                       // window rows per lane of the batch gridder
+  int nsm = 0;                              // SMs of the plan's device
 
   // localisation (toi_localise*): max_windows windows
   int tilted_slot = -1;                     // slot whose image p->tilted holds (-1: none)
@@ -252,7 +253,7 @@ cudaError_t launch_degrid_backward(toi_plan_s* p, Slot& s, const float* grad_ima
                                    float* grad_weight);
 
 // localise.cu
-size_t loc_part_doubles(int max_bl, int max_ch, int max_win);
+size_t loc_part_doubles(int max_bl, int max_win, int nsm);
 int loc_seed_max_tiles(int nwin);
 cudaError_t launch_localise_seed(toi_plan_s* p, Slot& s, const float* tlisi, int nwin, int* win,
                                  double* src);
@@ -269,6 +270,14 @@ void prof_end(toi_plan_s* p, int token);
 // Device helpers -----------------------------------------------------------
 __device__ __forceinline__ void set_status(int* st, int code) {
   atomicCAS(st, 0, code);
+}
+
+// Parallel-hand polarisations (reading c13): XX,XY,YX,YY -> 0 and 3; two pols
+// -> 0 and 1; Stokes I -> 0 (pa == pb).
+__device__ __forceinline__ void parallel_hands(int npol, int& pa, int& pb) {
+  if (npol == 4) { pa = 0; pb = 3; }
+  else if (npol == 2) { pa = 0; pb = 1; }
+  else { pa = 0; pb = 0; }
 }
 
 }  // namespace toi
