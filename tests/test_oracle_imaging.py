@@ -42,6 +42,19 @@ def test_svd_planted_plane_normal():
     assert abs(V[0, 1] - (-(n[0] * n[1]) / math.sqrt(1 - n[0] ** 2))) < 1e-12
 
 
+def test_omega_is_the_cofactor_for_any_rotation():
+    """Eq. 11 for a general basis: every entry of a rotation matrix equals its
+    cofactor, so omega = |V11 V22 - V21 V12| = |V33| for any V with det +1.
+    Random rotations have V21 != 0, which svd_basis's own convention (v1 in
+    the u-w plane) never produces."""
+    rng = np.random.default_rng(14)
+    for _ in range(20):
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        V = q if np.linalg.det(q) > 0 else -q
+        assert abs(V[1, 0]) > 1e-3 or abs(V[0, 1]) > 1e-3
+        assert O.omega_of(V) == pytest.approx(abs(V[2, 2]), abs=1e-14)
+
+
 def test_svd_coplanar_identity():
     """Exactly coplanar baselines (all w = 0): V = I, omega = 1, xi = eta = 0."""
     rng = np.random.default_rng(6)
@@ -69,6 +82,26 @@ def test_svd_matches_covariance_eigenvectors():
     ev, evec = np.linalg.eigh(C)
     n = evec[:, 0] * np.sign(evec[2, 0])
     assert np.allclose(p["V"][2], n, atol=1e-9)
+
+
+def test_flagged_samples_do_not_move_the_plane():
+    """Section 3.5 (reading c4): only selected samples (w_q > 0) enter the
+    plane fit, so a fully flagged baseline far off the plane leaves V the
+    plane's own basis."""
+    rng = np.random.default_rng(13)
+    a, b = -0.12, 0.05
+    u = rng.uniform(-3e3, 3e3, 40)
+    v = rng.uniform(-3e3, 3e3, 40)
+    uvw = np.stack([u, v, a * u + b * v], 1)          # a plane through the origin
+    uvw[7] = [500.0, -800.0, 2500.0]                  # off the plane, fully flagged
+    freq = np.linspace(1.0e9, 1.1e9, 6)
+    vis = np.ones((40, 6, 1), np.complex64)
+    flag = np.zeros((40, 6, 1), np.uint8)
+    flag[7] = 1
+    p = O.prepare(uvw, freq, vis, flag)
+    n = np.array([-a, -b, 1.0]) / math.sqrt(1 + a * a + b * b)
+    assert np.allclose(p["V"][2], n, atol=1e-12)
+    assert p["n_vis"] == 39 * 6
 
 
 def test_sample_weights_pol_average_by_hand():

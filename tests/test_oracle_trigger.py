@@ -124,10 +124,25 @@ def test_periodogram_matches_fft():
     assert np.allclose(sc, ref, rtol=1e-11)
 
 
+def test_periodic_score_at_the_highest_frequency():
+    """A series alternating 5/8, 3/8 over an even S puts all its power at
+    f = F = S/2: x_t - mean = (-1)^t / 8, so A_F = S/8, B_F = 0 and every other
+    P_f = 0.  The best harmonic sum is then h = 1 at f = F, score (S/8)^2,
+    exact in binary64 (the twiddles there are exactly +-1 and 0)."""
+    S = 40
+    t = np.arange(S)
+    series = np.where(t % 2 == 0, 0.625, 0.375).astype(np.float32)
+    cube = np.repeat(series[:, None, None], 6, axis=1).reshape(S, 2, 3)
+    assert np.all(O.periodic_scores(cube) == (S / 8.0) ** 2)
+
+
 def test_pairwise_sum_tree():
     a = [1e16, 1.0, -1e16, 1.0]
     # ((1e16 + 1) + (-1e16 + 1)) with binary64 rounding
     assert O.pairwise_sum(a) == (1e16 + 1.0) + (-1e16 + 1.0)
+    # an odd count splits below the middle: 1 + (1e16 - 1e16) = 1, where the
+    # other split would round 1 + 1e16 to 1e16 and give 0
+    assert O.pairwise_sum([1.0, 1e16, -1e16]) == 1.0
     rng = np.random.default_rng(11)
     v = rng.normal(size=1001)
     assert O.pairwise_sum(v) == pytest.approx(math.fsum(v), abs=1e-12)
@@ -173,8 +188,23 @@ def test_connected_boxes_by_hand():
     assert lab[1, 6] == 0 * 7 + 5 and lab[4, 2] == 3 * 7 + 1
 
 
+def test_threshold_by_hand():
+    """Reading c11, population moments: scores 1, 2, 3, 4 have mean 5/2 and
+    variance 5/4, so thr = 5/2 + k sqrt(5/4) (every step exact in binary64
+    but the square root)."""
+    thr, mu, sd = O.threshold(np.array([1.0, 2.0, 3.0, 4.0]), 5.0)
+    assert mu == 2.5 and sd == math.sqrt(1.25)
+    assert thr == 2.5 + 5.0 * math.sqrt(1.25)
+
+
 def test_threshold_strict_and_flat():
     sc = np.ones(16)
     thr, mu, sd = O.threshold(sc, 5.0)
     assert thr == 1.0 and sd == 0.0
     assert not (sc > thr).any()
+    # a flat cube has no outlier: every tile's score equals the threshold
+    # (16 equal scores sum exactly), and a candidate must exceed it
+    flat = np.full((12, 4, 4), 0.9, np.float32)
+    for mode in (O.MODE_PERIODIC, O.MODE_NONPERIODIC):
+        r = O.candidates(flat, 32, mode)
+        assert r["std"] == 0.0 and r["mask"].sum() == 0 and r["boxes"] == []
