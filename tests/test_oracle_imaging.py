@@ -269,6 +269,26 @@ def test_reprojection_gather_inverts_map():
     assert np.abs(m2 - jo[:, None]).max() < 1e-9
 
 
+def test_reproject_moves_a_point_where_the_wcs_route_maps_it():
+    """reproject() as a whole, cell given in arcsec: a single bright tilted
+    pixel lands, as the centroid of the gathered output, where Appendix A's
+    WCS route maps that pixel (within 0.02 px; the shifts are up to ~1 px at
+    this field and tilt)."""
+    N, cell = 256, 60.0
+    xi, eta = 0.3, -0.2
+    yy, xx = np.mgrid[0:N, 0:N]
+    largest = 0.0
+    for j2, j1 in ((230, 20), (30, 200), (200, 140)):
+        img = np.zeros((N, N))
+        img[j2, j1] = 1.0
+        out = O.reproject(img, cell, xi, eta)
+        c2, c1 = (out * yy).sum() / out.sum(), (out * xx).sum() / out.sum()
+        m1, m2 = O.reproject_map_wcs(j1 + 1.0, j2 + 1.0, N, cell / 3600.0, xi, eta)
+        assert abs(c1 - (float(m1) - 1)) < 0.02 and abs(c2 - (float(m2) - 1)) < 0.02
+        largest = max(largest, np.hypot(float(m1) - 1 - j1, float(m2) - 1 - j2))
+    assert largest > 0.5
+
+
 def test_bilinear_exact_on_planes():
     """Bilinear interpolation reproduces a linear function exactly inside."""
     N = 16

@@ -138,6 +138,9 @@ CASES = [
     ("fixed-point step with the wrong sign", "reproject_source_at",
      "p1 = p1o - (m1 - p1)", "p1 = p1o + (m1 - p1)",
      TI.test_reprojection_gather_inverts_map),
+    ("cell converted from arcminutes instead of arcseconds", "reproject",
+     "cell_arcsec / 3600.0", "cell_arcsec / 60.0",
+     TI.test_reproject_moves_a_point_where_the_wcs_route_maps_it),
     ("interpolation weights of the two axes swapped", "bilinear",
      "v = ((1 - fb) * ((1 - fa) * pad[b0c, a0c] + fa * pad[b0c, a0c + 1]) +",
      "v = ((1 - fa) * ((1 - fb) * pad[b0c, a0c] + fb * pad[b0c, a0c + 1]) +",
@@ -273,6 +276,7 @@ CASES = [
 ]
 
 
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")    # a mutant may produce NaN
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_pin_catches_planted_mistake(case, monkeypatch):
     _, name, old, new, pin = case
