@@ -151,8 +151,19 @@ def _stream(stream):
 
 def _check(status: int, plan=None):
     if status != TOI_OK:
-        msg = lib().toi_last_error(plan).decode() if plan is not None or True else ""
-        raise ToiError(status, msg)
+        raise ToiError(status, lib().toi_last_error(plan).decode())
+
+
+def _need(x, nbytes: int, name: str):
+    """The C calls receive bare addresses and cannot see the extent behind
+    them, so a tensor smaller than what a call reads or writes (the layouts
+    of toi.h) is refused here with TOI_ERR_ARG, before any launch.  Raw
+    integer addresses are the caller's responsibility."""
+    if x is None or isinstance(x, int):
+        return
+    have = x.numel() * x.element_size()
+    if have < nbytes:
+        raise ToiError(TOI_ERR_ARG, f"{name} holds {have} bytes; the call needs {nbytes}")
 
 
 def config_default(image_size, cell_arcsec, max_baselines, max_channels, n_pol) -> toi_config:
@@ -188,6 +199,39 @@ class Plan:
         self.handle = h.value
         self._torch = torch
         self._generation = [0] * grid_slots
+        self._set_extents(max_baselines, max_channels, n_pol, vis_dtype, batch_max)
+
+    # ------------------------------------------------- extent checks (host)
+    def _set_extents(self, max_bl, max_ch, n_pol, vis_dtype, batch_max):
+        self.max_bl, self.max_ch, self.npol = max_bl, max_ch, n_pol
+        self.half = vis_dtype == TOI_VIS_C16_CHANSCALE
+        self.batch_max = batch_max
+        self.nt = self.N // self.T
+        self._slot_dims = {}          # slot -> (n_bl, n_ch) of its last grid call
+
+    def _in_limits(self, nbl, nch) -> bool:
+        """Counts the library accepts; others are refused by its own checks
+        before it touches any buffer."""
+        return 0 < nbl <= self.max_bl and 0 < nch <= self.max_ch
+
+    def _need_inputs(self, nbl, nch, uvw, freq, vis, chan_scale, weight, flag, who=""):
+        rec = nbl * nch * self.npol
+        _need(uvw, 24 * nbl, who + "uvw")
+        _need(freq, 8 * nch, who + "freq")
+        _need(vis, rec * (4 if self.half else 8), who + "vis")
+        _need(chan_scale, 4 * nch, who + "chan_scale")
+        _need(weight, 4 * rec, who + "weight")
+        _need(flag, rec, who + "flag")
+
+    def _need_per_record(self, slot, grad_sample=None, grad_vis=None, grad_weight=None):
+        dims = self._slot_dims.get(slot)
+        if dims is None:              # gridded elsewhere (batch): nothing known here
+            return
+        nbl, nch = dims
+        rec = nbl * nch * self.npol
+        _need(grad_sample, 8 * nbl * nch, "grad_sample")
+        _need(grad_vis, 8 * rec, "grad_vis")
+        _need(grad_weight, 4 * rec, "grad_weight")
 
     # ---------------------------------------------------------------- calls
     def set_stream(self, stream):
@@ -198,11 +242,14 @@ class Plan:
         t = self._torch
         nbl = n_bl if n_bl is not None else uvw.shape[0]
         nch = n_ch if n_ch is not None else freq.shape[0]
+        if self._in_limits(nbl, nch):
+            self._need_inputs(nbl, nch, uvw, freq, vis, chan_scale, weight, flag)
         _check(lib().toi_grid(self.handle, _dev(uvw, t.float64, "uvw"), _dev(freq, t.float64, "freq"),
                               _dev(vis, None, "vis"), _dev(chan_scale, t.float32, "chan_scale"),
                               _dev(weight, t.float32, "weight"), _dev(flag, t.uint8, "flag"),
                               nbl, nch, slot), self.handle)
         self._generation[slot] += 1
+        self._slot_dims[slot] = (nbl, nch)
 
     def slot_generation(self, slot: int = 0) -> int:
         """Number of toi_grid calls made on `slot` through this object."""
@@ -210,11 +257,15 @@ class Plan:
 
     def image(self, slot: int = 0, out=None, snap_info=None):
         t = self._torch
+        _need(out, 4 * self.N * self.N, "image")
+        _need(snap_info, 8 * 16, "snap_info")
         _check(lib().toi_image(self.handle, slot, _dev(out, t.float32, "image"),
                                _dev(snap_info, t.float64, "snap_info")), self.handle)
         return out
 
     def tlisi_update(self, image=None, out=None) -> bool:
+        _need(image, 4 * self.N * self.N, "image")
+        _need(out, 4 * self.nt * self.nt, "tlisi")
         valid = C.c_int32(0)
         _check(lib().tlisi_update(self.handle, _dev(image, None, "image"), _dev(out, None, "tlisi"),
                                   C.byref(valid)), self.handle)
@@ -230,6 +281,9 @@ class Plan:
         float32 grad_weight [n_bl, n_ch, n_pol]; image is toi_image's float32
         output, needed for grad_weight)."""
         t = self._torch
+        _need(grad_image, 4 * self.N * self.N, "grad_image")
+        _need(image, 4 * self.N * self.N, "image")
+        self._need_per_record(slot, grad_sample, grad_vis, grad_weight)
         _check(lib().toi_degrid_backward(
             self.handle, slot, _dev(grad_image, t.float32, "grad_image"),
             _dev(image, t.float32, "image"), _dev(grad_sample, t.complex64, "grad_sample"),
@@ -243,6 +297,10 @@ class Plan:
         t = self._torch
         win = t.empty(n_win, 2, dtype=t.int32, device="cuda") if win is None else win
         src = t.empty(n_win, 3, dtype=t.float64, device="cuda") if src is None else src
+        _need(tlisi, 4 * self.nt * self.nt, "tlisi")
+        if n_win > 0:
+            _need(win, 8 * n_win, "win")
+            _need(src, 24 * n_win, "src")
         _check(lib().toi_localise_seed(self.handle, slot, _dev(tlisi, t.float32, "tlisi"), n_win,
                                        _dev(win, t.int32, "win"), _dev(src, t.float64, "src")),
                self.handle)
@@ -254,6 +312,12 @@ class Plan:
         float64 loss [n_win], float64 grad_src [n_win, 3], float32
         grad_weight [n_bl, n_ch, n_pol])."""
         t = self._torch
+        n = win.shape[0]
+        _need(src, 24 * n, "src")
+        _need(model, 4 * n * LOC_WINDOW * LOC_WINDOW, "model")
+        _need(loss, 8 * n, "loss")
+        _need(grad_src, 24 * n, "grad_src")
+        self._need_per_record(slot, grad_weight=grad_weight)
         _check(lib().toi_localise(
             self.handle, slot, win.shape[0], _dev(win, t.int32, "win"), _dev(src, t.float64, "src"),
             _dev(model, t.float32, "model"), _dev(loss, t.float64, "loss"),
@@ -265,6 +329,12 @@ class Plan:
         """toi_snapshot array for a list of dicts (uvw, freq, vis, flag,
         weight, chan_scale, image); the tensors are kept referenced."""
         t = self._torch
+        for i, d in enumerate(snaps):           # every snapshot checked before any is marshalled
+            nbl, nch = d["uvw"].shape[0], d["freq"].shape[0]
+            if self._in_limits(nbl, nch):
+                self._need_inputs(nbl, nch, d["uvw"], d["freq"], d["vis"], d.get("chan_scale"),
+                                  d.get("weight"), d.get("flag"), f"snapshot {i}: ")
+            _need(d.get("image"), 4 * self.N * self.N, f"snapshot {i}: image")
         arr = (toi_snapshot * len(snaps))()
         for i, d in enumerate(snaps):
             arr[i].uvw = _dev(d["uvw"], t.float64, "uvw")
@@ -279,8 +349,13 @@ class Plan:
         self._batch_refs = list(snaps)
         return arr
 
+    def _need_rows(self, snaps, tlisi):
+        if 0 < len(snaps) <= self.batch_max:
+            _need(tlisi, 4 * len(snaps) * self.nt * self.nt, "tlisi")
+
     def batch_prepare(self, snaps, tlisi=None) -> int:
         """toi_batch_prepare; returns first_valid."""
+        self._need_rows(snaps, tlisi)
         arr = self._snapshots(snaps)
         fv = C.c_int32(0)
         _check(lib().toi_batch_prepare(self.handle, C.cast(arr, C.c_void_p), len(snaps),
@@ -293,6 +368,7 @@ class Plan:
 
     def batch(self, snaps, tlisi=None) -> int:
         """toi_batch (prepare + run); returns first_valid."""
+        self._need_rows(snaps, tlisi)
         arr = self._snapshots(snaps)
         fv = C.c_int32(0)
         _check(lib().toi_batch(self.handle, C.cast(arr, C.c_void_p), len(snaps),
@@ -369,6 +445,7 @@ def tlisi_candidates(cube, tile: int, mode: int, max_boxes: int = 256, scores=No
     if cube.dtype != torch.float32 or not cube.is_cuda or cube.dim() != 3:
         raise ValueError("cube must be a 3-D float32 CUDA tensor")
     S, nty, ntx = cube.shape
+    _need(scores, 8 * nty * ntx, "scores")
     thr = C.c_double()
     nb = C.c_int32()
     boxes = (C.c_int32 * (4 * max(1, max_boxes)))()
@@ -388,6 +465,7 @@ def tlisi_candidates_noalloc(cube, tile: int, mode: int, max_boxes: int = 256, s
     if cube.dtype != torch.float32 or not cube.is_cuda or cube.dim() != 3:
         raise ValueError("cube must be a 3-D float32 CUDA tensor")
     S, nty, ntx = cube.shape
+    _need(scores, 8 * nty * ntx, "scores")
     thr = C.c_double()
     nb = C.c_int32()
     boxes = (C.c_int32 * (4 * max(1, max_boxes)))()
@@ -439,6 +517,9 @@ class Stream:
         s.chan_scale = _ptr(snap.get("chan_scale"))
         s.n_bl = snap["uvw"].shape[0]
         s.n_ch = snap["freq"].shape[0]
+        if self.plan._in_limits(s.n_bl, s.n_ch):
+            self.plan._need_inputs(s.n_bl, s.n_ch, snap["uvw"], snap["freq"], snap["vis"],
+                                   snap.get("chan_scale"), snap.get("weight"), snap.get("flag"))
         idx = C.c_int64(0)
         _check(lib().toi_stream_push(self.handle, C.byref(s), C.byref(idx)), self.plan.handle)
         self.pushed = idx.value + 1
@@ -458,7 +539,10 @@ class Stream:
 
     def pop(self, wait: bool = True, out=None):
         t = self._torch
+        if out is not None and out.is_cuda:
+            raise ValueError("out must be a host tensor")
         row = t.empty(self.nt, self.nt, dtype=t.float32) if out is None else out
+        _need(row, 4 * self.nt * self.nt, "out")
         r = C.c_int64(0)
         got = C.c_int32(0)
         _check(lib().toi_stream_pop(self.handle, row.data_ptr(), C.byref(r), 1 if wait else 0,
