@@ -700,7 +700,8 @@ def run_localise(args):
     nsel = w.n_bl * w.n_chan * (1.0 - w.flag_frac ** 2)
     flops = nsel * NW * 64 * 8 * nloc
     sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
-    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / (loc_ms / 1e3) / 1e12
     print(json.dumps({
         "metric": "snapshots/s of imaging + windowed point-source localisation (loss, d/d(l,m,S), "
@@ -715,7 +716,7 @@ def run_localise(args):
         "windows_per_s": round(NW * nloc / (ms / 1e3), 1),
         "roofline": {"bound": "alu", "kernel": "localise (facet gridding + degridding)",
                      "achieved": round(achieved, 2), "peak": round(peak, 1),
-                     "peak_kind": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x median SM clock",
+                     "peak_kind": f"FP32 FMA: {nsm} SMs x 128 lanes x 2 flop x median SM clock",
                      "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None},
         "stages": {k: {"ms_per_snapshot": round(v[0] / n, 4)} for k, v in prof.items() if v[1]},
         "gpu_launches": int(launches), "clocks": ck}))
