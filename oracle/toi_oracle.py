@@ -53,6 +53,9 @@ Parity status per function (pins live in tests/):
     of the loss (l, m, S and weights), a zero loss and gradient at the true
     source, the coplanar peak S / omega at the pixel source_of_pixel names,
     the window transpose identity and the gridded full image on the window.
+  Pin strength: tests/test_oracle_mutations.py plants one plausible mistake
+    at a time in these routines (a dropped term, a sign, an index, a
+    transposed operand, a constant) and requires a named pin to fail on each.
 """
 from __future__ import annotations
 
