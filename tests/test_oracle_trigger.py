@@ -176,6 +176,7 @@ def test_nonperiodic_dip_found():
     r = O.candidates(cube, 32, O.MODE_NONPERIODIC)
     assert r["mask"].sum() == 1
     assert r["boxes"] == [[6 * 32, 1 * 32, 7 * 32, 2 * 32]]
+    assert r["threshold"] == r["mean"] + 4.0 * r["std"]      # Section 6.3: 4 sigma
 
 
 def test_connected_boxes_by_hand():
