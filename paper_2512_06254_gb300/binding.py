@@ -503,7 +503,6 @@ class Stream:
         return max(0, self.pushed - 2) - self.popped
 
     def push(self, snap) -> int:
-        t = self._torch
         s = toi_snapshot()
         for k in ("uvw", "freq", "vis", "flag", "weight", "chan_scale"):
             x = snap.get(k)
@@ -528,7 +527,6 @@ class Stream:
         for k in [k for k in self._inputs if k < idx.value]:
             if self.input_free(k):
                 del self._inputs[k]
-        del t
         return idx.value
 
     def input_free(self, index: int, wait: bool = False) -> bool:
