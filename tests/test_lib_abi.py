@@ -75,3 +75,30 @@ def test_host_validation_without_gpu(libtoi):
     assert L.toi_stream_close(None) == libtoi.TOI_ERR_ARG
     assert L.tlisi_candidates(None, 1, 1, 1, 1, 0, None, None, None, None, 0, None) == libtoi.TOI_ERR_ARG
     assert L.toi_status_string(libtoi.TOI_ERR_RANGE)
+
+
+def test_config_fields_validated_on_the_host(libtoi):
+    """Every toi_config field outside its documented range is refused by
+    toi_plan before any CUDA call (so this runs without a GPU)."""
+    from paper_2512_06254_gb300 import binding as b
+    L = libtoi.lib()
+    h = C.c_void_p()
+    ARG, UNS = libtoi.TOI_ERR_ARG, libtoi.TOI_ERR_UNSUPPORTED
+    cases = [("vis_dtype", 2, ARG), ("kernel_support", 6, UNS), ("oversample", 3, UNS),
+             ("grid_slots", 0, ARG), ("grid_slots", 17, ARG), ("grid_run", 7, ARG),
+             ("grid_run", 1025, ARG), ("batch_max", -1, ARG), ("batch_max", 65, ARG),
+             ("mode", 1, ARG), ("mode", 4, ARG), ("max_moments", -1, ARG),
+             ("max_moments", 1025, ARG), ("grid_rows", 5, ARG), ("max_windows", -1, ARG),
+             ("cell_arcsec", float("inf"), ARG), ("cell_arcsec", float("nan"), ARG),
+             ("max_channels", 0, ARG)]
+    for field, value, want in cases:
+        cfg = b.config_default(128, 2.0, 10, 10, 4)
+        setattr(cfg, field, value)
+        assert L.toi_plan(C.byref(cfg), None, C.byref(h)) == want, (field, value)
+        assert h.value is None
+    cfg = b.config_default(128, 2.0, 10, 10, 4)
+    cfg.mode, cfg.batch_max = 3, 4                       # the batch is 2-D only
+    assert L.toi_plan(C.byref(cfg), None, C.byref(h)) == UNS
+    cfg = b.config_default(128, 2.0, 1 << 20, 1 << 20, 4)   # 2^42 records
+    assert L.toi_plan(C.byref(cfg), None, C.byref(h)) == ARG
+    assert L.toi_plan(None, None, C.byref(h)) == ARG
