@@ -19,7 +19,8 @@
 // traffic is therefore about W cells per cell of track length instead of
 // W^2 per sample; the 67 MB
 // half-plane grid of a 2048^2 image stays resident in L2 for these
-// reductions, and the streamed visibilities are read with evict-first loads.
+// reductions, while each lane stages its stream of visibilities, weights and
+// flags through shared memory with cp.async, two chunks ahead.
 // The grid starts from zero (the FFT row pass clears what it reads).  Cell
 // sums are exact up to float32 rounding order (the reductions commute).
 #include <cuda_fp16.h>
@@ -70,17 +71,6 @@ __device__ __forceinline__ float es_kernel(float x, float bl2) {
 
 __device__ __forceinline__ void red_add(float2* p, float2 v) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y));
-}
-
-template <bool HALF>
-__device__ __forceinline__ float2 load_vis(const void* vis, size_t idx, float scale) {
-  if (HALF) {
-    const unsigned int raw = __ldcs(reinterpret_cast<const unsigned int*>(vis) + idx);
-    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&raw));
-    return make_float2(f.x * scale, f.y * scale);
-  } else {
-    return __ldcs(reinterpret_cast<const float2*>(vis) + idx);
-  }
 }
 
 // A lane's register window, kept circular: logical column i (in the
@@ -205,39 +195,6 @@ struct Sample {
   float2 k;      // k = nu / c of its channel (float pair)
   bool sel;      // w_q > 0
 };
-
-template <bool HALF>
-__device__ __forceinline__ Sample load_sample(const void* vis, const float* chan_scale,
-                                              const float* weight, const uint8_t* flag,
-                                              const float2* kf, size_t o, int ch, int npol,
-                                              int pa, int pb) {
-  Sample s;
-  s.k = kf[ch];
-  bool fa = false, fb = false;
-  if (flag) {
-    if (npol == 4) {   // the four flag bytes of a record as one aligned word
-      const unsigned int f4 = __ldcs(reinterpret_cast<const unsigned int*>(flag + o));
-      fa = (f4 & 0xffu) != 0;
-      fb = (f4 >> 24) != 0;
-    } else {
-      fa = __ldcs(flag + o + pa) != 0;
-      fb = __ldcs(flag + o + pb) != 0;
-    }
-  }
-  float wa = fa ? 0.f : (weight ? __ldcs(weight + o + pa) : 1.f);
-  float wb = fb ? 0.f : (weight ? __ldcs(weight + o + pb) : 1.f);
-  if (pa == pb) wb = 0.f;
-  s.sel = wa + wb > 0.f;
-  const float sc = HALF ? chan_scale[ch] : 1.f;
-  const float2 va = load_vis<HALF>(vis, o + pa, sc);
-  s.c = make_float2(wa * va.x, wa * va.y);
-  if (pa != pb) {
-    const float2 vb = load_vis<HALF>(vis, o + pb, sc);
-    s.c.x += wb * vb.x;
-    s.c.y += wb * vb.y;
-  }
-  return s;
-}
 
 // Tap origin of one axis.  The coordinate is g = c0 + 4 + s k with s (per
 // track) and k = nu / c (per channel) known in float64, each held here as an
