@@ -212,14 +212,16 @@ toi_status tlisi_candidates(const float* cube, int32_t S, int32_t nty,
  * loads the library holds it until the process exits).  A cube whose search
  * needs more than that (scratch grows as about 8 (S/2 + 1) nty ntx bytes,
  * e.g. 64 x 64 tiles up to about 960 slices) is rejected with TOI_ERR_ARG
- * and a message giving the size; use tlisi_candidates for those.  The
- * array's device address is looked up once per device, with that device
- * current, on the first call made there, so make that first call before any
- * stream capture.  All calls on a device share the one array: calls whose
- * GPU work overlaps (other streams, other host threads) race and must be
- * serialised by the caller.  The array keeps the last call's contents; the
- * search writes every scratch word before reading it, so nothing needs
- * clearing.  Synchronises `stream`. */
+ * and a message giving the size; use tlisi_candidates for those.  Every call
+ * looks up the array's address on the calling thread's current device
+ * (cudaGetSymbolAddress), so the address is never stale.  All calls on a
+ * device share the one array: calls whose GPU work overlaps (other streams,
+ * other host threads) race and must be serialised by the caller.  The array
+ * keeps the last call's contents; the search writes every scratch word
+ * before reading it, so nothing needs clearing.  With scores NULL the scores
+ * stay in the array.  The call synchronises `stream` to return the
+ * threshold and boxes, so it cannot be recorded into a CUDA graph by stream
+ * capture. */
 toi_status tlisi_candidates_noalloc(const float* cube, int32_t S, int32_t nty,
                                     int32_t ntx, int32_t tile, int32_t mode,
                                     void* stream, double* threshold, int32_t* boxes,
@@ -290,6 +292,17 @@ toi_status toi_batch(toi_plan_t plan, const toi_snapshot* snaps, int32_t n, floa
  * were.  Errors as toi_batch_prepare. */
 toi_status toi_autotune(toi_plan_t plan, const toi_snapshot* snaps, int32_t n, int32_t* runs_out,
                         double* us_out);
+
+/* Gridder work split the plan uses for a snapshot of n_ch channels (host
+ * int32 outputs): *run = channels walked by one lane (or lane pair), *rows =
+ * window rows held per lane (8: the whole W x W footprint, 4: half of it in
+ * each lane of a pair), for batched launches (batched != 0, toi_batch*) or
+ * single toi_grid launches.  It reflects config.grid_run / grid_rows, then
+ * what toi_autotune chose, then the built-in defaults (Section 4.1 stage 3
+ * is the gridding step; the split itself is this library's design).  Host
+ * only, no device work.  TOI_ERR_ARG for a NULL plan or output or n_ch < 1. */
+toi_status toi_grid_lane_run(toi_plan_t plan, int32_t n_ch, int32_t batched, int32_t* run,
+                             int32_t* rows);
 
 /* Near-coplanar plan of the snapshot gridded into `slot` (mode 3; host
  * double[8]): N_slab, K, Phi_max, alpha_slab, dr3 (wavelengths), r3min,

@@ -32,7 +32,8 @@ EXPORTS = ("toi_config_default", "toi_plan", "toi_plan_destroy", "toi_set_stream
            "toi_image", "tlisi_update", "tlisi_reset", "tlisi_candidates",
            "tlisi_candidates_noalloc",
            "toi_degrid_backward", "toi_batch_prepare", "toi_batch_run", "toi_batch",
-           "toi_autotune", "toi_mode3_info", "toi_localise_seed", "toi_localise",
+           "toi_autotune", "toi_grid_lane_run", "toi_mode3_info", "toi_localise_seed",
+           "toi_localise",
            "toi_stream_open", "toi_stream_push", "toi_stream_input_free", "toi_stream_pop",
            "toi_stream_close",
            "toi_plan_buffer", "toi_profile_enable", "toi_profile_read",
@@ -94,6 +95,7 @@ def lib():
         "toi_batch": [P, P, I, P, C.POINTER(I)],
         "toi_autotune": [P, P, I, P, P],
         "toi_mode3_info": [P, I, P],
+        "toi_grid_lane_run": [P, I, I, C.POINTER(I), C.POINTER(I)],
         "toi_localise_seed": [P, I, P, I, P, P],
         "toi_localise": [P, I, I, P, P, P, P, P, P],
         "toi_stream_open": [P, I, I, I, C.POINTER(C.c_void_p)],
@@ -383,6 +385,13 @@ class Plan:
         _check(lib().toi_autotune(self.handle, C.cast(arr, C.c_void_p), len(snaps),
                                   C.cast(runs, C.c_void_p), C.cast(us, C.c_void_p)), self.handle)
         return ({b: runs[b] for b in range(4) if runs[b]}, {b: us[b] for b in range(4) if runs[b]})
+
+    def lane_run(self, n_ch: int, batched: bool = True):
+        """toi_grid_lane_run: (channels per lane, window rows per lane)."""
+        run, rows = C.c_int32(0), C.c_int32(0)
+        _check(lib().toi_grid_lane_run(self.handle, n_ch, 1 if batched else 0, C.byref(run),
+                                       C.byref(rows)), self.handle)
+        return run.value, rows.value
 
     def mode3_info(self, slot: int = 0):
         """toi_mode3_info as a dict."""

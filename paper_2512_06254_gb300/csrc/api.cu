@@ -538,6 +538,20 @@ static int lane_run(toi_plan_t p, int nch) {
   return t > 0 ? t : toi::grid_default_run(nch, true);
 }
 
+toi_status toi_grid_lane_run(toi_plan_t p, int32_t n_ch, int32_t batched, int32_t* run,
+                             int32_t* rows) {
+  if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
+  if (!run || !rows || n_ch < 1) return fail(p, TOI_ERR_ARG, "need run, rows and n_ch >= 1");
+  if (batched) {
+    *run = lane_run(p, n_ch);
+    *rows = p->batch_rows;
+  } else {
+    *run = p->cfg.grid_run > 0 ? p->cfg.grid_run : toi::grid_default_run(n_ch, false);
+    *rows = p->cfg.grid_rows ? p->cfg.grid_rows : toi::grid_default_rows(false);
+  }
+  return TOI_OK;
+}
+
 static toi_status check_batch(toi_plan_t p, const toi_snapshot* snaps, int32_t n) {
   if (!p) return fail(nullptr, TOI_ERR_ARG, "plan is NULL");
   if (p->batch_max < 1) return fail(p, TOI_ERR_ARG, "the plan was made with batch_max = 0");

@@ -10,10 +10,11 @@
 // this library holds until the process exits.
 //
 // Host code cannot hand the array's name to a kernel (on the host it names a
-// stand-in object, not device memory), so the device address is looked up
-// with cudaGetSymbolAddress once per device, with that device current, the
-// first time the entry point runs there; later calls reuse it.
-#include <mutex>
+// stand-in object, not device memory), so every call looks the device address
+// up with cudaGetSymbolAddress for the calling thread's current device.  The
+// lookup is cheap, and it is never stale: a cached address would outlive a
+// cudaDeviceReset or a primary-context teardown, after which the module (and
+// the array) is loaded again at a new address.
 #include <string>
 
 #include "toi_internal.cuh"
@@ -29,12 +30,8 @@ void set_planless_error(const std::string& msg);
 namespace {
 
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;   // 16 MiB
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_cand_scratch[kStaticScratchBytes];
-
-std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
 
 toi_status nofail(toi_status s, const std::string& msg) {
   toi::set_planless_error(msg);
@@ -65,22 +62,11 @@ extern "C" toi_status tlisi_candidates_noalloc(const float* cube, int32_t S, int
                                    " bytes of scratch, more than its fixed " +
                                    std::to_string(kStaticScratchBytes) +
                                    " bytes; use tlisi_candidates for larger cubes");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return nofail(TOI_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return nofail(TOI_ERR_ARG, "device index out of range");
+  // the array's address on the current device (see the file comment)
   void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-      void* addr = nullptr;
-      e = cudaGetSymbolAddress(&addr, g_cand_scratch);
-      if (e != cudaSuccess || !addr)
-        return nofail(TOI_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_scratch_addr[dev] = addr;
-    }
-    base = g_scratch_addr[dev];
-  }
+  cudaError_t e = cudaGetSymbolAddress(&base, g_cand_scratch);
+  if (e != cudaSuccess || !base)
+    return nofail(TOI_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   // Every kernel of the search writes each scratch word before reading it,
   // so the array's previous contents (it keeps those of the last call) need
   // no clearing.

@@ -23,7 +23,8 @@ def _abi_call(fn, cube, T, mode, max_boxes, scores):
     nb = C.c_int32()
     boxes = (C.c_int32 * (4 * max_boxes))()
     st = fn(cube.data_ptr(), S, nty, ntx, T, mode, torch.cuda.current_stream().cuda_stream,
-            C.byref(thr), C.cast(boxes, C.c_void_p), C.byref(nb), max_boxes, scores.data_ptr())
+            C.byref(thr), C.cast(boxes, C.c_void_p), C.byref(nb), max_boxes,
+            None if scores is None else scores.data_ptr())
     return st, thr.value, nb.value, [list(boxes[4 * i:4 * i + 4]) for i in range(min(nb.value, max_boxes))]
 
 
@@ -50,6 +51,22 @@ def test_noalloc_matches_allocating_search_twice(mode):
         assert thr_new == thr_ref
         assert nb_new == nb_ref and boxes_new == boxes_ref
         assert torch.equal(s_new, s_ref)
+
+
+def test_noalloc_without_scores_buffer():
+    """scores NULL: the scores stay in the fixed array; threshold and boxes
+    still equal the allocating search's, on two calls in a row."""
+    L = B.lib()
+    for seed in (303, 404):
+        cube = _cube(seed, 118, 64)
+        s_ref = torch.empty(64, 64, dtype=torch.float64, device="cuda")
+        st_ref, thr_ref, nb_ref, boxes_ref = _abi_call(L.tlisi_candidates, cube, 32,
+                                                       toi.TOI_CAND_PERIODIC, 64, s_ref)
+        st_new, thr_new, nb_new, boxes_new = _abi_call(L.tlisi_candidates_noalloc, cube, 32,
+                                                       toi.TOI_CAND_PERIODIC, 64, None)
+        assert st_ref == toi.TOI_OK and st_new == toi.TOI_OK
+        assert thr_new == thr_ref and nb_new == nb_ref and boxes_new == boxes_ref
+        assert nb_ref >= 1
 
 
 def test_noalloc_refuses_cube_beyond_its_scratch():
