@@ -510,21 +510,446 @@ __device__ __forceinline__ void grid_track(const BaselineCoef* __restrict__ coef
   flush_all(w, snk, G, ox, oy, sx, sy, rx, ry, rbase);
 }
 
+// ---------------------------------------------------------------------------
+// Two-dimensional gridding with packed single-precision pairs.
+//
+// Blackwell executes fma / mul / add on two float32 values held in one
+// 64-bit register pair as a single instruction (f32x2).  The gridder is
+// bound by instruction issue, and nearly every one of its float operations
+// comes in pairs: a window cell is a complex (re, im) that receives
+// px * (re, im) of the sample, and the kernel values are evaluated for
+// neighbouring taps.  This path therefore keeps the register window as packed
+// (re, im) cells and evaluates the kernel two taps at a time; only the
+// square root and exp2 (one MUFU operation each per value) stay scalar.
+//
+// Coordinates.  On a channel grid that is linear in k = nu / c (every
+// Measurement-Set spectral window this library has seen; checked per
+// snapshot by the plane fit, which records the largest deviation of any
+// channel from the chord k0 + ch dk), a track's first-tap coordinate
+// h(ch) = c0 + s k(ch) is an arithmetic progression.  Each lane starts from
+// h(c_begin) rounded to 32.32 fixed point (from float64) and adds the
+// rounded step once per channel: one 64-bit integer add per axis, exact
+// apart from the step's rounding, under 2^-33 cell per channel (6e-8 cell
+// over a 512-channel run).  The tap index is the ceiling of h and the
+// offset f = q - h in [0, 1) comes from the fraction bits (truncated to
+// float32's 23).  A snapshot whose channels deviate from the chord by more
+// than 1e-7 cell on a track takes the error-free float32 route of
+// tap_origin instead.
+
+typedef unsigned long long f2x;   // two float32 in one 64-bit register pair
+
+__device__ __forceinline__ f2x pk(float a, float b) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk(f2x v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// psi at two packed arguments x in [-4, 4] (W = 8).  1 - (2x/W)^2 is formed
+// as (1 - x/4)(1 + x/4): each factor is >= 0 for such x after rounding, so
+// no clamp is needed, and it keeps its relative accuracy near the support
+// edge where 1 - x^2/16 cancels.
+__device__ __forceinline__ void es_kernel2(f2x x, f2x bl2x2, f2x nbl2x2, float& p0, float& p1) {
+  const f2x u = fma2(x, pk(-0.25f, -0.25f), pk(1.f, 1.f));
+  const f2x v = fma2(x, pk(0.25f, 0.25f), pk(1.f, 1.f));
+  float t0, t1;
+  upk(mul2(u, v), t0, t1);
+  float e0, e1;
+  upk(fma2(pk(sqrt_approx(t0), sqrt_approx(t1)), bl2x2, nbl2x2), e0, e1);
+  p0 = ex2_approx(e0);
+  p1 = ex2_approx(e1);
+}
+
+// first tap q = ceil(h) and offset f = q - h of a 32.32 fixed-point h
+__device__ __forceinline__ void fixed_tap(long long h, int& q, float& f) {
+  const unsigned int lo = (unsigned int)h;
+  q = (int)(h >> 32) + (lo != 0u ? 1 : 0);
+  const unsigned int fb = 0u - lo;   // (q - h) 2^32 in [0, 2^32)
+  f = __uint_as_float(0x3f800000u | (fb >> 9)) - 1.0f;
+}
+
+__device__ __forceinline__ void flush_cell2(float2* H, int G, int x, int y, f2x v) {
+  float re, im;
+  upk(v, re, im);
+  if ((re != 0.f || im != 0.f) && (unsigned)x < (unsigned)G && (unsigned)y < (unsigned)(G >> 1))
+    red_add(H + (size_t)y * G + x, make_float2(re, im));
+}
+
+template <int RH>
+struct Win2 {
+  f2x a[RH][kWin];   // a[owned physical row - row base][physical column], (re, im)
+};
+
+template <int RH>
+__device__ __forceinline__ void flush_all2(Win2<RH>& w, float2* H, int G, int ox, int oy, int sx,
+                                           int sy, int rx, int ry, int rbase) {
+#pragma unroll
+  for (int j = 0; j < RH; ++j) {
+    const int y = phys_to_abs(rbase + j, ry, oy, sy);
+#pragma unroll
+    for (int i = 0; i < kWin; ++i) {
+      flush_cell2(H, G, phys_to_abs(i, rx, ox, sx), y, w.a[j][i]);
+      w.a[j][i] = 0ull;
+    }
+  }
+}
+
+// Column slide: physical column P (logical column 0) is final.  Every other
+// column moves one step closer to the sample's first tap and column P
+// becomes the last (offset 7 steps): the packed offsets ofx2 follow.
+template <int P, int RH>
+__device__ __forceinline__ void slide_col2(Win2<RH>& w, f2x (&ofx2)[kWin / 2], f2x nsx2,
+                                           float fsx7, float2* H, int G, int x, int oy, int sy,
+                                           int ry, int rbase) {
+#pragma unroll
+  for (int j = 0; j < RH; ++j) {
+    flush_cell2(H, G, x, phys_to_abs(rbase + j, ry, oy, sy), w.a[j][P]);
+    w.a[j][P] = 0ull;
+  }
+#pragma unroll
+  for (int i = 0; i < kWin / 2; ++i) ofx2[i] = add2(ofx2[i], nsx2);
+  float a, b;
+  upk(ofx2[P / 2], a, b);
+  ofx2[P / 2] = (P & 1) ? pk(a, fsx7) : pk(fsx7, b);
+}
+
+template <int RH>
+__device__ __forceinline__ void slide_x2(Win2<RH>& w, f2x (&ofx2)[kWin / 2], f2x nsx2, float fsx7,
+                                         float2* H, int G, int ox, int oy, int sy, int rx, int ry,
+                                         int rbase) {
+  switch (rx) {
+    case 0: slide_col2<0>(w, ofx2, nsx2, fsx7, H, G, ox, oy, sy, ry, rbase); break;
+    case 1: slide_col2<1>(w, ofx2, nsx2, fsx7, H, G, ox, oy, sy, ry, rbase); break;
+    case 2: slide_col2<2>(w, ofx2, nsx2, fsx7, H, G, ox, oy, sy, ry, rbase); break;
+    case 3: slide_col2<3>(w, ofx2, nsx2, fsx7, H, G, ox, oy, sy, ry, rbase); break;
+    case 4: slide_col2<4>(w, ofx2, nsx2, fsx7, H, G, ox, oy, sy, ry, rbase); break;
+    case 5: slide_col2<5>(w, ofx2, nsx2, fsx7, H, G, ox, oy, sy, ry, rbase); break;
+    case 6: slide_col2<6>(w, ofx2, nsx2, fsx7, H, G, ox, oy, sy, ry, rbase); break;
+    default: slide_col2<7>(w, ofx2, nsx2, fsx7, H, G, ox, oy, sy, ry, rbase); break;
+  }
+}
+
+// Row slide: physical row R (logical row 0) is final; its owner flushes it.
+// Every owned row's offset moves one step closer and row R becomes the last.
+template <int R, int RH>
+__device__ __forceinline__ void slide_row2(Win2<RH>& w, f2x (&ofy2)[RH / 2], f2x nsy2, float fsy7,
+                                           float2* H, int G, int y, int ox, int sx, int rx) {
+#pragma unroll
+  for (int i = 0; i < kWin; ++i) {
+    flush_cell2(H, G, phys_to_abs(i, rx, ox, sx), y, w.a[R][i]);
+    w.a[R][i] = 0ull;
+  }
+  float a, b;
+  upk(ofy2[R / 2], a, b);
+  ofy2[R / 2] = (R & 1) ? pk(a, fsy7) : pk(fsy7, b);
+}
+
+template <int RH>
+__device__ __forceinline__ void slide_y2(Win2<RH>& w, f2x (&ofy2)[RH / 2], f2x nsy2, float fsy7,
+                                         float2* H, int G, int ox, int oy, int sx, int rx, int ry,
+                                         int rbase) {
+#pragma unroll
+  for (int i = 0; i < RH / 2; ++i) ofy2[i] = add2(ofy2[i], nsy2);
+  const int r = ry - rbase;   // owned row index, or outside [0, RH)
+  switch (r) {
+    case 0: slide_row2<0>(w, ofy2, nsy2, fsy7, H, G, oy, ox, sx, rx); break;
+    case 1: slide_row2<1 % RH>(w, ofy2, nsy2, fsy7, H, G, oy, ox, sx, rx); break;
+    case 2: slide_row2<2 % RH>(w, ofy2, nsy2, fsy7, H, G, oy, ox, sx, rx); break;
+    case 3: slide_row2<3 % RH>(w, ofy2, nsy2, fsy7, H, G, oy, ox, sx, rx); break;
+    case 4: if (RH == kWin) slide_row2<4 % RH>(w, ofy2, nsy2, fsy7, H, G, oy, ox, sx, rx); break;
+    case 5: if (RH == kWin) slide_row2<5 % RH>(w, ofy2, nsy2, fsy7, H, G, oy, ox, sx, rx); break;
+    case 6: if (RH == kWin) slide_row2<6 % RH>(w, ofy2, nsy2, fsy7, H, G, oy, ox, sx, rx); break;
+    case 7: if (RH == kWin) slide_row2<7 % RH>(w, ofy2, nsy2, fsy7, H, G, oy, ox, sx, rx); break;
+    default: break;   // the other lane of the pair owns this row
+  }
+}
+
+// One sample ready for the window: packed weighted visibility, offsets of
+// its first taps (in the direction of travel) and the first taps.
+struct Prep2 {
+  f2x c;
+  float fxs, fys;
+  int kx0, ky0;
+};
+
+// The weighted visibility of a staged sample (flags, weights, parallel-hand
+// average; Section 3.5), packed, or 0 when it is not selected.
+template <bool HALF>
+__device__ __forceinline__ f2x staged_vis(const StageBuf& sb, int sidx, int u, int lane,
+                                          const float* chan_scale, const float* weight,
+                                          const uint8_t* flag, size_t o, int ch, int npol,
+                                          int pa, int pb) {
+  bool fa = false, fb = false;
+  if (flag) {
+    if (npol == 4) {
+      const unsigned int f = sb.f[sidx][u][lane];
+      fa = (f & 0xffu) != 0;
+      fb = (f >> 24) != 0;
+    } else {
+      fa = flag[o + pa] != 0;
+      fb = flag[o + pb] != 0;
+    }
+  }
+  const float wa = fa ? 0.f : (weight ? sb.wa[sidx][u][lane] : 1.f);
+  float wb = fb ? 0.f : (weight ? sb.wb[sidx][u][lane] : 1.f);
+  if (pa == pb) wb = 0.f;
+  float2 va = sb.va[sidx][u][lane], vbv = (pa != pb) ? sb.vb[sidx][u][lane] : make_float2(0.f, 0.f);
+  if (HALF) {
+    const float sc = chan_scale[ch];
+    const unsigned int ra = __float_as_uint(va.x), rb = __float_as_uint(vbv.x);
+    const float2 fa2 = __half22float2(*reinterpret_cast<const __half2*>(&ra));
+    const float2 fb2 = __half22float2(*reinterpret_cast<const __half2*>(&rb));
+    va = make_float2(fa2.x * sc, fa2.y * sc);
+    vbv = make_float2(fb2.x * sc, fb2.y * sc);
+  }
+  const f2x c = fma2(pk(wb, wb), pk(vbv.x, vbv.y), mul2(pk(wa, wa), pk(va.x, va.y)));
+  return (wa + wb > 0.f) ? c : 0ull;
+}
+
+template <bool HALF, int RH>
+__device__ __forceinline__ void grid_track2(const BaselineCoef* __restrict__ coef,
+                                            const float2* __restrict__ kf,
+                                            const double* __restrict__ snap,
+                                            const void* __restrict__ vis,
+                                            const float* __restrict__ chan_scale,
+                                            const float* __restrict__ weight,
+                                            const uint8_t* __restrict__ flag, int nbl, int nch,
+                                            int npol, int G, float bl2, int run, int track,
+                                            int seg, StageBuf& sb, float2* __restrict__ H) {
+  const int lane = threadIdx.x & 31;
+  constexpr int RPW = 32 * RH / kWin;                   // channel runs per warp
+  const int run_idx = (RH == kWin) ? lane : (lane >> 1);
+  const int rbase = (RH == kWin) ? 0 : RH * (lane & 1); // first owned physical row
+  const int mirror = track >= nbl ? 1 : 0;
+  const int bl = track - mirror * nbl;
+  const TrackGeom t = track_geom(coef[bl], mirror);
+  const float2 kfirst = kf[0], klast = kf[nch - 1];
+  const double kf0 = (double)kfirst.x + (double)kfirst.y;
+  const double kf1 = (double)klast.x + (double)klast.y;
+  // the mirror track only reaches the stored rows when it passes within
+  // W/2 + 1 cells of k2' = 0
+  if (mirror && fabs(t.s2) * fmin(kf0, kf1) > 0.5 * kW + 1.0) return;
+  // a track far outside the grid (an oversized cell, reported by the plane
+  // fit) stores nothing
+  const double reach = fmax(fabs(t.s1), fabs(t.s2)) * fmax(kf0, kf1);
+  if (!(reach < 2.0 * G)) return;
+  const int c_begin = (seg * RPW + run_idx) * run;
+  const int c_end = min(nch, c_begin + run);
+  if (c_begin >= nch) return;
+  int pa, pb;
+  parallel_hands(npol, pa, pb);
+  // coordinates: fixed-point steps on a linear channel grid, else tap_origin
+  const double cxd = (double)(G / 2 - kW / 2), cyd = (double)(-kW / 2);
+  const double k0 = snap[SNAP_K0], dkl = snap[SNAP_DK];
+  const bool lin = snap[SNAP_KDEV] * fmax(fabs(t.s1), fabs(t.s2)) <= 1e-7;   // warp-uniform
+  long long hx = 0, hy = 0, vx = 0, vy = 0;
+  if (lin) {
+    const double kb = k0 + (double)c_begin * dkl;
+    hx = __double2ll_rn((cxd + t.s1 * kb) * 4294967296.0);
+    hy = __double2ll_rn((cyd + t.s2 * kb) * 4294967296.0);
+    vx = __double2ll_rn(t.s1 * dkl * 4294967296.0);
+    vy = __double2ll_rn(t.s2 * dkl * 4294967296.0);
+  }
+  const float s1hi = (float)t.s1, s1lo = (float)(t.s1 - (double)s1hi);
+  const float s2hi = (float)t.s2, s2lo = (float)(t.s2 - (double)s2hi);
+  const float cx = (float)cxd, cy = (float)cyd;
+  const double dk = kf1 - kf0;
+  const int sx = (t.s1 * dk >= 0.0) ? 1 : -1;
+  const int sy = (t.s2 * dk >= 0.0) ? 1 : -1;
+  const float fsx = (float)sx, fsy = (float)sy;
+  const float xoff = sx > 0 ? -0.5f * kW : 0.5f * kW - 1.0f;   // first tap in the direction of travel
+  const float yoff = sy > 0 ? -0.5f * kW : 0.5f * kW - 1.0f;
+  const f2x cflip = t.conj ? 0x8000000000000000ull : 0ull;     // conjugate: flip the sign of im
+  const size_t obase = (size_t)bl * nch * npol;
+  const f2x bl2x2 = pk(bl2, bl2), nbl2x2 = pk(-bl2, -bl2);
+
+  // the coordinates of channel ch (called once per channel, in order)
+  auto coords = [&](int ch, int& kx0, int& ky0, float& fx, float& fy) {
+    if (lin) {
+      fixed_tap(hx, kx0, fx);
+      fixed_tap(hy, ky0, fy);
+      hx += vx;
+      hy += vy;
+    } else {
+      const float2 k = kf[ch];
+      tap_origin(s1hi, s1lo, k.x, k.y, cx, kx0, fx);
+      tap_origin(s2hi, s2lo, k.x, k.y, cy, ky0, fy);
+    }
+  };
+
+  Win2<RH> w;
+#pragma unroll
+  for (int j = 0; j < RH; ++j)
+#pragma unroll
+    for (int i = 0; i < kWin; ++i) w.a[j][i] = 0ull;
+
+  const int nchunk = (c_end - c_begin + kStage - 1) / kStage;
+  // staging helper: chunk q lands in stage q & 1
+  auto issue = [&](int q) {
+    if (q < nchunk) {
+      const int c0 = c_begin + q * kStage;
+      const int sidx = q & 1;
+#pragma unroll
+      for (int u = 0; u < kStage; ++u) {
+        const int ch = c0 + u;
+        if (ch < c_end) {
+          const size_t o = obase + (size_t)ch * npol;
+          const char* vb = reinterpret_cast<const char*>(vis);
+          const int vbytes = HALF ? 4 : 8;
+          cp_async(&sb.va[sidx][u][lane], vb + (o + pa) * vbytes, vbytes);
+          if (pa != pb) cp_async(&sb.vb[sidx][u][lane], vb + (o + pb) * vbytes, vbytes);
+          if (flag && npol == 4) cp_async(&sb.f[sidx][u][lane], flag + o, 4);
+          if (weight) {
+            cp_async(&sb.wa[sidx][u][lane], weight + o + pa, 4);
+            if (pa != pb) cp_async(&sb.wb[sidx][u][lane], weight + o + pb, 4);
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  issue(0);
+  issue(1);
+  cp_async_wait1();   // chunk 0 landed
+
+  Prep2 cur;
+  {
+    float fx, fy;
+    coords(c_begin, cur.kx0, cur.ky0, fx, fy);
+    cur.fxs = fx + xoff;
+    cur.fys = fy + yoff;
+    cur.c = staged_vis<HALF>(sb, 0, 0, lane, chan_scale, weight, flag,
+                             obase + (size_t)c_begin * npol, c_begin, npol, pa, pb) ^ cflip;
+  }
+  int ox = sx > 0 ? cur.kx0 : cur.kx0 + kW - 1;
+  int oy = sy > 0 ? cur.ky0 : cur.ky0 + kW - 1;
+  int rx = 0, ry = 0;
+  const f2x nsx2 = pk(-fsx, -fsx), nsy2 = pk(-fsy, -fsy);
+  const float fsx7 = 7.f * fsx, fsy7 = 7.f * fsy;
+  // offset of physical column p from the first tap, in the direction of
+  // travel: sx ((p - rx) mod W), packed in pairs; rows likewise (owned rows)
+  f2x ofx2[kWin / 2], ofy2[RH / 2];
+#pragma unroll
+  for (int p = 0; p < kWin / 2; ++p) ofx2[p] = pk(fsx * (float)(2 * p), fsx * (float)(2 * p + 1));
+#pragma unroll
+  for (int r = 0; r < RH / 2; ++r)
+    ofy2[r] = pk(fsy * (float)(rbase + 2 * r), fsy * (float)(rbase + 2 * r + 1));
+#pragma unroll 1
+  for (int ch = c_begin; ch < c_end; ++ch) {
+    const int rel = ch - c_begin;
+    const int q = rel / kStage, u = rel - q * kStage;
+    // the next sample (ch + 1) may start a new chunk: wait for it, and refill
+    // the stage that chunk q has just vacated
+    const int chn = ch + 1;
+    Prep2 nxt;
+    nxt.c = 0ull;
+    if (chn < c_end) {
+      const int qn = q + (u + 1 == kStage ? 1 : 0);
+      const int un = (u + 1 == kStage) ? 0 : u + 1;
+      if (un == 0) {
+        issue(qn + 1);
+        cp_async_wait1();
+      }
+      nxt.c = staged_vis<HALF>(sb, qn & 1, un, lane, chan_scale, weight, flag,
+                               obase + (size_t)chn * npol, chn, npol, pa, pb) ^ cflip;
+    }
+    // footprint start of the current sample in window coordinates
+    int dx = sx > 0 ? cur.kx0 - ox : ox - (cur.kx0 + kW - 1);
+    int dy = sy > 0 ? cur.ky0 - oy : oy - (cur.ky0 + kW - 1);
+    if (dx < 0 || dy < 0 || dx >= kWin || dy >= kWin) {
+      flush_all2(w, H, G, ox, oy, sx, sy, rx, ry, rbase);
+      ox = sx > 0 ? cur.kx0 : cur.kx0 + kW - 1;
+      oy = sy > 0 ? cur.ky0 : cur.ky0 + kW - 1;
+      rx = 0;
+      ry = 0;
+      dx = 0;
+      dy = 0;
+#pragma unroll
+      for (int p = 0; p < kWin / 2; ++p) ofx2[p] = pk(fsx * (float)(2 * p), fsx * (float)(2 * p + 1));
+#pragma unroll
+      for (int r = 0; r < RH / 2; ++r)
+        ofy2[r] = pk(fsy * (float)(rbase + 2 * r), fsy * (float)(rbase + 2 * r + 1));
+    }
+    while (dx > 0) {
+      slide_x2(w, ofx2, nsx2, fsx7, H, G, ox, oy, sy, rx, ry, rbase);
+      ox += sx;
+      rx = (rx + 1) & (kWin - 1);
+      --dx;
+    }
+    while (dy > 0) {
+      slide_y2(w, ofy2, nsy2, fsy7, H, G, ox, oy, sx, rx, ry, rbase);
+      oy += sy;
+      ry = (ry + 1) & (kWin - 1);
+      --dy;
+    }
+    if (chn < c_end) {
+      float fx, fy;
+      coords(chn, nxt.kx0, nxt.ky0, fx, fy);
+      nxt.fxs = fx + xoff;
+      nxt.fys = fy + yoff;
+    } else {
+      nxt.kx0 = cur.kx0;
+      nxt.ky0 = cur.ky0;
+      nxt.fxs = cur.fxs;
+      nxt.fys = cur.fys;
+    }
+    // kernel values in physical order: physical index p holds tap (p - r) mod W
+    const f2x fxs2 = pk(cur.fxs, cur.fxs), fys2 = pk(cur.fys, cur.fys);
+    float px[kWin], py[RH];
+#pragma unroll
+    for (int p = 0; p < kWin / 2; ++p)
+      es_kernel2(add2(fxs2, ofx2[p]), bl2x2, nbl2x2, px[2 * p], px[2 * p + 1]);
+#pragma unroll
+    for (int r = 0; r < RH / 2; ++r)
+      es_kernel2(add2(fys2, ofy2[r]), bl2x2, nbl2x2, py[2 * r], py[2 * r + 1]);
+#pragma unroll
+    for (int j = 0; j < RH; ++j) {
+      const f2x b = mul2(cur.c, pk(py[j], py[j]));
+#pragma unroll
+      for (int i = 0; i < kWin; ++i) w.a[j][i] = fma2(pk(px[i], px[i]), b, w.a[j][i]);
+    }
+    cur = nxt;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  flush_all2(w, H, G, ox, oy, sx, sy, rx, ry, rbase);
+}
+
 template <bool HALF, bool MOM, int RH>
 __global__ void __launch_bounds__(kWarps * 32)
 grid_tracks_kernel(const BaselineCoef* __restrict__ coef, const float2* __restrict__ kf,
-                   const void* __restrict__ vis, const float* __restrict__ chan_scale,
-                   const float* __restrict__ weight, const uint8_t* __restrict__ flag, int nbl,
-                   int nch, int npol, int G, float bl2, int run, int nseg,
-                   float2* __restrict__ H, MomentPass mp) {
+                   const double* __restrict__ snap, const void* __restrict__ vis,
+                   const float* __restrict__ chan_scale, const float* __restrict__ weight,
+                   const uint8_t* __restrict__ flag, int nbl, int nch, int npol, int G, float bl2,
+                   int run, int nseg, float2* __restrict__ H, MomentPass mp) {
   __shared__ StageBuf stage_all[kWarps];
   const int wib = threadIdx.x >> 5;
   const int warp = blockIdx.x * kWarps + wib;
   if (warp >= 2 * nbl * nseg) return;
   // warps [0, nbl * nseg) walk the upper-half tracks, the rest their mirrors
   // (most mirror warps exit at once, so they are kept out of the busy blocks)
-  grid_track<HALF, MOM, RH>(coef, kf, vis, chan_scale, weight, flag, nbl, nch, npol, G, bl2, run,
-                            warp / nseg, warp % nseg, stage_all[wib], H, mp);
+  if (MOM)
+    grid_track<HALF, MOM, RH>(coef, kf, vis, chan_scale, weight, flag, nbl, nch, npol, G, bl2, run,
+                              warp / nseg, warp % nseg, stage_all[wib], H, mp);
+  else
+    grid_track2<HALF, RH>(coef, kf, snap, vis, chan_scale, weight, flag, nbl, nch, npol, G, bl2,
+                          run, warp / nseg, warp % nseg, stage_all[wib], H);
 }
 
 // Persistent gridder over a batch: each warp takes work items from a
@@ -561,10 +986,8 @@ grid_batch_kernel(const BatchEntry* __restrict__ E, const BatchHeader* __restric
     const BatchEntry& e = E[ent];
     const int seg = (int)(local % e.nseg);
     const int track = (int)(local / e.nseg) + (mir ? e.nbl : 0);
-    const MomentPass none{};
-    grid_track<HALF, false, RH>(e.coef, e.kf, e.vis, e.chan_scale, e.weight, e.flag, e.nbl,
-                                e.nch, npol, G, bl2, e.run, track, seg, stage_all[wib], e.grid,
-                                none);
+    grid_track2<HALF, RH>(e.coef, e.kf, e.snap, e.vis, e.chan_scale, e.weight, e.flag, e.nbl,
+                          e.nch, npol, G, bl2, e.run, track, seg, stage_all[wib], e.grid);
   }
 }
 
@@ -643,12 +1066,12 @@ static void launch_tracks(toi_plan_s* p, Slot& s, int rows, int blocks, const vo
                           int nbl, int nch, float bl2, int run, int nseg, const MomentPass& m) {
   if (rows == 4)
     grid_tracks_kernel<HALF, MOM, 4><<<blocks, kWarps * 32, 0, p->stream>>>(
-        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, p->G, bl2, run,
-        nseg, s.grid, m);
+        s.coef, p->kf, s.snap, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, p->G, bl2,
+        run, nseg, s.grid, m);
   else
     grid_tracks_kernel<HALF, MOM, 8><<<blocks, kWarps * 32, 0, p->stream>>>(
-        s.coef, p->kf, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, p->G, bl2, run,
-        nseg, s.grid, m);
+        s.coef, p->kf, s.snap, vis, chan_scale, weight, flag, nbl, nch, p->cfg.n_pol, p->G, bl2,
+        run, nseg, s.grid, m);
 }
 
 static cudaError_t launch_grid_impl(toi_plan_s* p, Slot& s, const void* vis,

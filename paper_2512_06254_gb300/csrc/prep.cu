@@ -367,11 +367,28 @@ __device__ bool smallest_eigvec(const double Cd[3][3], double v3[3]) {
 }
 
 __device__ __forceinline__ void prep_finalize_body(const double* __restrict__ bpart, int nbpart,
+                                                   const double* __restrict__ kch, int nch,
                                                    double* __restrict__ snap, int* status,
                                                    double beta_rad) {
   // one warp per sum: lanes take partials in a fixed stride, then a fixed tree
   __shared__ double v[11];
+  __shared__ unsigned long long kdev_bits;
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the channel grid against its chord k0 + c dk: the largest |deviation|
+  // (non-negative doubles order like their bit patterns)
+  if (threadIdx.x == 0) kdev_bits = 0ull;
+  __syncthreads();
+  {
+    const double k0 = kch[0];
+    const double dk = nch > 1 ? (kch[nch - 1] - k0) / (double)(nch - 1) : 0.0;
+    double dev = 0.0;
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) dev = fmax(dev, fabs(kch[c] - (k0 + c * dk)));
+    atomicMax(&kdev_bits, (unsigned long long)__double_as_longlong(dev));
+    if (threadIdx.x == 0) {
+      snap[SNAP_K0] = k0;
+      snap[SNAP_DK] = dk;
+    }
+  }
   for (int i = wib; i < 11; i += blockDim.x >> 5) {
     double a = 0.0;
     for (int b = lane; b < nbpart; b += 32) a += bpart[(size_t)b * 11 + i];
@@ -424,11 +441,13 @@ __device__ __forceinline__ void prep_finalize_body(const double* __restrict__ bp
   snap[SNAP_REPRO + 1] = (double)(float)(snap[SNAP_ETA] / beta_rad);
   snap[SNAP_REPRO + 2] = (double)(float)(beta_rad * beta_rad);
   snap[15] = 0.0;
+  snap[SNAP_KDEV] = __longlong_as_double((long long)kdev_bits);
 }
 
 __global__ void prep_finalize_kernel(const double* __restrict__ bpart, int nbpart,
+                                     const double* __restrict__ kch, int nch,
                                      double* __restrict__ snap, int* status, double beta_rad) {
-  prep_finalize_body(bpart, nbpart, snap, status, beta_rad);
+  prep_finalize_body(bpart, nbpart, kch, nch, snap, status, beta_rad);
 }
 
 // Per baseline: R = V uvw (float64), grid coefficients a1 = -r1 beta G,
@@ -496,7 +515,8 @@ __global__ void prep_finalize_batch(const BatchEntry* __restrict__ E,
                                     double beta_rad) {
   if ((int)blockIdx.y >= hdr->n) return;
   const BatchEntry& e = E[blockIdx.y];
-  prep_finalize_body(e.bpart, (e.nbl + kMomWarps - 1) / kMomWarps, e.snap, status, beta_rad);
+  prep_finalize_body(e.bpart, (e.nbl + kMomWarps - 1) / kMomWarps, e.kch, e.nch, e.snap, status,
+                     beta_rad);
 }
 
 __global__ void prep_coef_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr,
@@ -518,8 +538,8 @@ cudaError_t launch_prep(toi_plan_s* p, Slot& s, const double* uvw, const double*
                                                      p->d_status);
   prep_baselines_kernel<<<nbblk, kMomWarps * 32, 0, p->stream>>>(
       flag, weight, p->kch, p->kch_sum, nkblk, uvw, nbl, nch, p->cfg.n_pol, p->bpart);
-  prep_finalize_kernel<<<1, 352, 0, p->stream>>>(p->bpart, nbblk, s.snap, p->d_status,
-                                                 p->beta_rad);
+  prep_finalize_kernel<<<1, 352, 0, p->stream>>>(p->bpart, nbblk, p->kch, nch, s.snap,
+                                                 p->d_status, p->beta_rad);
   prep_coef_kernel<<<(nbl + 127) / 128, 128, 0, p->stream>>>(uvw, nbl, nch, p->kch, s.snap,
                                                              p->beta_rad, p->G, p->W, s.coef,
                                                              p->d_status);

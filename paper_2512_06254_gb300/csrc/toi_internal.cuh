@@ -26,7 +26,13 @@ enum SnapField {
   SNAP_ROWMAX = 14,  // largest stored grid row reached by a footprint (+1 margin)
   SNAP_LEN = 16,     // the part copied to snap_info
   SNAP_REPRO = 16,   // float32 re-projection constants -xi/beta, eta/beta, beta^2 (as doubles)
-  SNAP_ALLOC = 20
+  // linear model of the channel grid, k(ch) ~ k0 + ch dk (k = nu / c), and the
+  // largest deviation of any channel from it (the gridder steps coordinates
+  // in fixed point along a track when that deviation is negligible)
+  SNAP_K0 = 20,
+  SNAP_DK = 21,
+  SNAP_KDEV = 22,
+  SNAP_ALLOC = 24
 };
 
 // Per-baseline record written by the plane fit: coefficients of the grid
