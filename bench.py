@@ -197,6 +197,52 @@ def bind_host_to_gpu(index):
     return None
 
 
+def fft_comparison(prof, per_launch, G, dev):
+    """cuFFT (through torch.fft), timed with CUDA events on the same device, as
+    the comparison baseline of the hand-written inverse transform (stage 4 of
+    Section 4.1): a batch of G x G single-precision C2C inverse transforms,
+    and the C2R form that, like the library, uses the Hermitian half plane.
+    The library's figure is its row pass plus column pass (correction and
+    normalisation fused), per snapshot, from the timed step."""
+    import torch
+    n = max(1, min(per_launch, 8))
+    ours = (prof["fft_rows"][0] / max(prof["fft_rows"][1], 1) +
+            prof["fft_cols"][0] / max(prof["fft_cols"][1], 1)) / per_launch * 1e3
+    out = {"ours_us_per_snapshot": round(ours, 2), "grid": G, "batch": n}
+    g = torch.Generator(device=dev).manual_seed(11)
+    for name, shape, fn in (("cufft_c2c_us_per_snapshot", (n, G, G),
+                             lambda x: torch.fft.ifft2(x)),
+                            ("cufft_c2r_us_per_snapshot", (n, G, G // 2 + 1),
+                             lambda x: torch.fft.irfft2(x, s=(G, G)))):
+        x = torch.randn(*shape, dtype=torch.complex64, device=dev, generator=g)
+        y = fn(x)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            y = fn(x)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = round(e0.elapsed_time(e1) / 5 / n * 1e3, 2)
+        del x, y
+        torch.cuda.empty_cache()
+    return out
+
+
+def headline_config(args, world):
+    """The `config` object of the headline line (both arms print the same)."""
+    snap_mb = N_BL * N_CH * N_POL * 9 / 1e6
+    sharded = args.shard_observation and world > 1
+    return {"workload": WORKLOAD, "snapshots_per_step": args.snapshots, "mode": args.mode,
+            "engine": args.engine + (f"{args.batch}" if args.engine == "batch" else ""),
+            "resident_pool": args.pool, "image": N_IMG, "grid": G, "cell_arcsec": 2.0,
+            "tlisi_tile": 32, "candidate_mode": "periodic",
+            "l2": (f"inputs larger than L2 ({snap_mb:.0f} MB per snapshot, {args.pool} distinct "
+                   f"= {snap_mb * args.pool / 1e3:.1f} GB cycled; 40 = one pulsar period)"),
+            "parallelism": f"snapshot-shards{world}" if sharded else f"replicas{world}"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -264,7 +310,13 @@ def run_ours(args):
             image_batched(0, S, cube.data_ptr())
             return toi.tlisi_candidates(cube, T, toi.TOI_CAND_PERIODIC)
         if sharded:
-            shard.run_shard(S, world, rank, image_and_tlisi, local)
+            if B:   # this rank's [lo - 2, hi) through the batched engine
+                def image_batch(s0, s1, row):
+                    snaps = [pool[s % len(pool)] for s in range(s0, s1)]
+                    return plan.batch(snaps, local.data_ptr() + row * row_bytes)
+                shard.run_shard_batched(S, world, rank, image_batch, B)
+            else:
+                shard.run_shard(S, world, rank, image_and_tlisi, local)
             full = shard.gather_cube(local, S, world, rank)
             return toi.tlisi_candidates(full, T, toi.TOI_CAND_PERIODIC)
         for s in range(S):
@@ -438,6 +490,9 @@ def run_ours(args):
                          "grid ring, depth-5 image ring)"}
 
     mode3_plan = plan.mode3_info() if args.mode == 3 else None
+    fft_cmp = None
+    if rank == 0 and args.mode == 2 and not args.no_fft_comparison:
+        fft_cmp = fft_comparison(prof, per_launch, 2 * w.image_size, dev)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and default_shape:
         cpu = cpu_baseline()
@@ -448,18 +503,20 @@ def run_ours(args):
                "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
                "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (seeded MeerKAT-shaped snapshots, resident pool)",
-               "config": {"workload": workload + ("-3d-heights16m" if args.mode == 3 else ""),
-                          "snapshots_per_step": S, "mode": args.mode,
-                          "mode3_plan": mode3_plan,
-                          "engine": args.engine + (f"{B}" if B else ""),
-                          "resident_pool": args.pool, "image": w.image_size,
-                          "grid": 2 * w.image_size, "cell_arcsec": round(cell, 6),
-                          "tlisi_tile": T, "candidate_mode": "periodic",
-                          "l2": (f"inputs larger than L2 ({snap_mb:.0f} MB per snapshot, "
-                                 f"{args.pool} distinct = {snap_mb * args.pool / 1e3:.1f} GB "
-                                 f"cycled; 40 = one pulsar period)"),
-                          "parallelism": (f"snapshot-shards{world}" if sharded
-                                          else f"replicas{world}")},
+               "config": (headline_config(args, world) if default_shape and args.mode == 2 else
+                          {"workload": workload + ("-3d-heights16m" if args.mode == 3 else ""),
+                           "snapshots_per_step": S, "mode": args.mode,
+                           "mode3_plan": mode3_plan,
+                           "engine": args.engine + (f"{B}" if B else ""),
+                           "resident_pool": args.pool, "image": w.image_size,
+                           "grid": 2 * w.image_size, "cell_arcsec": round(cell, 6),
+                           "tlisi_tile": T, "candidate_mode": "periodic",
+                           "l2": (f"inputs larger than L2 ({snap_mb:.0f} MB per snapshot, "
+                                  f"{args.pool} distinct = {snap_mb * args.pool / 1e3:.1f} GB "
+                                  f"cycled)"),
+                           "parallelism": (f"snapshot-shards{world}" if sharded
+                                           else f"replicas{world}")}),
+               "fft_comparison": fft_cmp,
                "roofline": roofline, "stages": stages, "gpu_launches": int(launches),
                "candidates_found": found[2] if found else None,
                "clocks": ck, "e2e": e2e, "cpu_baseline": cpu}
@@ -594,6 +651,137 @@ def run_uneven(args):
         "clocks": ck}))
     for p in plans.values():
         p.close()
+
+
+def run_fp16(args):
+    """The precision workload: one observation of 300 distinct snapshots of
+    the faint-transient stream at the MeerKAT shape (two transients at 3 and
+    5 sigma of the image noise in 10-snapshot windows, a pulsar ramping from
+    1 to 2 Jy, 5 % flags), imaged by the batched engine with the visibilities
+    stored as FP16 pairs with a per-channel FP32 scale (FP32 gridding and FFT,
+    FP64 plane fit and coordinate factors), then the non-periodic candidate
+    search (Section 6.3, 4 sigma).  The same observation stored as complex64
+    is timed next to it, and the two pipelines' images are compared on every
+    25th snapshot."""
+    import torch
+
+    import paper_2512_06254_gb300 as toi
+    from paper_2512_06254_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    host_cpus = bind_host_to_gpu(0)
+    S = args.snapshots if args.snapshots != 1500 else 300
+    B, T = args.batch, 32
+    w = synth.faint_transient_workload(n_snap=S)
+    nt = w.image_size // T
+    peak, peak_kind = load_peaks()
+    sample = list(range(2, S, 25))
+    results, images = {}, {}
+    for storage in ("fp16", "c64"):
+        snaps = []
+        for s in range(S):
+            sn = synth.make_snapshot(w, s, device=dev)
+            sn.pop("weight")
+            if storage == "fp16":
+                q, scale = synth.to_fp16_channel_scaled(sn["vis"])
+                sn["vis"], sn["chan_scale"] = q, scale
+            snaps.append(sn)
+        torch.cuda.synchronize()
+        vdt = toi.TOI_VIS_C16_CHANSCALE if storage == "fp16" else toi.TOI_VIS_C64
+        plan = toi.Plan(w.image_size, w.cell_arcsec, w.n_bl, w.n_chan, w.n_pol, tlisi_tile=T,
+                        batch_max=B, vis_dtype=vdt)
+        cube = torch.empty(S, nt, nt, dtype=torch.float32, device=dev)
+
+        def step(with_images=False):
+            plan.tlisi_reset()
+            for lo in range(0, S, B):
+                hi = min(S, lo + B)
+                group = snaps[lo:hi]
+                if with_images:
+                    group = [dict(g, image=images[storage][i]) if i in images[storage] else g
+                             for i, g in zip(range(lo, hi), group)]
+                plan.batch(group, cube[lo:hi])
+            return toi.tlisi_candidates(cube[2:], T, toi.TOI_CAND_NONPERIODIC)
+
+        images[storage] = {i: torch.empty(w.image_size, w.image_size, device=dev) for i in sample}
+        step(with_images=True)
+        for _ in range(args.warmup):
+            step()
+        if plan.sync_status() != toi.TOI_OK:
+            raise RuntimeError(plan.last_error())
+        plan.profile_read()
+        plan.profile_enable(True)
+        clocks = ClockSampler(0)
+        torch.cuda.synchronize()
+        clocks.start()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        found = None
+        for _ in range(args.steps):
+            found = step()
+        t1.record()
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        ms = t0.elapsed_time(t1)
+        prof = plan.profile_read()
+        plan.profile_enable(False)
+        if plan.sync_status() != toi.TOI_OK:
+            raise RuntimeError(plan.last_error())
+        n = S * args.steps
+        sb = survey_bytes(w.n_bl, w.n_chan, w.n_pol, w.image_size,
+                          vis_bytes=4 if storage == "fp16" else 8)
+        g_ms = prof["grid"][0]
+        g_gbs = sb["grid"] * n / (g_ms / 1e3) / 1e9
+        path_b = sum(sb[k] for k in PATH_STAGES)
+        path_gbs = path_b * n / (ms / 1e3) / 1e9
+        results[storage] = {
+            "value": round(n / (ms / 1e3), 2), "ms_per_step": round(ms / args.steps, 3),
+            "candidates": found[2], "boxes": found[1], "threshold": found[0],
+            "roofline": {"bound": "hbm", "kernel": "grid", "achieved": round(g_gbs, 1),
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": round(g_gbs / peak, 4), "traffic": None,
+                         "alg_bytes_per_launch": sb["grid"] * B,
+                         "share": round(g_ms / sum(v[0] for v in prof.values()), 3),
+                         "path_alg_bytes_per_snapshot": path_b, "path_gbs": round(path_gbs, 1),
+                         "path_frac": round(path_gbs / peak, 4)},
+            "stages": {k: {"ms_per_launch": round(v[0] / max(v[1], 1), 4), "launches": v[1]}
+                       for k, v in prof.items() if v[1]},
+            "gpu_launches": int(sum(v[1] for v in prof.values()) + 5 * args.steps),
+            "clocks": ck}
+        plan.close()
+        del snaps, cube
+        torch.cuda.empty_cache()
+    diffs = []
+    for i in sample:
+        a, b = images["fp16"][i], images["c64"][i]
+        diffs.append(float((a - b).abs().max() / b.abs().max()))
+    r16, r32 = results["fp16"], results["c64"]
+    print(json.dumps({
+        "metric": METRIC, "value": r16["value"], "unit": "snapshots/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r16["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (visibilities stored f16 + per-channel f32 scale)",
+        "data": "synthetic (seeded faint-transient MeerKAT-shaped stream, all snapshots distinct "
+                "and resident)",
+        "config": {"workload": f"meerkat-faint-transients-2016bl-4096ch-4pol-2048px-{S}snap-fp16",
+                   "snapshots_per_step": S, "engine": f"batch{B}",
+                   "candidate_mode": "nonperiodic (4 sigma)", "host_cpus": host_cpus,
+                   "l2": "inputs larger than L2 (165 MB per FP16 snapshot, all distinct)"},
+        "roofline": r16["roofline"], "stages": r16["stages"],
+        "gpu_launches": r16["gpu_launches"], "clocks": r16["clocks"],
+        "candidates": {"fp16": {"n": r16["candidates"], "boxes": r16["boxes"],
+                                "threshold": r16["threshold"]},
+                       "c64": {"n": r32["candidates"], "boxes": r32["boxes"],
+                               "threshold": r32["threshold"]},
+                       "same_boxes": r16["boxes"] == r32["boxes"]},
+        "fp16_vs_c64_image_max_rel_err": {"max": max(diffs), "snapshots": sample,
+                                          "per_snapshot": [round(d, 9) for d in diffs]},
+        "c64_same_stream": {"value": r32["value"], "ms_per_step": r32["ms_per_step"],
+                            "roofline": r32["roofline"], "stages": r32["stages"],
+                            "clocks": r32["clocks"]},
+        "e2e": None, "cpu_baseline": None}))
 
 
 def run_adjoint(args):
@@ -771,23 +959,96 @@ print(json.dumps({{"seconds": dt}}))
 """
 
 
-def cpu_baseline(snap_index: int = 7):
-    """The FP64 oracle, as it stands, imaging one MeerKAT-shaped snapshot
-    (S1-S7) on one host core, in a fresh process."""
+POOL_SNIPPET = r"""
+import concurrent.futures as cf, json, multiprocessing as mp, os, sys, time
+sys.path.insert(0, {root!r})
+
+def one(s):
+    import numpy as np
+    from paper_2512_06254_gb300 import synth
+    from oracle import toi_oracle as O
+    w = synth.meerkat_workload()
+    sn = synth.make_snapshot(w, s)
+    h = {{k: (v.numpy() if v is not None else None) for k, v in sn.items()}}
+    rng = np.random.default_rng(s)
+    prev = [rng.normal(size=(w.image_size, w.image_size)) for _ in range(2)]
+    t0 = time.time()
+    r = O.image_snapshot(h["uvw"], h["freq"], h["vis"], h["flag"], None, w.image_size,
+                         w.cell_arcsec)
+    O.tlisi(prev[0], prev[1], r["image"], 32)
+    return t0, time.time()
+
+if __name__ == "__main__":
+    n, workers = {n}, {workers}
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        spans = list(ex.map(one, range(n)))
+    print(json.dumps({{"seconds": max(b for _, b in spans) - min(a for a, _ in spans)}}))
+"""
+
+
+def mem_available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return 16.0
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+def _oracle_env():
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
+    return env
+
+
+def cpu_baseline(snap_index: int = 7, all_cores: bool = True):
+    """The FP64 oracle, as it stands, imaging MeerKAT-shaped snapshots (S1-S7)
+    in fresh processes: one snapshot on one host core, and (all_cores) 16
+    snapshots over a pool of one single-threaded process per host core."""
     code = CPU_SNIPPET.format(root=ROOT, s=snap_index)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=900)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                       env=_oracle_env(), timeout=900)
     if r.returncode != 0:
         return {"error": r.stderr[-400:]}
     sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
-    return {"value": round(1.0 / sec, 5), "unit": "snapshots/s", "cores": 1, "kind": "oracle",
-            "sample": "1 MeerKAT-shaped snapshot (2016 bl x 4096 ch x 4 pol, 2048^2): S1-S6 "
-                      "imaging + one tLISI matrix, FP64 numpy oracle, 1 thread",
-            "seconds": round(sec, 2)}
+    ncores = len(os.sched_getaffinity(0))
+    out = {"value": round(1.0 / sec, 5), "unit": "snapshots/s", "cores": 1, "kind": "oracle",
+           "sample": "1 MeerKAT-shaped snapshot (2016 bl x 4096 ch x 4 pol, 2048^2): S1-S6 "
+                     "imaging + one tLISI matrix, FP64 numpy oracle, 1 thread",
+           "seconds": round(sec, 2), "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+           "host_cores_available": ncores}
+    if all_cores:
+        n = 16
+        # about 3.5 GB of host memory per oracle process at this shape
+        workers = max(1, min(n, ncores, int(mem_available_gb() // 4.5)))
+        code = POOL_SNIPPET.format(root=ROOT, n=n, workers=workers)
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                           env=_oracle_env(), timeout=1800)
+        if r.returncode == 0:
+            wall = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+            out["all_cores"] = {"value": round(n / wall, 4), "unit": "snapshots/s",
+                                "cores": workers, "seconds": round(wall, 2),
+                                "sample": f"{n} MeerKAT-shaped snapshots (S1-S6 + one tLISI "
+                                          f"matrix each), one single-threaded oracle process "
+                                          f"per core, wall time of the imaging"}
+        else:
+            out["all_cores"] = {"error": r.stderr[-300:]}
+    return out
 
 
 def run_reference(args):
@@ -807,7 +1068,7 @@ def run_reference(args):
         O.image_snapshot(h["uvw"], h["freq"], h["vis"], h["flag"], None, tw.image_size, tw.cell_arcsec)
     secs = []
     for k in range(args.steps):
-        cb = cpu_baseline(snap_index=k)
+        cb = cpu_baseline(snap_index=k, all_cores=False)
         if "error" in cb:
             print(json.dumps({"impl": "reference", "unavailable": cb["error"][-200:]}))
             return
@@ -815,13 +1076,16 @@ def run_reference(args):
     total = sum(secs)
     value = args.steps / total
     cpu = {"value": round(value, 5), "unit": "snapshots/s", "cores": 1, "kind": "oracle",
-           "sample": "1 MeerKAT-shaped snapshot per step (S1-S6 + one tLISI matrix), FP64 numpy"}
+           "sample": "1 MeerKAT-shaped snapshot per step (S1-S6 + one tLISI matrix), FP64 numpy",
+           "cpu_model": cpu_model(), "nproc": os.cpu_count()}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(value, 5),
                       "unit": "snapshots/s", "n_gpus": world, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 1),
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                       "dtype": "f64", "data": "synthetic (seeded MeerKAT-shaped snapshots)",
-                      "config": {"workload": WORKLOAD, "snapshots_per_step": 1},
+                      "config": headline_config(args, world),
+                      "reference_sample": "each step images 1 MeerKAT-shaped snapshot of the "
+                                          "workload with the FP64 oracle on 1 host core",
                       "cpu_baseline": cpu,
                       "e2e": {"value": round(value, 5), "unit": "snapshots/s",
                               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -871,6 +1135,8 @@ def main():
     ap.add_argument("--e2e-warmup", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fft-comparison", action="store_true",
+                    help="skip the cuFFT comparison of the inverse transform")
     ap.add_argument("--engine", default="batch", choices=["single", "batch"],
                     help="single: toi_grid + toi_image + tlisi_update per snapshot; batch: "
                          "toi_batch over --batch snapshots per launch")
@@ -896,9 +1162,11 @@ def main():
     ap.add_argument("--windows", type=int, default=64,
                     help="localise workload: candidate windows per snapshot")
     ap.add_argument("--workload", default="meerkat",
-                    choices=["meerkat", "uneven", "adjoint", "localise"],
+                    choices=["meerkat", "uneven", "adjoint", "localise", "fp16"],
                     help="meerkat: the headline stream; uneven: the batched uneven stream "
-                         "(512 snapshots, 1024-4096 channels, 0-60%% flags, 1024/2048 px)")
+                         "(512 snapshots, 1024-4096 channels, 0-60%% flags, 1024/2048 px); "
+                         "fp16: 300 faint-transient snapshots stored as FP16 + channel scale, "
+                         "next to the same stream in complex64")
     ap.add_argument("--graph", action="store_true",
                     help="uneven workload: replay one captured toi_batch_run per batch")
     ap.add_argument("--shard-observation", action="store_true",
@@ -916,6 +1184,8 @@ def main():
         run_uneven(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "fp16":
+        run_fp16(args)
     elif args.workload == "localise":
         run_localise(args)
     else:

@@ -60,6 +60,29 @@ def run_shard(S: int, world: int, rank: int,
     return lo, hi
 
 
+def run_shard_batched(S: int, world: int, rank: int,
+                      image_batch: Callable[[int, int, int], int], batch: int) -> Tuple[int, int]:
+    """Image this rank's snapshots [lo - 2, hi) in order, in batches of at
+    most `batch` (the library's batched engine).  `image_batch(s0, s1, row)`
+    images snapshots [s0, s1) as the next batch of the plan's stream and
+    returns its first_valid (the entries before it have no three-image
+    window yet); the tLISI of snapshot s >= lo belongs in local row s - lo,
+    and `row` = s0 - lo is the local row of the batch's first snapshot
+    (negative for the 2-snapshot halo, whose entries get no tLISI).
+    Returns (lo, hi)."""
+    if batch < 1:
+        raise ValueError("batch must be >= 1")
+    first, hi = image_range(S, world, rank)
+    lo, _ = tlisi_range(S, world, rank)
+    for s0 in range(first, hi, batch):
+        s1 = min(hi, s0 + batch)
+        fv = image_batch(s0, s1, s0 - lo)
+        expected = max(0, min(lo - s0, s1 - s0))
+        if fv != expected:
+            raise RuntimeError(f"batch [{s0}, {s1}): first_valid {fv}, expected {expected}")
+    return lo, hi
+
+
 def gather_cube(local: torch.Tensor, S: int, world: int, rank: int, group=None) -> torch.Tensor:
     """All-gather the ranks' tLISI blocks into the full cube [S - 2, nty, ntx]
     (same device as `local`).  `local` holds this rank's hi - lo slices in its

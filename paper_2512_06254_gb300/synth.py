@@ -232,18 +232,22 @@ def meerkat_workload(n_snap: int = 1500, n_chan: int = 4096,
     return replace(w, sources=tuple(src))
 
 
-def faint_transient_workload(n_snap: int = 300) -> Workload:
+def faint_transient_workload(n_snap: int = 300, n_chan: int = 4096, image_size: int = 2048,
+                             cell_arcsec: float = 2.0) -> Workload:
     """MeerKAT shape with two faint transients (3 and 5 sigma of the image
-    noise) in disjoint 10-snapshot windows and a pulsar whose flux ramps
-    from 1 to 2 Jy over the run."""
-    base = meerkat_workload(n_snap=n_snap)
+    noise of this channel count) in disjoint 10-snapshot windows starting at
+    n_snap // 3 and 40 snapshots later (100 and 140 for 300 snapshots), and a
+    pulsar whose flux ramps from 1 to 2 Jy over the run."""
+    base = meerkat_workload(n_snap=n_snap, n_chan=n_chan, image_size=image_size,
+                            cell_arcsec=cell_arcsec)
     n_vis = base.n_bl * base.n_chan * 2 * (1 - base.flag_frac)
     sigma_img = base.noise_sigma / math.sqrt(n_vis)
     src = list(s for s in base.sources if s.kind == "steady")
+    t0 = n_snap // 3
     for k, nsig in enumerate((3.0, 5.0)):
         l, m = random_position(base.fov_rad, base.seed_sky + 200 + k)
         src.append(Source(l, m, nsig * sigma_img, kind="window",
-                          on_from=100 + 40 * k, on_to=110 + 40 * k))
+                          on_from=t0 + 40 * k, on_to=t0 + 10 + 40 * k))
     l, m = random_position(base.fov_rad, base.seed_sky + 100)
     src.append(Source(l, m, 1.0, kind="ramp", ramp_to=2.0))
     return replace(base, name="meerkat-faint-transients", sources=tuple(src))

@@ -22,10 +22,13 @@ class Job:
     uvw_index: Optional[int] = None
     with_weights: bool = False
     keep: tuple = ("image",)    # keys of the oracle result to return
+    fp16: bool = False          # also image the FP16-stored values (decoded) -> "image_dec",
+                                # with the quantisation bound sum |dc| / (omega sum w) -> "bound"
 
 
 def _run(job: Job):
     import numpy as np
+    import torch
     from paper_2512_06254_gb300 import synth
     from oracle import toi_oracle as O
     w = job.workload
@@ -33,7 +36,23 @@ def _run(job: Job):
     h = {k: (v.numpy() if v is not None else None) for k, v in sn.items()}
     r = O.image_snapshot(h["uvw"], h["freq"], h["vis"], h["flag"], h["weight"], w.image_size,
                          w.cell_arcsec)
-    return {k: np.asarray(r[k]) for k in job.keep}
+    out = {k: np.asarray(r[k]) for k in job.keep}
+    if job.fp16:
+        q, scale = synth.to_fp16_channel_scaled(sn["vis"])
+        qd = q.double()
+        dec = torch.complex(qd[..., 0], qd[..., 1]) * scale.double()[None, :, None]
+        rd = O.image_snapshot(h["uvw"], h["freq"], dec.numpy(), h["flag"], h["weight"],
+                              w.image_size, w.cell_arcsec)
+        out["image_dec"] = np.asarray(rd["image"])
+        pa, pb = O.parallel_hands(w.n_pol)
+        d = (dec - sn["vis"].to(torch.complex128)).numpy()
+        keep = (h["flag"] == 0)
+        wts = h["weight"] if h["weight"] is not None else np.ones(keep.shape)
+        dc = d[..., pa] * keep[..., pa] * wts[..., pa]
+        if pb != pa:
+            dc = dc + d[..., pb] * keep[..., pb] * wts[..., pb]
+        out["bound"] = float(np.abs(dc).sum()) / (r["omega"] * r["sumw"])
+    return out
 
 
 def _init():
