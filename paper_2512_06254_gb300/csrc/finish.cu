@@ -64,13 +64,25 @@ __device__ __forceinline__ Source reproject_source(int o1, int o2, int N, float 
   // few 1e-2 at most, so each step shrinks the error by that factor.  Steps
   // stop once one moves the position by less than 2^-16 px (the error left
   // is that factor times smaller), at most 8.
+  //
+  // z = q / (1 + sqrt(1 - q)) = 1 - sqrt(1 - q) has the binomial series
+  // q/2 + q^2/8 + q^3/16 + 5 q^4/128 + 7 q^5/256 + 21 q^6/1024 + ...; for
+  // q < 4e-3 (fields up to about 5 degrees across) the terms after q^5 are
+  // below 1e-14 of z, so the series (five fused multiply-adds) replaces the
+  // square root and division there.
   float e1 = 0.f, e2 = 0.f;
+  const bool series = b2 * (D1 * D1 + D2 * D2) < 4e-3f;
   for (int it = 0; it < 8; ++it) {
     const float u1 = D1 + e1, u2 = D2 + e2;
     const float q = b2 * (u1 * u1 + u2 * u2);
-    float rt;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(rt) : "f"(1.0f - q));
-    const float z = __fdividef(q, 1.0f + rt);
+    float z;
+    if (series) {
+      z = q * fmaf(q, fmaf(q, fmaf(q, fmaf(q, 0.02734375f, 0.0390625f), 0.0625f), 0.125f), 0.5f);
+    } else {
+      float rt;
+      asm("sqrt.approx.f32 %0, %1;" : "=f"(rt) : "f"(1.0f - q));
+      z = __fdividef(q, 1.0f + rt);
+    }
     const float n1 = -K1 * z, n2 = -K2 * z;
     const float step = fabsf(n1 - e1) + fabsf(n2 - e2);
     e1 = n1;
@@ -183,77 +195,93 @@ image_tile_kernel(const float* __restrict__ src, int N, int T, const double* __r
                          with_moments, tile_mom, max_cur, blockIdx.x);
 }
 
-// Batch, in two launches.  Entry i's window holds entries i-1 and i-2 of
-// the same batch, so the images are made first, all entries in parallel
-// (image_tile_body without moments: ring, caller's image, max |I|); then one
-// block per tile walks the entries in stream order and forms the window
-// moments, keeping each pixel's two previous images in registers so that
-// every stored image is read once.  Pixel order and sums are those of
-// image_tile_body: the moments equal the unbatched ones bit for bit.
-__global__ void __launch_bounds__(kFinThreads)
-image_tile_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
-                 int T, double beta_rad) {
-  if ((int)blockIdx.y >= hdr->n) return;
-  const BatchEntry& e = E[blockIdx.y];
-  image_tile_body<true>(e.tilted, N, T, e.snap, beta_rad, e.ring_cur, e.ring_p1, e.ring_p2,
-                        e.image_out, 0, e.tile_mom, e.max_cur, blockIdx.x);
-}
-
 constexpr int kBatchPix = 4;   // pixels per thread of a tile of up to 32 x 32
 
 constexpr int kMaxBatch = 64;   // toi_config.batch_max limit
 
+// Batch, in one launch: one block per tile walks the entries in stream
+// order.  For entry i it re-projects the tile from the entry's tilted image
+// (as image_tile_body), stores it to the ring and the caller's image, and
+// forms the window moments of entry i from the tile's pixels of entries
+// i - 2, i - 1 and i, which it keeps in registers (the two images before the
+// batch are read from the ring once).  Every image of the batch is written
+// once and never read back.  Pixel order, arithmetic and the reduction order
+// are those of image_tile_body and window_moments_batch, so the images and
+// moments equal theirs bit for bit.
 __global__ void __launch_bounds__(kFinThreads)
-window_moments_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
-                     int T) {
-  // per entry and warp, the five float32 warp sums (as in block_reduce_d)
+image_walk_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
+                 int T) {
   __shared__ float part[kMaxBatch][kFinThreads / 32][5];
   const int n = hdr->n;
   const int tile = blockIdx.x;
   const int ntx = N / T;
   const int tx = tile % ntx, ty = tile / ntx;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int o1v[kBatchPix], o2v[kBatchPix];
   size_t pixv[kBatchPix];
   bool live[kBatchPix];
-  float prev1[kBatchPix], prev2[kBatchPix], cur[kBatchPix];
+  float prev1[kBatchPix], prev2[kBatchPix];
 #pragma unroll
   for (int b = 0; b < kBatchPix; ++b) {
     const int e = threadIdx.x + b * kFinThreads;
     live[b] = e < T * T;
     const int ee = live[b] ? e : 0;
-    pixv[b] = (size_t)(ty * T + ee / T) * N + tx * T + (ee % T);
+    o1v[b] = tx * T + (ee % T);
+    o2v[b] = ty * T + (ee / T);
+    pixv[b] = (size_t)o2v[b] * N + o1v[b];
     prev1[b] = E[0].ring_p1[pixv[b]];
     prev2[b] = E[0].ring_p2[pixv[b]];
-    cur[b] = E[0].ring_cur[pixv[b]];
   }
   for (int i = 0; i < n; ++i) {
-    // prefetch the next entry's pixels while this one is summed
-    float nxt[kBatchPix];
-    const float* nsrc = (i + 1 < n) ? E[i + 1].ring_cur : nullptr;
+    const BatchEntry& e = E[i];
+    const float K1 = (float)e.snap[SNAP_REPRO];
+    const float K2 = (float)e.snap[SNAP_REPRO + 1];
+    const float b2 = (float)e.snap[SNAP_REPRO + 2];
+    const float* __restrict__ src = e.tilted;
+    float v[kBatchPix];
 #pragma unroll
-    for (int b = 0; b < kBatchPix; ++b) nxt[b] = nsrc ? nsrc[pixv[b]] : 0.f;
-    float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int b = 0; b < kBatchPix; ++b) {
+      const Source sr = reproject_source(o1v[b], o2v[b], N, K1, K2, b2);
+      const bool ok = live[b] && sr.ok;
+      const int i1 = ok ? sr.i1 : 0, i2 = ok ? sr.i2 : 0;
+      const bool has1 = i1 + 1 < N, has2 = i2 + 1 < N;
+      const float* r0 = src + (size_t)i2 * N;
+      const float* r1 = has2 ? r0 + N : r0;
+      const int i1n = has1 ? i1 + 1 : i1;
+      const float a00 = r0[i1], a01r = r0[i1n], a10r = r1[i1], a11r = r1[i1n];
+      const float a01 = has1 ? a01r : 0.f;
+      const float a10 = has2 ? a10r : 0.f;
+      const float a11 = (has1 && has2) ? a11r : 0.f;
+      const float f1 = sr.f1, f2 = sr.f2;
+      const float val = (1.f - f2) * ((1.f - f1) * a00 + f1 * a01) + f2 * ((1.f - f1) * a10 + f1 * a11);
+      v[b] = ok ? val : 0.f;
+    }
+    float mx = 0.f;
+    float m5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int b = 0; b < kBatchPix; ++b) {
       if (!live[b]) continue;
-      const float a = prev1[b] - prev2[b], bd = cur[b] - prev1[b];
-      v[0] += a; v[1] += bd; v[2] += a * a; v[3] += bd * bd; v[4] += a * bd;
+      e.ring_cur[pixv[b]] = v[b];
+      if (e.image_out) e.image_out[pixv[b]] = v[b];
+      mx = fmaxf(mx, fabsf(v[b]));
+      const float a = prev1[b] - prev2[b], bd = v[b] - prev1[b];
+      m5[0] += a; m5[1] += bd; m5[2] += a * a; m5[3] += bd * bd; m5[4] += a * bd;
     }
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    if (lane == 0) atomicMax(e.max_cur, __float_as_uint(mx));
 #pragma unroll
     for (int k = 0; k < 5; ++k)
-      for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+      for (int off = 16; off > 0; off >>= 1) m5[k] += __shfl_down_sync(0xffffffffu, m5[k], off);
     if (lane == 0)
 #pragma unroll
-      for (int k = 0; k < 5; ++k) part[i][wib][k] = v[k];
+      for (int k = 0; k < 5; ++k) part[i][wib][k] = m5[k];
 #pragma unroll
     for (int b = 0; b < kBatchPix; ++b) {
       prev2[b] = prev1[b];
-      prev1[b] = cur[b];
-      cur[b] = nxt[b];
+      prev1[b] = v[b];
     }
   }
   __syncthreads();
-  // the warp totals of each entry summed in float64 in warp order
   for (int q = threadIdx.x; q < n * 5; q += blockDim.x) {
     const int i = q / 5, k = q - 5 * (q / 5);
     const BatchEntry& e = E[i];
@@ -411,12 +439,9 @@ cudaError_t launch_finish_batch(toi_plan_s* p) {
   const int B = p->batch_max;
   if (p->T * p->T > kBatchPix * kFinThreads) return cudaErrorInvalidConfiguration;
   int tok = prof_begin(p, PROF_REPROJECT, 1);
-  image_tile_batch<<<dim3(ntl, B), kFinThreads, 0, p->stream>>>(p->bentry_dev, p->bheader_dev,
-                                                                p->N, p->T, p->beta_rad);
+  image_walk_batch<<<ntl, kFinThreads, 0, p->stream>>>(p->bentry_dev, p->bheader_dev, p->N, p->T);
   prof_end(p, tok);
-  tok = prof_begin(p, PROF_TLISI, 2);
-  window_moments_batch<<<ntl, kFinThreads, 0, p->stream>>>(p->bentry_dev, p->bheader_dev, p->N,
-                                                           p->T);
+  tok = prof_begin(p, PROF_TLISI, 1);
   tlisi_finish_batch<<<dim3((ntl + 255) / 256, B), 256, 0, p->stream>>>(p->bentry_dev,
                                                                          p->bheader_dev, ntl, p->T);
   prof_end(p, tok);

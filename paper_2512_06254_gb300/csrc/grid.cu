@@ -266,7 +266,7 @@ __device__ __forceinline__ float2 moment_value(float2 c, float r3, const MomentP
 // Per-lane shared-memory staging of the visibility stream: each lane keeps
 // two stages of kStage samples in flight with cp.async (completion tracked by
 // async-copy groups, so no register waits on outstanding loads).
-constexpr int kStage = 8;
+constexpr int kStage = 4;
 
 // Stage layout (per warp, struct of arrays so lane l's 4- and 8-byte words
 // fall in distinct banks): [stage][sample][lane].
@@ -750,8 +750,8 @@ __device__ __forceinline__ void grid_track2(const BaselineCoef* __restrict__ coe
   // fit) stores nothing
   const double reach = fmax(fabs(t.s1), fabs(t.s2)) * fmax(kf0, kf1);
   if (!(reach < 2.0 * G)) return;
-  const int c_begin = (seg * RPW + run_idx) * run;
-  const int c_end = min(nch, c_begin + run);
+  int c_begin = (seg * RPW + run_idx) * run;
+  int c_end = min(nch, c_begin + run);
   if (c_begin >= nch) return;
   int pa, pb;
   parallel_hands(npol, pa, pb);
@@ -759,6 +759,41 @@ __device__ __forceinline__ void grid_track2(const BaselineCoef* __restrict__ coe
   const double cxd = (double)(G / 2 - kW / 2), cyd = (double)(-kW / 2);
   const double k0 = snap[SNAP_K0], dkl = snap[SNAP_DK];
   const bool lin = snap[SNAP_KDEV] * fmax(fabs(t.s1), fabs(t.s2)) <= 1e-7;   // warp-uniform
+  // Run alignment.  The lanes of a warp walk consecutive runs of one track,
+  // all at the same speed v cells per channel; with runs of equal length
+  // their fractional positions differ, so each lane slides its window at
+  // its own iteration and the warp executes ~16 separate slides per cell of
+  // travel.  When the track moves fast enough on its major axis (at least
+  // one cell per kAlignChannels channels), every run boundary is moved
+  // forward by less than one crossing period so that each run starts at the
+  // fractional position of the track's first channel: the major-axis
+  // crossings of all lanes then fall in the same iteration (or the next),
+  // and one slide execution serves the whole warp.  Boundaries stay shared
+  // between neighbouring runs, so every channel is still gridded once.
+  if (lin) {
+    constexpr double kAlignChannels = 64.0;
+    const double vx = t.s1 * dkl, vy = t.s2 * dkl;
+    const bool xmaj = fabs(vx) >= fabs(vy);
+    const double v = xmaj ? vx : vy, sm = xmaj ? t.s1 : t.s2, cm = xmaj ? cxd : cyd;
+    if (fabs(v) * kAlignChannels >= 1.0 && fabs(v) * run >= 4.0) {
+      const double h0 = cm + sm * k0;
+      const double ph0 = h0 - floor(h0);
+      // first channel of the track's run L
+      auto aligned = [&](int L) -> int {
+        const int cn = L * run;
+        if (L <= 0) return 0;
+        if (cn >= nch) return nch;
+        const double hn = cm + sm * (k0 + (double)cn * dkl);
+        const double d = ph0 - (hn - floor(hn));
+        const double delta = v > 0.0 ? (d - floor(d)) / v : ((-d) - floor(-d)) / (-v);
+        return min(nch, cn + (int)rint(delta));
+      };
+      const int L = seg * RPW + run_idx;
+      c_begin = aligned(L);
+      c_end = aligned(L + 1);
+      if (c_begin >= c_end) return;
+    }
+  }
   long long hx = 0, hy = 0, vx = 0, vy = 0;
   if (lin) {
     const double kb = k0 + (double)c_begin * dkl;

@@ -155,7 +155,41 @@ prep_baselines_body(const uint8_t* __restrict__ flag, const float* __restrict__ 
       }
     };
     constexpr int U = 8;   // independent loads in flight per lane
-    if (npol == 4 && flag && (nch & 3) == 0 &&
+    if (npol == 4 && flag && !weight && (nch & 3) == 0 &&
+        (reinterpret_cast<uintptr_t>(flag) & 15) == 0) {
+      // Unit weights (the common case): per channel only integer work on
+      // the flag word.  The two parallel-hand bytes (pols 0 and 3) are
+      // reduced to one "nonzero" bit each; their population count is the
+      // number of flagged hands, and a channel with both set is deselected.
+      const uint4* f16 = reinterpret_cast<const uint4*>(flag + base);
+      const int ngrp = nch >> 2;
+      int unflagged = 0;
+      for (int g0 = lane; g0 < ngrp; g0 += 32 * U) {
+        uint4 fv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int g = g0 + 32 * u;
+          fv[u] = g < ngrp ? __ldcs(f16 + g) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        unsigned int dmask = 0u;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const bool live = g0 + 32 * u < ngrp;
+          const unsigned int w4[4] = {fv[u].x, fv[u].y, fv[u].z, fv[u].w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            unsigned int nz = w4[i] | (w4[i] >> 4);
+            nz |= nz >> 2;
+            nz |= nz >> 1;
+            nz &= 0x01000001u;
+            if (live) unflagged += 2 - __popc(nz);
+            if (live && nz == 0x01000001u) dmask |= 1u << (4 * u + i);
+          }
+        }
+        fold(dmask, [&](int bit) { return 4 * (g0 + 32 * (bit >> 2)) + (bit & 3); });
+      }
+      cnt = unflagged;
+    } else if (npol == 4 && flag && (nch & 3) == 0 &&
         (reinterpret_cast<uintptr_t>(flag) & 15) == 0) {
       // 16 bytes = the 4 pols of 4 consecutive channels; 32 KB per warp in flight
       const uint4* f16 = reinterpret_cast<const uint4*>(flag + base);
