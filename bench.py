@@ -238,6 +238,10 @@ def headline_config(args, world):
             "engine": args.engine + (f"{args.batch}" if args.engine == "batch" else ""),
             "resident_pool": args.pool, "image": N_IMG, "grid": G, "cell_arcsec": 2.0,
             "tlisi_tile": 32, "candidate_mode": "periodic",
+            "candidate_search": ("pipelined: observation k's search on a low-priority stream "
+                                 "during observation k+1's imaging"
+                                 if args.s8_overlap and args.engine == "batch" and not sharded
+                                 else "after each observation's imaging"),
             "l2": (f"inputs larger than L2 ({snap_mb:.0f} MB per snapshot, {args.pool} distinct "
                    f"= {snap_mb * args.pool / 1e3:.1f} GB cycled; 40 = one pulsar period)"),
             "parallelism": f"snapshot-shards{world}" if sharded else f"replicas{world}"}
@@ -280,12 +284,36 @@ def run_ours(args):
     nt = w.image_size // T
     pool = make_pool(w, args.pool, dev)
     B = args.batch if args.engine == "batch" else 0
+    sharded = args.shard_observation and world > 1
+    # Observations are pipelined as a streaming deployment runs them: the
+    # candidate search (S8, float64, about 50 ms for 1498 x 64 x 64 on this
+    # GPU) of observation k runs on its own low-priority stream while
+    # observation k + 1 is imaged on a high-priority one; every step still
+    # images its 1500 snapshots and searches its own cube, and the timed
+    # region ends when the last search has finished.
+    overlap = (args.s8_overlap and B > 0 and not sharded and args.mode == 2)
+    lo_prio, hi_prio = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+    img_stream = torch.cuda.Stream(device=dev, priority=hi_prio) if overlap else None
+    s8_stream = torch.cuda.Stream(device=dev, priority=lo_prio) if overlap else None
+    if overlap:
+        torch.cuda.set_stream(img_stream)
     plan = toi.Plan(w.image_size, w.cell_arcsec, w.n_bl, w.n_chan, w.n_pol, tlisi_tile=T,
                     batch_max=B, mode=args.mode, grid_rows=args.grid_rows)
-    cube = torch.empty(S - 2, nt, nt, dtype=torch.float32, device=dev)
+    cubes = [torch.empty(S - 2, nt, nt, dtype=torch.float32, device=dev)
+             for _ in range(2 if overlap else 1)]
+    cube = cubes[0]
     row_bytes = nt * nt * 4
+    import concurrent.futures as _cf
+    s8_pool = _cf.ThreadPoolExecutor(1) if overlap else None
+    s8_pending = [None, None]
+    s8_done = []
 
-    sharded = args.shard_observation and world > 1
+    def s8_job(c, ev):
+        with torch.cuda.stream(s8_stream):          # the worker thread's current stream
+            s8_stream.wait_event(ev)
+            return toi.tlisi_candidates(c, T, toi.TOI_CAND_PERIODIC, stream=s8_stream)
+
+    step_no = [0]
     if sharded:
         # one observation split across ranks (2-snapshot halos, one all-gather)
         local = torch.empty(-(-(S - 2) // world), nt, nt, dtype=torch.float32, device=dev)
@@ -306,6 +334,16 @@ def run_ours(args):
 
     def step():
         plan.tlisi_reset()
+        if overlap:
+            k = step_no[0] % 2
+            step_no[0] += 1
+            if s8_pending[k] is not None:            # the search still reading this cube
+                s8_done.append(s8_pending[k].result())
+            image_batched(0, S, cubes[k].data_ptr())
+            ev = torch.cuda.Event()
+            ev.record(img_stream)
+            s8_pending[k] = s8_pool.submit(s8_job, cubes[k], ev)
+            return None
         if B and not sharded:
             image_batched(0, S, cube.data_ptr())
             return toi.tlisi_candidates(cube, T, toi.TOI_CAND_PERIODIC)
@@ -323,8 +361,19 @@ def run_ours(args):
             image_and_tlisi(s, cube[s - 2] if s >= 2 else None)
         return toi.tlisi_candidates(cube, T, toi.TOI_CAND_PERIODIC)
 
+    def drain():
+        out = None
+        for k in (0, 1):
+            if s8_pending[k] is not None:
+                s8_done.append(s8_pending[k].result())
+                s8_pending[k] = None
+        if s8_done:
+            out = s8_done[-1]
+        return out
+
     for _ in range(args.warmup):
         step()
+    drain()
     if plan.sync_status() != toi.TOI_OK:
         raise RuntimeError(plan.last_error())
     plan.profile_read()                       # reset counters
@@ -338,8 +387,12 @@ def run_ours(args):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
     found = None
+    s8_done.clear()
     for _ in range(args.steps):
         found = step()
+    if overlap:
+        found = drain()                       # the last observations' searches
+        assert len(s8_done) == args.steps
     t1.record()
     torch.cuda.synchronize()
     if world > 1:
@@ -1137,6 +1190,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fft-comparison", action="store_true",
                     help="skip the cuFFT comparison of the inverse transform")
+    ap.add_argument("--s8-overlap", type=int, default=0, choices=[0, 1],
+                    help="1: the candidate search of observation k runs on a low-priority stream "
+                         "while observation k + 1 is imaged (batched engine)")
     ap.add_argument("--engine", default="batch", choices=["single", "batch"],
                     help="single: toi_grid + toi_image + tlisi_update per snapshot; batch: "
                          "toi_batch over --batch snapshots per launch")

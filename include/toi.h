@@ -193,6 +193,9 @@ toi_status tlisi_reset(toi_plan_t plan);
  * nboxes:    host int32 out, the number of boxes found (may exceed
  *            max_boxes; only the first max_boxes are written).
  * scores:    dev float64 [nty][ntx] out, or NULL.
+ * nty * ntx may be at most 131072 (TOI_ERR_ARG beyond): the labelling runs
+ * in one block, whose worst case (one component winding through every tile)
+ * grows with the square of the tile count.
  * Allocates and frees its device scratch; synchronises `stream`. */
 toi_status tlisi_candidates(const float* cube, int32_t S, int32_t nty,
                             int32_t ntx, int32_t tile, int32_t mode,

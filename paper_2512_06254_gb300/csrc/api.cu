@@ -747,7 +747,8 @@ toi_status tlisi_candidates(const float* cube, int32_t S, int32_t nty, int32_t n
                             int32_t* nboxes, int32_t max_boxes, double* scores) {
   if (!cube || !threshold || !nboxes) return fail(nullptr, TOI_ERR_ARG, "cube, threshold and nboxes must be non-NULL");
   if (S < 1 || nty < 1 || ntx < 1 || tile < 1) return fail(nullptr, TOI_ERR_ARG, "S, nty, ntx, tile must be >= 1");
-  if ((long long)nty * ntx > (1 << 20)) return fail(nullptr, TOI_ERR_ARG, "too many tiles");
+  if ((long long)nty * ntx > toi::kMaxCandTiles)
+    return fail(nullptr, TOI_ERR_ARG, "more than 131072 tiles (the labelling runs in one block)");
   if (mode != TOI_CAND_PERIODIC && mode != TOI_CAND_NONPERIODIC) return fail(nullptr, TOI_ERR_ARG, "unknown mode");
   if (max_boxes < 0 || (max_boxes > 0 && !boxes)) return fail(nullptr, TOI_ERR_ARG, "boxes must hold max_boxes entries");
   cudaStream_t st = (cudaStream_t)stream;

@@ -49,7 +49,8 @@ extern "C" toi_status tlisi_candidates_noalloc(const float* cube, int32_t S, int
     return nofail(TOI_ERR_ARG, "cube, threshold and nboxes must be non-NULL");
   if (S < 1 || nty < 1 || ntx < 1 || tile < 1)
     return nofail(TOI_ERR_ARG, "S, nty, ntx, tile must be >= 1");
-  if ((long long)nty * ntx > (1 << 20)) return nofail(TOI_ERR_ARG, "too many tiles");
+  if ((long long)nty * ntx > toi::kMaxCandTiles)
+    return nofail(TOI_ERR_ARG, "more than 131072 tiles (the labelling runs in one block)");
   if (mode != TOI_CAND_PERIODIC && mode != TOI_CAND_NONPERIODIC)
     return nofail(TOI_ERR_ARG, "unknown mode");
   if (max_boxes < 0 || (max_boxes > 0 && !boxes))

@@ -12,6 +12,13 @@
 namespace toi {
 
 constexpr double kCLight = 299792458.0;
+
+// Largest tile grid the candidate search accepts.  Its threshold, labelling
+// and box ranking run in one block: labels spread one tile per sweep, so a
+// component winding through every tile needs up to one sweep per tile, and
+// each root is ranked against every tile; 2^17 tiles (362 x 362, e.g.
+// 10240 px in tiles of 32) bound that worst case to seconds.
+constexpr long long kMaxCandTiles = 1LL << 17;
 constexpr double kArcsec = 3.14159265358979323846 / 648000.0;
 
 

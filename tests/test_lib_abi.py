@@ -74,6 +74,13 @@ def test_host_validation_without_gpu(libtoi):
     assert L.toi_stream_input_free(None, 0, 0, C.byref(got)) == libtoi.TOI_ERR_ARG
     assert L.toi_stream_close(None) == libtoi.TOI_ERR_ARG
     assert L.tlisi_candidates(None, 1, 1, 1, 1, 0, None, None, None, None, 0, None) == libtoi.TOI_ERR_ARG
+    # the candidate search's single-block labelling takes at most 2^17 tiles; refused on the
+    # host (the cube address is never touched)
+    thr, nb = C.c_double(), C.c_int32()
+    for fn in (L.tlisi_candidates, L.tlisi_candidates_noalloc):
+        assert fn(C.c_void_p(256), 10, 363, 362, 32, 0, None, C.byref(thr), None, C.byref(nb), 0,
+                  None) == libtoi.TOI_ERR_ARG
+        assert b"131072" in L.toi_last_error(None)
     assert L.toi_status_string(libtoi.TOI_ERR_RANGE)
 
 
