@@ -113,9 +113,42 @@ __device__ __forceinline__ void dft5(float2* v) {
   v[3] = csub(a2, cmuli(b2));
 }
 
+// radix 16 as 4 x 4: j = 4 j1 + j2, k = k1 + 4 k2; 4-point DFTs over j1, the
+// twiddles e^{+2 pi i j2 k1 / 16}, 4-point DFTs over j2
+__device__ __forceinline__ void dft16(float2* v) {
+  const float c1 = 0.92387953251128676f, s1 = 0.38268343236508977f;   // cos, sin pi/8
+  const float r = 0.70710678118654752f;
+  float2 a[4][4];
+#pragma unroll
+  for (int j2 = 0; j2 < 4; ++j2) {
+    float2 t[4] = {v[j2], v[4 + j2], v[8 + j2], v[12 + j2]};
+    dft4(t);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) a[j2][k1] = t[k1];
+  }
+  // w^m, w = e^{+2 pi i / 16}, for m = j2 k1
+  a[1][1] = cmul(a[1][1], make_float2(c1, s1));                          // m = 1
+  a[1][2] = make_float2(r * (a[1][2].x - a[1][2].y), r * (a[1][2].x + a[1][2].y));   // m = 2
+  a[1][3] = cmul(a[1][3], make_float2(s1, c1));                          // m = 3
+  a[2][1] = make_float2(r * (a[2][1].x - a[2][1].y), r * (a[2][1].x + a[2][1].y));   // m = 2
+  a[2][2] = cmuli(a[2][2]);                                              // m = 4
+  a[2][3] = make_float2(-r * (a[2][3].x + a[2][3].y), r * (a[2][3].x - a[2][3].y));  // m = 6
+  a[3][1] = cmul(a[3][1], make_float2(s1, c1));                          // m = 3
+  a[3][2] = make_float2(-r * (a[3][2].x + a[3][2].y), r * (a[3][2].x - a[3][2].y));  // m = 6
+  a[3][3] = cmul(a[3][3], make_float2(-c1, -s1));                        // m = 9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    dft4(t);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+  }
+}
+
 template <int R>
 __device__ __forceinline__ void dftR(float2* v) {
-  if constexpr (R == 8) dft8(v);
+  if constexpr (R == 16) dft16(v);
+  else if constexpr (R == 8) dft8(v);
   else if constexpr (R == 5) dft5(v);
   else if constexpr (R == 4) dft4(v);
   else if constexpr (R == 3) dft3(v);
@@ -125,7 +158,17 @@ __device__ __forceinline__ void dftR(float2* v) {
 // twiddle powers w^r, r = 1..R-1, with w = e^{+2 pi i step / G}
 template <int R>
 __device__ __forceinline__ void twiddles(const float2* __restrict__ tw, int step, float2* w) {
-  if constexpr (R == 8) {
+  if constexpr (R == 16) {
+    const float2 w1 = __ldg(tw + step), w2 = __ldg(tw + 2 * step), w4 = __ldg(tw + 4 * step),
+                 w8 = __ldg(tw + 8 * step);
+    w[1] = w1; w[2] = w2; w[4] = w4; w[8] = w8;
+    w[3] = cmul(w2, w1);
+    w[5] = cmul(w4, w1);
+    w[6] = cmul(w4, w2);
+    w[7] = cmul(w4, w[3]);
+#pragma unroll
+    for (int r = 1; r < 8; ++r) w[8 + r] = cmul(w8, w[r]);
+  } else if constexpr (R == 8) {
     const float2 w1 = __ldg(tw + step), w2 = __ldg(tw + 2 * step), w4 = __ldg(tw + 4 * step);
     w[1] = w1; w[2] = w2; w[4] = w4;
     w[3] = cmul(w2, w1);
@@ -205,10 +248,20 @@ struct Factors {
 template <int G, int NSEQ, int NT>
 __device__ __forceinline__ void fft_smem(float2* x, const float2* __restrict__ tw) {
   constexpr int F = Factors<G>::F, LOG = Factors<G>::LOG;
-  constexpr int N8 = LOG / 3;
-  constexpr int REM = LOG - 3 * N8;
+  // radix-16 passes while four bits remain, then at most one radix-8 pass:
+  // fewer passes through shared memory than all-radix-8 (3 instead of 4 at
+  // 4096 points)
+  constexpr int N16 = LOG / 4;
+  constexpr int N8 = (LOG - 4 * N16) / 3;
+  constexpr int REM = LOG - 4 * N16 - 3 * N8;
+  constexpr int BPT16 = (NSEQ * (G / 16) + NT - 1) / NT;
   constexpr int BPT8 = (NSEQ * (G / 8) + NT - 1) / NT;
   int Ns = 1;
+#pragma unroll
+  for (int p = 0; p < N16; ++p) {
+    stockham_pass<G, 16, BPT16>(x, NSEQ, Ns, tw);
+    Ns *= 16;
+  }
 #pragma unroll
   for (int p = 0; p < N8; ++p) {
     stockham_pass<G, 8, BPT8>(x, NSEQ, Ns, tw);
@@ -236,7 +289,8 @@ __device__ __forceinline__ int row_limit(const double* snap, int G) {
 
 template <int G>
 struct RowCfg {
-  static constexpr int NT = (G / 8 < 64) ? 64 : (G / 8 > 512 ? 512 : G / 8);
+  // one thread per radix-16 butterfly of a row (64 to 512 threads)
+  static constexpr int NT = (G / 16 < 64) ? 64 : (G / 16 > 512 ? 512 : G / 16);
 };
 
 template <int G>
@@ -247,12 +301,20 @@ __device__ __forceinline__ void fft_rows_body(float2* __restrict__ H, int N,
   extern __shared__ float2 x[];
   if (row > row_limit(snap, G)) return;
   float2* src = H + (size_t)row * G;
+  // columns of this row inside the disc that holds every non-zero cell (in
+  // float32: radius and row are below 2^14, and the cell of margin on each
+  // side covers its rounding; float64 is slow on this GPU)
+  const float rad = (float)snap[SNAP_RADMAX];
+  const float h2 = rad * rad - (float)row * (float)row;
+  const float hw = h2 > 0.f ? sqrtf(h2) : 0.f;
+  const int n_lo = max(0, (int)floorf(0.5f * G - hw) - 1);
+  const int n_hi = min(G - 1, (int)ceilf(0.5f * G + hw) + 1);
   constexpr int PER = (G + RowCfg<G>::NT - 1) / RowCfg<G>::NT;
   float2 v[PER];
 #pragma unroll
   for (int u = 0; u < PER; ++u) {   // all loads first, then the stores
     const int n = threadIdx.x + u * RowCfg<G>::NT;
-    v[u] = n < G ? src[n] : make_float2(0.f, 0.f);
+    v[u] = (n >= n_lo && n <= n_hi) ? src[n] : make_float2(0.f, 0.f);
   }
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
@@ -268,8 +330,9 @@ __device__ __forceinline__ void fft_rows_body(float2* __restrict__ H, int N,
     if (jp & 1) { v.x = -v.x; v.y = -v.y; }
     dst[j] = v;
   }
-  // leave the grid slot cleared for the next gridding
-  for (int n = threadIdx.x; n < G; n += blockDim.x) src[n] = make_float2(0.f, 0.f);
+  // leave the grid slot cleared for the next gridding (outside the disc it is
+  // zero already)
+  for (int n = n_lo + (int)threadIdx.x; n <= n_hi; n += blockDim.x) src[n] = make_float2(0.f, 0.f);
 }
 
 template <int G>

@@ -470,6 +470,7 @@ __device__ __forceinline__ void prep_finalize_body(const double* __restrict__ bp
   snap[SNAP_SUMW] = empty ? 0.0 : v[10];
   snap[SNAP_NVIS] = empty ? 0.0 : N;
   snap[14] = 0.0;   // largest stored grid row touched (written by the coefficient kernel)
+  snap[SNAP_RADMAX] = 0.0;   // largest footprint radius (likewise)
   // re-projection constants, once per snapshot instead of per block
   snap[SNAP_REPRO] = (double)(float)(-snap[SNAP_XI] / beta_rad);
   snap[SNAP_REPRO + 1] = (double)(float)(snap[SNAP_ETA] / beta_rad);
@@ -513,6 +514,12 @@ __device__ __forceinline__ void prep_coef_body(const double* __restrict__ uvw, i
   const double rowmax = fmin(fabs(cf.a2) * kmax + 0.5 * W + 1.0, 0.5 * G);
   atomicMax(reinterpret_cast<unsigned long long*>(snap + 14),
             (unsigned long long)__double_as_longlong(rowmax));
+  // and the largest distance from the grid centre of any cell it reaches:
+  // a sample lies at radius |a| k <= |a| kmax, its taps within W/2 sqrt(2) <
+  // W of it (plus a cell of margin for rounding)
+  const double radmax = sqrt(cf.a1 * cf.a1 + cf.a2 * cf.a2) * kmax + (double)W + 1.0;
+  atomicMax(reinterpret_cast<unsigned long long*>(snap + SNAP_RADMAX),
+            (unsigned long long)__double_as_longlong(radmax));
 }
 
 __global__ void prep_coef_kernel(const double* __restrict__ uvw, int nbl, int nch,

@@ -39,6 +39,10 @@ enum SnapField {
   SNAP_K0 = 20,
   SNAP_DK = 21,
   SNAP_KDEV = 22,
+  // largest distance (cells) of any grid cell a footprint reaches from the
+  // grid centre (G/2, 0): the FFT row pass reads and clears only the columns
+  // of each row inside this disc (every other cell of the grid is zero)
+  SNAP_RADMAX = 23,
   SNAP_ALLOC = 24
 };
 
