@@ -13,9 +13,10 @@ namespace toi {
 cudaError_t fft_configure(int G);
 bool fft_length_supported(int G);
 size_t candidates_scratch_bytes(int S, int nt);
+size_t candidates_centre_bytes(int S, int nt);
 cudaError_t candidates_run(const float* cube, int S, int nty, int ntx, int T, int mode,
                            cudaStream_t st, void* scratch, double* scores_out, int max_boxes,
-                           int* boxes_dev, double** thr_dev, int** nbox_dev);
+                           int* boxes_dev, double** thr_dev, int** nbox_dev, double* xbuf);
 
 // psi_hat(f) = integral over |x| <= W/2 of psi(x) cos(2 pi x f) dx for the
 // exponential of semicircle psi(x) = exp(beta (sqrt(1 - (2x/W)^2) - 1)).
@@ -753,15 +754,20 @@ toi_status tlisi_candidates(const float* cube, int32_t S, int32_t nty, int32_t n
   if (max_boxes < 0 || (max_boxes > 0 && !boxes)) return fail(nullptr, TOI_ERR_ARG, "boxes must hold max_boxes entries");
   cudaStream_t st = (cudaStream_t)stream;
   const int nt = nty * ntx;
-  const size_t bytes = toi::candidates_scratch_bytes(S, nt) + sizeof(int) * 4 * (size_t)(max_boxes + 1);
+  // work, boxes, and (periodic) the centred series, each 256-byte aligned
+  const size_t work = toi::candidates_scratch_bytes(S, nt);
+  const size_t box_bytes = (sizeof(int) * 4 * (size_t)(max_boxes + 1) + 255) & ~(size_t)255;
+  const size_t xoff = ((work + 255) & ~(size_t)255) + box_bytes;
+  const size_t bytes = xoff + (mode == TOI_CAND_PERIODIC ? toi::candidates_centre_bytes(S, nt) : 0);
   void* scratch = nullptr;
   cudaError_t e = cudaMallocAsync(&scratch, bytes, st);
   if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(nullptr, e, "tlisi_candidates/scratch"); }
-  int* boxes_dev = (int*)((char*)scratch + toi::candidates_scratch_bytes(S, nt));
+  int* boxes_dev = (int*)((char*)scratch + ((work + 255) & ~(size_t)255));
+  double* xbuf = mode == TOI_CAND_PERIODIC ? (double*)((char*)scratch + xoff) : nullptr;
   double* thr_dev = nullptr;
   int* nbox_dev = nullptr;
   e = toi::candidates_run(cube, S, nty, ntx, tile, mode, st, scratch, scores, max_boxes, boxes_dev,
-                          &thr_dev, &nbox_dev);
+                          &thr_dev, &nbox_dev, xbuf);
   int nb = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(threshold, thr_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nb, nbox_dev, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -70,25 +70,47 @@ __global__ void mean_kernel(const float* __restrict__ cube, int S, int nt, int m
   }
 }
 
-// One thread per (f, tile): the power P_f of the mean-removed series.
-__global__ void power_kernel(const float* __restrict__ cube, int S, int nt, int F,
-                             const double* __restrict__ mu, const double* __restrict__ ct,
-                             const double* __restrict__ st, double* __restrict__ P) {
+// The mean-removed series x_t = tLISI_t - mean of every tile, once.
+__global__ void centre_kernel(const float* __restrict__ cube, int S, int nt,
+                              const double* __restrict__ mu, double* __restrict__ x) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (long long)F * nt) return;
+  if (id >= (long long)S * nt) return;
   const int k = (int)(id % nt);
-  const int f = (int)(id / nt) + 1;
+  x[id] = __dsub_rn((double)cube[id], mu[k]);
+}
+
+// One thread per (frequency pair, tile): the powers P_f and P_{f+H} (H =
+// ceil(F/2)) of the mean-removed series, so that each x_t feeds four
+// independent sums.  x is the centred series from centre_kernel, or NULL to
+// form x_t here (bit-identical: the same subtraction).
+__global__ void power_kernel(const float* __restrict__ cube, const double* __restrict__ xs,
+                             int S, int nt, int F, const double* __restrict__ mu,
+                             const double* __restrict__ ct, const double* __restrict__ st,
+                             double* __restrict__ P) {
+  const int H = (F + 1) / 2;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)H * nt) return;
+  const int k = (int)(id % nt);
+  const int f1 = (int)(id / nt) + 1, f2 = f1 + H;
+  const bool two = f2 <= F;
   const double m = mu[k];
-  double A = 0.0, B = 0.0;
-  int idx = 0;   // (f * t) mod S, advanced incrementally
+  double A1 = 0.0, B1 = 0.0, A2 = 0.0, B2 = 0.0;
+  int i1 = 0, i2 = 0;   // (f * t) mod S, advanced incrementally
   for (int t = 0; t < S; ++t) {
-    const double x = __dsub_rn((double)cube[(size_t)t * nt + k], m);
-    A = __dadd_rn(A, __dmul_rn(x, ct[idx]));
-    B = __dadd_rn(B, __dmul_rn(x, st[idx]));
-    idx += f;
-    if (idx >= S) idx -= S;
+    const double x = xs ? xs[(size_t)t * nt + k] : __dsub_rn((double)cube[(size_t)t * nt + k], m);
+    A1 = __dadd_rn(A1, __dmul_rn(x, ct[i1]));
+    B1 = __dadd_rn(B1, __dmul_rn(x, st[i1]));
+    if (two) {
+      A2 = __dadd_rn(A2, __dmul_rn(x, ct[i2]));
+      B2 = __dadd_rn(B2, __dmul_rn(x, st[i2]));
+    }
+    i1 += f1;
+    if (i1 >= S) i1 -= S;
+    i2 += two ? f2 : 0;
+    if (i2 >= S) i2 -= S;
   }
-  P[(size_t)f * nt + k] = __dadd_rn(__dmul_rn(A, A), __dmul_rn(B, B));
+  P[(size_t)f1 * nt + k] = __dadd_rn(__dmul_rn(A1, A1), __dmul_rn(B1, B1));
+  if (two) P[(size_t)f2 * nt + k] = __dadd_rn(__dmul_rn(A2, A2), __dmul_rn(B2, B2));
 }
 
 __global__ void harmonic_kernel(const double* __restrict__ P, int nt, int F,
@@ -247,9 +269,13 @@ size_t candidates_scratch_bytes(int S, int nt) {
   return b + 256;
 }
 
+// Bytes of the optional centred-series buffer (periodic mode): with it the
+// series is centred once instead of once per frequency.
+size_t candidates_centre_bytes(int S, int nt) { return sizeof(double) * (size_t)S * nt; }
+
 cudaError_t candidates_run(const float* cube, int S, int nty, int ntx, int T, int mode,
                            cudaStream_t st, void* scratch, double* scores_out, int max_boxes,
-                           int* boxes_dev, double** thr_dev, int** nbox_dev) {
+                           int* boxes_dev, double** thr_dev, int** nbox_dev, double* xbuf) {
   const int nt = nty * ntx;
   const int F = S / 2;
   char* p = reinterpret_cast<char*>(scratch);
@@ -272,8 +298,13 @@ cudaError_t candidates_run(const float* cube, int S, int nty, int ntx, int T, in
   if (mode == TOI_CAND_PERIODIC) {
     if (F > 0) {
       twiddle_kernel<<<(S + 255) / 256, 256, 0, st>>>(S, ct, stw);
-      const long long n = (long long)F * nt;
-      power_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cube, S, nt, F, mean, ct, stw, P);
+      if (xbuf) {
+        const long long nx = (long long)S * nt;
+        centre_kernel<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(cube, S, nt, mean, xbuf);
+      }
+      const long long n = (long long)((F + 1) / 2) * nt;
+      power_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cube, xbuf, S, nt, F, mean, ct,
+                                                                stw, P);
       harmonic_kernel<<<(nt + 255) / 256, 256, 0, st>>>(P, nt, F, score);
     } else {
       cudaMemsetAsync(score, 0, sizeof(double) * nt, st);

@@ -23,7 +23,7 @@ namespace toi {
 size_t candidates_scratch_bytes(int S, int nt);
 cudaError_t candidates_run(const float* cube, int S, int nty, int ntx, int T, int mode,
                            cudaStream_t st, void* scratch, double* scores_out, int max_boxes,
-                           int* boxes_dev, double** thr_dev, int** nbox_dev);
+                           int* boxes_dev, double** thr_dev, int** nbox_dev, double* xbuf);
 void set_planless_error(const std::string& msg);
 }  // namespace toi
 
@@ -75,8 +75,10 @@ extern "C" toi_status tlisi_candidates_noalloc(const float* cube, int32_t S, int
   int* boxes_dev = reinterpret_cast<int*>(reinterpret_cast<char*>(base) + work);
   double* thr_dev = nullptr;
   int* nbox_dev = nullptr;
+  // no room for a centred copy of the series here: the search centres it per
+  // frequency instead (the same bits)
   e = toi::candidates_run(cube, S, nty, ntx, tile, mode, st, base, scores, max_boxes, boxes_dev,
-                          &thr_dev, &nbox_dev);
+                          &thr_dev, &nbox_dev, nullptr);
   int nb = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(threshold, thr_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nb, nbox_dev, sizeof(int), cudaMemcpyDeviceToHost, st);
