@@ -86,11 +86,11 @@ PATH_STAGES = ("prep", "grid", "fft_rows", "fft_cols", "reproject", "tlisi")
 
 # DRAM bytes (read + write) per snapshot of the gridder, from an ncu capture
 # of the profile case (dram__bytes_read.sum + dram__bytes_write.sum): the
-# batched kernel over 16 references to one MeerKAT-shaped snapshot (4988 +
-# 186 MB; each reference streams its visibilities again, L2 being smaller
+# batched kernel over 16 references to one MeerKAT-shaped snapshot (5001.5 +
+# 184.2 MB; each reference streams its visibilities again, L2 being smaller
 # than them).  A launch's traffic is this times the snapshots it grids.  The
 # single-snapshot kernel has not been captured in its current form.
-GRID_DRAM_BYTES_PER_SNAPSHOT = {"batch": 5174.2e6 / 16, "single": None}
+GRID_DRAM_BYTES_PER_SNAPSHOT = {"batch": 5185.7e6 / 16, "single": None}
 
 
 def load_peaks():
@@ -1040,14 +1040,30 @@ if __name__ == "__main__":
 
 
 def mem_available_gb():
+    """Host memory this process may still use: MemAvailable, capped by the
+    cgroup's limit where one is set."""
+    avail = 16.0
     try:
         with open("/proc/meminfo") as f:
             for line in f:
                 if line.startswith("MemAvailable:"):
-                    return int(line.split()[1]) / 1e6
+                    avail = int(line.split()[1]) / 1e6
     except OSError:
         pass
-    return 16.0
+    for lim_path, use_path in (("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory.current"),
+                               ("/sys/fs/cgroup/memory/memory.limit_in_bytes",
+                                "/sys/fs/cgroup/memory/memory.usage_in_bytes")):
+        try:
+            with open(lim_path) as f:
+                lim = f.read().strip()
+            with open(use_path) as f:
+                use = int(f.read().strip())
+            if lim.isdigit():
+                avail = min(avail, (int(lim) - use) / 1e9)
+            break
+        except (OSError, ValueError):
+            continue
+    return avail
 
 
 def cpu_model():
@@ -1087,11 +1103,16 @@ def cpu_baseline(snap_index: int = 7, all_cores: bool = True):
            "host_cores_available": ncores}
     if all_cores:
         n = 16
-        # about 3.5 GB of host memory per oracle process at this shape
-        workers = max(1, min(n, ncores, int(mem_available_gb() // 4.5)))
-        code = POOL_SNIPPET.format(root=ROOT, n=n, workers=workers)
-        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
-                           env=_oracle_env(), timeout=1800)
+        # about 3.5 GB of host memory per oracle process at this shape, more
+        # with the interpreter and torch; halve the pool if a worker dies
+        workers = max(1, min(n, ncores, int(mem_available_gb() // 6.0)))
+        while True:
+            code = POOL_SNIPPET.format(root=ROOT, n=n, workers=workers)
+            r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                               env=_oracle_env(), timeout=1800)
+            if r.returncode == 0 or workers == 1:
+                break
+            workers = max(1, workers // 2)
         if r.returncode == 0:
             wall = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
             out["all_cores"] = {"value": round(n / wall, 4), "unit": "snapshots/s",
