@@ -276,6 +276,7 @@ struct StageBuf {
   unsigned int f[2][kStage][32];
   float wa[2][kStage][32];
   float wb[2][kStage][32];
+  float sc[2][kStage][32];   // FP16 storage: the channel's scale
 };
 
 __device__ __forceinline__ void cp_async(void* sdst, const void* gsrc, int bytes_tag) {
@@ -711,15 +712,16 @@ __device__ __forceinline__ f2x staged_vis(const StageBuf& sb, int sidx, int u, i
   float wb = fb ? 0.f : (weight ? sb.wb[sidx][u][lane] : 1.f);
   if (pa == pb) wb = 0.f;
   float2 va = sb.va[sidx][u][lane], vbv = (pa != pb) ? sb.vb[sidx][u][lane] : make_float2(0.f, 0.f);
+  float sa = wa, sbw = wb;   // weights, times the channel scale for FP16 storage
   if (HALF) {
-    const float sc = chan_scale[ch];
+    const float sc = sb.sc[sidx][u][lane];
     const unsigned int ra = __float_as_uint(va.x), rb = __float_as_uint(vbv.x);
-    const float2 fa2 = __half22float2(*reinterpret_cast<const __half2*>(&ra));
-    const float2 fb2 = __half22float2(*reinterpret_cast<const __half2*>(&rb));
-    va = make_float2(fa2.x * sc, fa2.y * sc);
-    vbv = make_float2(fb2.x * sc, fb2.y * sc);
+    va = __half22float2(*reinterpret_cast<const __half2*>(&ra));
+    vbv = __half22float2(*reinterpret_cast<const __half2*>(&rb));
+    sa *= sc;
+    sbw *= sc;
   }
-  const f2x c = fma2(pk(wb, wb), pk(vbv.x, vbv.y), mul2(pk(wa, wa), pk(va.x, va.y)));
+  const f2x c = fma2(pk(sbw, sbw), pk(vbv.x, vbv.y), mul2(pk(sa, sa), pk(va.x, va.y)));
   return (wa + wb > 0.f) ? c : 0ull;
 }
 
@@ -855,6 +857,7 @@ __device__ __forceinline__ void grid_track2(const BaselineCoef* __restrict__ coe
             cp_async(&sb.wa[sidx][u][lane], weight + o + pa, 4);
             if (pa != pb) cp_async(&sb.wb[sidx][u][lane], weight + o + pb, 4);
           }
+          if (HALF) cp_async(&sb.sc[sidx][u][lane], chan_scale + ch, 4);
         }
       }
     }
