@@ -1106,13 +1106,18 @@ def cpu_baseline(snap_index: int = 7, all_cores: bool = True):
         # about 3.5 GB of host memory per oracle process at this shape, more
         # with the interpreter and torch; halve the pool if a worker dies
         workers = max(1, min(n, ncores, int(mem_available_gb() // 6.0)))
-        while True:
-            code = POOL_SNIPPET.format(root=ROOT, n=n, workers=workers)
-            r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
-                               env=_oracle_env(), timeout=1800)
-            if r.returncode == 0 or workers == 1:
-                break
-            workers = max(1, workers // 2)
+        # the pool's worker function must be importable by the spawned
+        # processes, so the script runs from a file, not from "-c"
+        with tempfile.TemporaryDirectory() as tmp:
+            script = os.path.join(tmp, "oracle_pool_timing.py")
+            while True:
+                with open(script, "w") as f:
+                    f.write(POOL_SNIPPET.format(root=ROOT, n=n, workers=workers))
+                r = subprocess.run([sys.executable, script], capture_output=True, text=True,
+                                   env=_oracle_env(), timeout=1800)
+                if r.returncode == 0 or workers == 1:
+                    break
+                workers = max(1, workers // 2)
         if r.returncode == 0:
             wall = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
             out["all_cores"] = {"value": round(n / wall, 4), "unit": "snapshots/s",
