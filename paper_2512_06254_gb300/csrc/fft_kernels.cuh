@@ -26,6 +26,9 @@
 // Shared memory is padded by one slot per sixteen: a half warp's run of 16
 // consecutive complex values then fills the 32 banks exactly, which keeps
 // every pass's loads and all but one radix-8 span's stores conflict-free.
+// The image passes read their first pass's operands straight from global
+// memory and write their last pass's outputs straight to it (fft_io), so
+// only the passes in between go through shared memory.
 #pragma once
 #include "toi_internal.cuh"
 
@@ -282,6 +285,100 @@ __device__ __forceinline__ void fft_smem(float2* x, const float2* __restrict__ t
   }
 }
 
+// The same transform with its first pass reading the input straight from
+// global memory, load(seq, n) = x[n] of sequence seq, and its last pass
+// handing the outputs to store(seq, m, X[m]) instead of shared memory: two
+// of the shared-memory round trips (the staging of the input and the read of
+// the outputs) are saved.  A first pass has span Ns = 1 (no twiddles); a last
+// pass has Ns = G / R, so its butterfly j holds the outputs m = j + r Ns.
+//
+// With two sequences, neighbouring threads take the same butterfly of the
+// two (seq = id mod 2): their global loads and stores then touch neighbouring
+// 16-byte halves of one 32-byte sector.  The sequences lie SSTRIDE apart in
+// shared memory, SSTRIDE = 8 (mod 16) slots, so that the two halves of a
+// half-warp fall in opposite halves of the banks.
+template <int G, int R, int BPT, int NSEQ, int SSTRIDE, bool FROM, bool TO, class Load, class Store>
+__device__ __forceinline__ void stockham_io(float2* x, int Ns, const float2* __restrict__ tw,
+                                            Load& load, Store& store) {
+  constexpr int NB = G / R;
+  constexpr int nseq = NSEQ;
+  constexpr int LEN = SSTRIDE;
+  float2 v[BPT][R];
+  int jj[BPT], ss[BPT];
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    const int id = threadIdx.x + b * blockDim.x;
+    const int seq = id % NSEQ, j = id / NSEQ;
+    jj[b] = j;
+    ss[b] = seq;
+    if (j < NB) {
+      const int k = j & (Ns - 1);
+      if constexpr (FROM) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b][r] = load(seq, j + r * NB);
+      } else {
+        const float2* xs = x + (size_t)seq * LEN;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b][r] = xs[pad(j + r * NB)];
+      }
+      if (k > 0) {
+        float2 w[R];
+        twiddles<R>(tw, (G / (Ns * R)) * k, w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
+      }
+      dftR<R>(v[b]);
+    }
+  }
+  // in place: every read of this pass before any write (a first pass reads
+  // no shared memory, a last pass writes none)
+  if constexpr (!FROM && !TO) __syncthreads();
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    if (jj[b] < NB) {
+      const int j = jj[b];
+      const int k = j & (Ns - 1);
+      const int base = (j - k) * R + k;
+      if constexpr (TO) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) store(ss[b], base + r * Ns, v[b][r]);
+      } else {
+        float2* xs = x + (size_t)ss[b] * LEN;
+#pragma unroll
+        for (int r = 0; r < R; ++r) xs[pad(base + r * Ns)] = v[b][r];
+      }
+    }
+  }
+  if constexpr (!TO) __syncthreads();
+}
+
+// Pass P of fft_io and the ones after it (the radices of fft_smem, in order).
+template <int G, int NSEQ, int SSTRIDE, int NT, int P, class Load, class Store>
+__device__ __forceinline__ void fft_io_from(float2* x, int Ns, const float2* __restrict__ tw,
+                                            Load& load, Store& store) {
+  constexpr int F = Factors<G>::F, LOG = Factors<G>::LOG;
+  constexpr int N16 = LOG / 4;
+  constexpr int N8 = (LOG - 4 * N16) / 3;
+  constexpr int REM = LOG - 4 * N16 - 3 * N8;
+  constexpr int NREM = REM > 0 ? 1 : 0;
+  constexpr int NP = N16 + N8 + NREM + (F > 1 ? 1 : 0);
+  static_assert(NP >= 2, "fft_io needs a first and a last pass");
+  if constexpr (P < NP) {
+    constexpr int R = P < N16 ? 16
+                    : (P < N16 + N8 ? 8 : (P < N16 + N8 + NREM ? (REM == 2 ? 4 : 2) : F));
+    constexpr int BPT = (NSEQ * (G / R) + NT - 1) / NT;
+    stockham_io<G, R, BPT, NSEQ, SSTRIDE, P == 0, P == NP - 1>(x, Ns, tw, load, store);
+    fft_io_from<G, NSEQ, SSTRIDE, NT, P + 1>(x, Ns * R, tw, load, store);
+  }
+}
+
+template <int G, int NSEQ, int SSTRIDE, int NT, class Load, class Store>
+__device__ __forceinline__ void fft_io(float2* x, const float2* __restrict__ tw, Load& load,
+                                       Store& store) {
+  static_assert(NSEQ == 1 || SSTRIDE % 16 == 8, "two sequences need a stride of 8 mod 16 slots");
+  fft_io_from<G, NSEQ, SSTRIDE, NT, 0>(x, 1, tw, load, store);
+}
+
 __device__ __forceinline__ int row_limit(const double* snap, int G) {
   const int r = (int)ceil(snap[SNAP_ROWMAX]);
   return r < G / 2 ? r : G / 2 - 1;
@@ -291,6 +388,10 @@ template <int G>
 struct RowCfg {
   // one thread per radix-16 butterfly of a row (64 to 512 threads)
   static constexpr int NT = (G / 16 < 64) ? 64 : (G / 16 > 512 ? 512 : G / 16);
+  // blocks per SM the registers are sized for: 1024 threads (64 registers a
+  // thread) while two rows fit in shared memory, so that loads of several
+  // rows are in flight; beyond that the shared memory allows one block
+  static constexpr int MINB = G <= 8192 ? 1024 / NT : 1;
 };
 
 template <int G>
@@ -309,41 +410,34 @@ __device__ __forceinline__ void fft_rows_body(float2* __restrict__ H, int N,
   const float hw = h2 > 0.f ? sqrtf(h2) : 0.f;
   const int n_lo = max(0, (int)floorf(0.5f * G - hw) - 1);
   const int n_hi = min(G - 1, (int)ceilf(0.5f * G + hw) + 1);
-  constexpr int PER = (G + RowCfg<G>::NT - 1) / RowCfg<G>::NT;
-  float2 v[PER];
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {   // all loads first, then the stores
-    const int n = threadIdx.x + u * RowCfg<G>::NT;
-    v[u] = (n >= n_lo && n <= n_hi) ? src[n] : make_float2(0.f, 0.f);
-  }
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const int n = threadIdx.x + u * RowCfg<G>::NT;
-    if (n < G) x[pad(n)] = v[u];
-  }
-  __syncthreads();
-  fft_smem<G, 1, RowCfg<G>::NT>(x, tw);
+  // first pass from the grid row (zero outside the disc), last pass straight
+  // to the N central outputs: (-1)^j1' Z[j1' mod G]
+  auto load = [&](int, int n) -> float2 {
+    return (n >= n_lo && n <= n_hi) ? src[n] : make_float2(0.f, 0.f);
+  };
   float2* dst = T + (size_t)row * N;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const int jp = j - N / 2;
-    float2 v = x[pad(jp < 0 ? jp + G : jp)];
-    if (jp & 1) { v.x = -v.x; v.y = -v.y; }
-    dst[j] = v;
-  }
+  auto store = [&](int, int m, float2 v) {
+    const int jp = m < G / 2 ? m : m - G;
+    if (jp >= -N / 2 && jp < N / 2) {
+      if (jp & 1) { v.x = -v.x; v.y = -v.y; }
+      dst[jp + N / 2] = v;
+    }
+  };
+  fft_io<G, 1, G + G / 16, RowCfg<G>::NT>(x, tw, load, store);
   // leave the grid slot cleared for the next gridding (outside the disc it is
   // zero already)
   for (int n = n_lo + (int)threadIdx.x; n <= n_hi; n += blockDim.x) src[n] = make_float2(0.f, 0.f);
 }
 
 template <int G>
-__global__ void __launch_bounds__(RowCfg<G>::NT)
+__global__ void __launch_bounds__(RowCfg<G>::NT, RowCfg<G>::MINB)
 fft_rows_kernel(float2* __restrict__ H, int N, const float2* __restrict__ tw,
                 const double* __restrict__ snap, float2* __restrict__ T) {
   fft_rows_body<G>(H, N, tw, snap, T, blockIdx.x);
 }
 
 template <int G>
-__global__ void __launch_bounds__(RowCfg<G>::NT)
+__global__ void __launch_bounds__(RowCfg<G>::NT, RowCfg<G>::MINB)
 fft_rows_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
                const float2* __restrict__ tw) {
   if ((int)blockIdx.y >= hdr->n) return;
@@ -359,6 +453,12 @@ struct ColCfg {
   static constexpr int CW = 2 * NSEQ;     // columns per block
   static constexpr int NT = 512;
   static constexpr int LEN = G + G / 16;
+  // distance of the two sequences in shared memory (8 mod 16 slots)
+  static constexpr int SSTRIDE = NSEQ == 2 ? LEN + ((24 - LEN % 16) % 16) : LEN;
+  static constexpr int SMEM = NSEQ * SSTRIDE * (int)sizeof(float2);
+  // two blocks per SM (64 registers a thread) up to G = 4096; above that
+  // the butterflies of a thread need more registers than 64 without spills
+  static constexpr int MINB = G <= 4096 ? 2 : 1;
 };
 
 template <int G>
@@ -367,68 +467,47 @@ __device__ __forceinline__ void fft_cols_body(const float2* __restrict__ T, int 
                                               const float* __restrict__ corr,
                                               const double* __restrict__ snap,
                                               float* __restrict__ out, int blk) {
-  constexpr int CW = ColCfg<G>::CW, LEN = ColCfg<G>::LEN, NSEQ = ColCfg<G>::NSEQ;
+  constexpr int CW = ColCfg<G>::CW, NSEQ = ColCfg<G>::NSEQ;
   extern __shared__ float2 x[];
   const int col0 = blk * CW;
   constexpr int half = G / 2;
   const int rmax = row_limit(snap, G);
-  // all of a thread's loads first (one memory latency per block), then the
-  // shared-memory stores
-  constexpr int NT = ColCfg<G>::NT, ITEMS = half * NSEQ;
-  constexpr int PER = (ITEMS + NT - 1) / NT;
-  float4 ld[PER];
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const int e = threadIdx.x + u * NT;
-    const int r = e / NSEQ, pr = e - r * NSEQ;   // row, column pair
-    ld[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (e < ITEMS && r <= rmax)
-      ld[u] = *reinterpret_cast<const float4*>(T + (size_t)r * N + col0 + 2 * pr);
-  }
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const int e = threadIdx.x + u * NT;
-    if (e >= ITEMS) break;
-    const int r = e / NSEQ, pr = e - r * NSEQ;
-    float2* xs = x + (size_t)pr * LEN;
-    const float2 a = make_float2(ld[u].x, ld[u].y), b = make_float2(ld[u].z, ld[u].w);
-    // Z[r] = U_a[r] + i U_b[r];  Z[-r] = conj(U_a[r]) + i conj(U_b[r])
-    xs[pad(r)] = make_float2(a.x - b.y, a.y + b.x);
-    if (r > 0) xs[pad(G - r)] = make_float2(a.x + b.y, b.x - a.y);
-    else xs[pad(half)] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  fft_smem<G, NSEQ, ColCfg<G>::NT>(x, tw);
+  // Sequence s transforms columns a = col0 + 2s, b = a + 1 of the row pass as
+  // Z = U_a + i U_b over the full length G, rebuilt from the stored rows:
+  //   Z[r] = U_a[r] + i U_b[r],  Z[G - r] = conj(U_a[r]) + i conj(U_b[r]),
+  // rows beyond the last non-zero one and Z[G/2] zero.
+  auto load = [&](int sq, int n) -> float2 {
+    const int r = n < half ? n : G - n;
+    if (n == half || r > rmax) return make_float2(0.f, 0.f);
+    const float4 t = __ldg(reinterpret_cast<const float4*>(T + (size_t)r * N + col0 + 2 * sq));
+    return n < half ? make_float2(t.x - t.w, t.y + t.z) : make_float2(t.x + t.w, t.z - t.y);
+  };
   const double omega = snap[SNAP_OMEGA], sumw = snap[SNAP_SUMW];
   const float norm = sumw > 0.0 ? (float)(0.5 / (omega * sumw)) : 0.f;
-  if constexpr (NSEQ == 2) {
-    const float ca = corr[col0], cb = corr[col0 + 1], cc = corr[col0 + 2], cd = corr[col0 + 3];
-    for (int j2 = threadIdx.x; j2 < N; j2 += blockDim.x) {
-      const int jp = j2 - N / 2;
-      const int m = pad(jp < 0 ? jp + G : jp);
-      const float2 z0 = x[m], z1 = x[LEN + m];
-      const float s = norm * corr[j2];
-      float4 o;
-      o.x = z0.x * (s * ca);
-      o.y = z0.y * (s * cb);
-      o.z = z1.x * (s * cc);
-      o.w = z1.y * (s * cd);
-      *reinterpret_cast<float4*>(out + (size_t)j2 * N + col0) = o;
-    }
-  } else {
-    const float ca = corr[col0], cb = corr[col0 + 1];
-    for (int j2 = threadIdx.x; j2 < N; j2 += blockDim.x) {
-      const int jp = j2 - N / 2;
-      const float2 z0 = x[pad(jp < 0 ? jp + G : jp)];
-      const float s = norm * corr[j2];
-      *reinterpret_cast<float2*>(out + (size_t)j2 * N + col0) =
-          make_float2(z0.x * (s * ca), z0.y * (s * cb));
-    }
+  float ca[NSEQ], cb[NSEQ];
+#pragma unroll
+  for (int q = 0; q < NSEQ; ++q) {
+    ca[q] = corr[col0 + 2 * q];
+    cb[q] = corr[col0 + 2 * q + 1];
   }
+  // Re -> column a, Im -> column b of output row j2' = m (mod G), times the
+  // grid correction of both axes and 1/2 1/(omega sum w)
+  auto store = [&](int sq, int m, float2 z) {
+    const int jp = m < half ? m : m - G;
+    if (jp >= -N / 2 && jp < N / 2) {
+      const int j2 = jp + N / 2;
+      const float sc = norm * corr[j2];
+      float cq_a = ca[0], cq_b = cb[0];
+      if (NSEQ == 2 && sq == 1) { cq_a = ca[NSEQ - 1]; cq_b = cb[NSEQ - 1]; }
+      *reinterpret_cast<float2*>(out + (size_t)j2 * N + col0 + 2 * sq) =
+          make_float2(z.x * (sc * cq_a), z.y * (sc * cq_b));
+    }
+  };
+  fft_io<G, NSEQ, ColCfg<G>::SSTRIDE, ColCfg<G>::NT>(x, tw, load, store);
 }
 
 template <int G>
-__global__ void __launch_bounds__(ColCfg<G>::NT)
+__global__ void __launch_bounds__(ColCfg<G>::NT, ColCfg<G>::MINB)
 fft_cols_kernel(const float2* __restrict__ T, int N, const float2* __restrict__ tw,
                 const float* __restrict__ corr, const double* __restrict__ snap,
                 float* __restrict__ out) {
@@ -436,7 +515,7 @@ fft_cols_kernel(const float2* __restrict__ T, int N, const float2* __restrict__ 
 }
 
 template <int G>
-__global__ void __launch_bounds__(ColCfg<G>::NT)
+__global__ void __launch_bounds__(ColCfg<G>::NT, ColCfg<G>::MINB)
 fft_cols_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr, int N,
                const float2* __restrict__ tw, const float* __restrict__ corr) {
   if ((int)blockIdx.y >= hdr->n) return;
@@ -516,7 +595,7 @@ fft_adj_rows_kernel(const float2* __restrict__ Y, int N, const float2* __restric
 template <int G>
 cudaError_t configure_g() {
   const int row_smem = (G + G / 16) * (int)sizeof(float2);
-  const int col_smem = ColCfg<G>::NSEQ * ColCfg<G>::LEN * (int)sizeof(float2);
+  const int col_smem = ColCfg<G>::SMEM;   // also covers the adjoint's NSEQ * LEN
   cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        row_smem);
   if (e == cudaSuccess)
@@ -543,7 +622,7 @@ void launch_batch_g(toi_plan_s* p) {
       p->bentry_dev, p->bheader_dev, N, p->twiddle);
   prof_end(p, tok);
   tok = prof_begin(p, PROF_FFT_COLS, 1);
-  fft_cols_batch<G><<<dim3(N / CW, B), ColCfg<G>::NT, ColCfg<G>::NSEQ * ColCfg<G>::LEN * sizeof(float2),
+  fft_cols_batch<G><<<dim3(N / CW, B), ColCfg<G>::NT, ColCfg<G>::SMEM,
                       p->stream>>>(p->bentry_dev, p->bheader_dev, N, p->twiddle, p->corr);
   prof_end(p, tok);
 }
@@ -567,7 +646,7 @@ void launch_g(toi_plan_s* p, Slot& s, float* out) {
   prof_end(p, tok);
   tok = prof_begin(p, PROF_FFT_COLS, 1);
   constexpr int CW = ColCfg<G>::CW;
-  fft_cols_kernel<G><<<N / CW, ColCfg<G>::NT, ColCfg<G>::NSEQ * ColCfg<G>::LEN * sizeof(float2), p->stream>>>(
+  fft_cols_kernel<G><<<N / CW, ColCfg<G>::NT, ColCfg<G>::SMEM, p->stream>>>(
       p->fft_tmp, N, p->twiddle, p->corr, s.snap, out);
   prof_end(p, tok);
 }
