@@ -64,7 +64,7 @@ def alg_bytes(nbl=N_BL, nch=N_CH, npol=N_POL, N=N_IMG, T=32):
 ALG_BYTES = alg_bytes()
 
 
-def survey_bytes(nbl=N_BL, nch=N_CH, npol=N_POL, N=N_IMG, vis_bytes=8):
+def scope_table_bytes(nbl=N_BL, nch=N_CH, npol=N_POL, N=N_IMG, vis_bytes=8):
     """The scope table's design-minimum byte model per snapshot, the roofline
     denominator: visibilities and flags read (flags twice: plane fit and
     gridding), the full G x G complex grid written once, two FFT passes (the
@@ -418,7 +418,7 @@ def run_ours(args):
         imaged = (last - first) * args.steps
     else:
         imaged = S * args.steps
-    sb = survey_bytes(w.n_bl, w.n_chan, w.n_pol, w.image_size)
+    sb = scope_table_bytes(w.n_bl, w.n_chan, w.n_pol, w.image_size)
     dom_b = sb.get(dom, ab[dom])
     achieved = dom_b * imaged / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
     design = ab[dom] * imaged / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
@@ -783,7 +783,7 @@ def run_fp16(args):
         if plan.sync_status() != toi.TOI_OK:
             raise RuntimeError(plan.last_error())
         n = S * args.steps
-        sb = survey_bytes(w.n_bl, w.n_chan, w.n_pol, w.image_size,
+        sb = scope_table_bytes(w.n_bl, w.n_chan, w.n_pol, w.image_size,
                           vis_bytes=4 if storage == "fp16" else 8)
         g_ms = prof["grid"][0]
         g_gbs = sb["grid"] * n / (g_ms / 1e3) / 1e9
