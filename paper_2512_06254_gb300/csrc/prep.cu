@@ -158,12 +158,19 @@ prep_baselines_body(const uint8_t* __restrict__ flag, const float* __restrict__ 
     if (npol == 4 && flag && !weight && (nch & 3) == 0 &&
         (reinterpret_cast<uintptr_t>(flag) & 15) == 0) {
       // Unit weights (the common case): per channel only integer work on
-      // the flag word.  The two parallel-hand bytes (pols 0 and 3) are
-      // reduced to one "nonzero" bit each; their population count is the
-      // number of flagged hands, and a channel with both set is deselected.
+      // the flag words, four channels at a time.  The two parallel-hand
+      // bytes (pols 0 and 3) of two channels are gathered into one word
+      // (byte permute), each byte's "nonzero" becomes its high bit (adding
+      // 0x7f to the low seven bits carries into bit 7 exactly when they are
+      // not all zero), the population count is the number of flagged hands,
+      // and a channel with both hands set is deselected.  Loads past the end
+      // are zero words: no hand flagged, counted out below.
       const uint4* f16 = reinterpret_cast<const uint4*>(flag + base);
       const int ngrp = nch >> 2;
-      int unflagged = 0;
+      int flagged = 0;
+      auto nonzero_bytes = [](unsigned int v) {
+        return (((v & 0x7f7f7f7fu) + 0x7f7f7f7fu) | v) & 0x80808080u;
+      };
       for (int g0 = lane; g0 < ngrp; g0 += 32 * U) {
         uint4 fv[U];
 #pragma unroll
@@ -174,21 +181,20 @@ prep_baselines_body(const uint8_t* __restrict__ flag, const float* __restrict__ 
         unsigned int dmask = 0u;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const bool live = g0 + 32 * u < ngrp;
-          const unsigned int w4[4] = {fv[u].x, fv[u].y, fv[u].z, fv[u].w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            unsigned int nz = w4[i] | (w4[i] >> 4);
-            nz |= nz >> 2;
-            nz |= nz >> 1;
-            nz &= 0x01000001u;
-            if (live) unflagged += 2 - __popc(nz);
-            if (live && nz == 0x01000001u) dmask |= 1u << (4 * u + i);
-          }
+          // bytes [c0 pol 0, c0 pol 3, c1 pol 0, c1 pol 3], likewise c2, c3
+          const unsigned int ta = nonzero_bytes(__byte_perm(fv[u].x, fv[u].y, 0x7430));
+          const unsigned int tb = nonzero_bytes(__byte_perm(fv[u].z, fv[u].w, 0x7430));
+          flagged += __popc(ta) + __popc(tb);
+          const unsigned int da = ta & (ta >> 8), db = tb & (tb >> 8);   // both hands
+          if ((da | db) & 0x00800080u)
+            dmask |= (((da >> 7) & 1u) | ((da >> 22) & 2u) | ((db >> 5) & 4u) | ((db >> 20) & 8u))
+                     << (4 * u);
         }
         fold(dmask, [&](int bit) { return 4 * (g0 + 32 * (bit >> 2)) + (bit & 3); });
       }
-      cnt = unflagged;
+      // the lane's hands: 8 per group it owns (groups lane, lane + 32, ...)
+      const int mine = lane < ngrp ? 8 * ((ngrp - 1 - lane) / 32 + 1) : 0;
+      cnt = mine - flagged;
     } else if (npol == 4 && flag && (nch & 3) == 0 &&
         (reinterpret_cast<uintptr_t>(flag) & 15) == 0) {
       // 16 bytes = the 4 pols of 4 consecutive channels; 32 KB per warp in flight
@@ -541,7 +547,7 @@ __global__ void prep_channels_batch(const BatchEntry* __restrict__ E,
   prep_channels_body(e.freq, e.nch, e.kch, e.kf, e.kpart, status, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kMomWarps * 32)
+__global__ void __launch_bounds__(kMomWarps * 32, 4)
 prep_baselines_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict__ hdr,
                      int npol) {
   if ((int)blockIdx.y >= hdr->n) return;
