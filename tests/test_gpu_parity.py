@@ -167,6 +167,38 @@ def test_ragged_and_edge_shapes(n_ant, n_chan, N, n_pol, weights):
     plan.close()
 
 
+def test_flag_bytes_any_nonzero_value():
+    """Section 3.5 flags a sample by any nonzero flag byte.  The plane fit's
+    unit-weight path (4 pols, no weights, channels a multiple of 4) counts
+    flagged hands four channels at a time with a per-byte nonzero test; the
+    flag bytes here take the values 0x80, 0xff, 0x7f, 0x02 and 0x01 in every
+    combination of the two parallel hands and of the cross hands (which must
+    not count), so each bit of that test is exercised."""
+    w = _small_workload(12, 64, 256, 4, cell=1.0)
+    sn = synth.make_snapshot(w, 2)
+    rng = np.random.default_rng(7)
+    f = sn["flag"].numpy()
+    vals = np.array([0x80, 0xFF, 0x7F, 0x02, 0x01], dtype=np.uint8)
+    pick = rng.random(f.shape) < 0.3
+    f[:] = np.where(pick, vals[rng.integers(0, len(vals), f.shape)], 0)
+    # a block of channels with both hands flagged (deselected) and one with
+    # only the cross hands flagged (still selected)
+    f[3, 8:16, 0] = 0x80
+    f[3, 8:16, 3] = 0x01
+    f[4, 20:28, 1:3] = 0xFF
+    f[4, 20:28, 0] = 0
+    f[4, 20:28, 3] = 0
+    s = to_np(sn)
+    r = O.image_snapshot(s["uvw"], s["freq"], s["vis"], s["flag"], None, w.image_size,
+                         w.cell_arcsec)
+    plan = plan_for(w)
+    out = gpu_image(plan, to_dev(sn))
+    assert out["status"] == toi.TOI_OK
+    _check_geometry(out["info"], r)
+    assert rel_err(out["image"], r["image"]) < IMG_TOL
+    plan.close()
+
+
 def test_all_flagged_reports_empty():
     w = _small_workload(6, 16, 64, 4)
     sn = synth.make_snapshot(w, 0)
