@@ -407,7 +407,10 @@ def run_ours(args):
     ms = shard.max_over_ranks(ms, device=dev)
     snaps = S * args.steps * (1 if sharded else world)
     value = snaps / (ms / 1e3)
-    launches = sum(v[1] for v in prof.values()) + 5 * args.steps
+    # the plan's profiled stage launches, plus the periodic candidate search's
+    # six kernels (mean, twiddles, centring, periodogram, harmonic sum, labels)
+    # once per step
+    launches = sum(v[1] for v in prof.values()) + 6 * args.steps
 
     # roofline of the dominant stage (CUDA events on the plan's stream)
     peak, peak_kind = load_peaks()
@@ -801,7 +804,8 @@ def run_fp16(args):
                          "path_frac": round(path_gbs / peak, 4)},
             "stages": {k: {"ms_per_launch": round(v[0] / max(v[1], 1), 4), "launches": v[1]}
                        for k, v in prof.items() if v[1]},
-            "gpu_launches": int(sum(v[1] for v in prof.values()) + 5 * args.steps),
+            # the non-periodic search: two kernels (scores, labels) per step
+            "gpu_launches": int(sum(v[1] for v in prof.values()) + 2 * args.steps),
             "clocks": ck}
         plan.close()
         del snaps, cube
