@@ -1226,7 +1226,7 @@ def main():
     ap.add_argument("--engine", default="batch", choices=["single", "batch"],
                     help="single: toi_grid + toi_image + tlisi_update per snapshot; batch: "
                          "toi_batch over --batch snapshots per launch")
-    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--grid-rows", type=int, default=0, choices=[0, 4, 8],
                     help="gridder window rows per lane (0: the library's default)")
     ap.add_argument("--mode", type=int, default=2, choices=[2, 3],

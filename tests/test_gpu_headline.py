@@ -1,7 +1,7 @@
 """The batched engine at the configuration the throughput figure is measured
 on, against the FP64 oracle: MeerKAT-shaped snapshots (2016 baselines, up
 to 4096 channels x 4 pols), 2048^2 images of 2 arcsec (G = 4096), a plan
-with batch_max = 16 and the default lane runs (256 channels at 4096).
+with batch_max = 32 and the default lane runs (256 channels at 4096).
 
 * One batch of six distinct snapshots: four full-band, one 2048-channel and
   one 1024-channel sub-band (30 % and 50 % flags), one with weights.  Every
@@ -78,7 +78,7 @@ def _dev_snaps(spec):
 def _plan(**kw):
     base = synth.meerkat_workload()
     return toi.Plan(base.image_size, base.cell_arcsec, base.n_bl, base.n_chan, base.n_pol,
-                    tlisi_tile=T, batch_max=16, **kw)
+                    tlisi_tile=T, batch_max=32, **kw)
 
 
 def _run_batch(plan, ds):
