@@ -301,7 +301,6 @@ template <int G, int R, int BPT, int NSEQ, int SSTRIDE, bool FROM, bool TO, clas
 __device__ __forceinline__ void stockham_io(float2* x, int Ns, const float2* __restrict__ tw,
                                             Load& load, Store& store) {
   constexpr int NB = G / R;
-  constexpr int nseq = NSEQ;
   constexpr int LEN = SSTRIDE;
   float2 v[BPT][R];
   int jj[BPT], ss[BPT];
