@@ -963,7 +963,13 @@ def periodic_scores(cube: np.ndarray) -> np.ndarray:
     removed) is Fourier transformed along time, P_f = A_f^2 + B_f^2 with
     A_f = sum_t x_t cos(2 pi f t / S), B_f = sum_t x_t sin(2 pi f t / S)
     (f = 1..F, F = floor(S/2)); harmonic sums H_h(f) = sum_{i=1..h, i f <= F}
-    P_{i f} for h in (1, 2, 4, 8); score = max_{f,h} H_h(f) / sqrt(h)."""
+    P_{i f} for h in (1, 2, 4, 8); score = max_{f,h} H_h(f) / sqrt(h).
+
+    The series is real, so times t and S - t share their cosine and have
+    opposite sines (2 pi f (S - t) / S = 2 pi f - 2 pi f t / S); the sums run
+    over u_t = x_t + x_{S-t} and v_t = x_t - x_{S-t} for t = 1..floor((S-1)/2)
+    with the twiddle of t, after A = x_0 cos(0) and before the middle time
+    S/2 of an even S (reading c10's order)."""
     S = cube.shape[0]
     x = cube.reshape(S, -1).astype(np.float64)
     nt = x.shape[1]
@@ -976,14 +982,21 @@ def periodic_scores(cube: np.ndarray) -> np.ndarray:
     if F == 0:
         return np.zeros(nt)
     cos_t, sin_t = twiddle_table(S)
+    Th = (S - 1) // 2
+    u = [None] + [xc[t] + xc[S - t] for t in range(1, Th + 1)]
+    v = [None] + [xc[t] - xc[S - t] for t in range(1, Th + 1)]
     P = np.zeros((F + 1, nt))
     for f in range(1, F + 1):
-        A = np.zeros(nt)
+        A = xc[0] * cos_t[0]
         B = np.zeros(nt)
-        for t in range(S):
+        for t in range(1, Th + 1):
             m = (f * t) % S
-            A = A + xc[t] * cos_t[m]
-            B = B + xc[t] * sin_t[m]
+            A = A + u[t] * cos_t[m]
+            B = B + v[t] * sin_t[m]
+        if S % 2 == 0:
+            m = (f * (S // 2)) % S
+            A = A + xc[S // 2] * cos_t[m]
+            B = B + xc[S // 2] * sin_t[m]
         P[f] = A * A + B * B
     best = np.zeros(nt)
     roots = {h: math.sqrt(float(h)) for h in HARMONICS}

@@ -70,19 +70,36 @@ __global__ void mean_kernel(const float* __restrict__ cube, int S, int nt, int m
   }
 }
 
-// The mean-removed series x_t = tLISI_t - mean of every tile, once.
+// The series of every tile, mean removed (x_t = tLISI_t - mean), folded once
+// for the transform (reading c10): slot 0 holds x_0, slots 1..Th the sums
+// u_t = x_t + x_{S-t}, slots Th+1..2Th the differences v_t = x_t - x_{S-t}
+// (Th = floor((S-1)/2)), and for an even S slot S-1 the middle x_{S/2}.
+__device__ __forceinline__ double folded(const float* __restrict__ cube, int S, int nt, int k,
+                                         double m, int slot) {
+  const int Th = (S - 1) / 2;
+  auto xt = [&](int t) { return __dsub_rn((double)cube[(size_t)t * nt + k], m); };
+  if (slot == 0) return xt(0);
+  if (slot <= Th) return __dadd_rn(xt(slot), xt(S - slot));
+  if (slot <= 2 * Th) return __dsub_rn(xt(slot - Th), xt(S - slot + Th));
+  return xt(S / 2);
+}
+
 __global__ void centre_kernel(const float* __restrict__ cube, int S, int nt,
                               const double* __restrict__ mu, double* __restrict__ x) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (long long)S * nt) return;
   const int k = (int)(id % nt);
-  x[id] = __dsub_rn((double)cube[id], mu[k]);
+  x[id] = folded(cube, S, nt, k, mu[k], (int)(id / nt));
 }
 
 // One thread per (frequency pair, tile): the powers P_f and P_{f+H} (H =
-// ceil(F/2)) of the mean-removed series, so that each x_t feeds four
-// independent sums.  x is the centred series from centre_kernel, or NULL to
-// form x_t here (bit-identical: the same subtraction).
+// ceil(F/2)) of the mean-removed series, so that each folded value feeds
+// four independent sums.  The series is real, so times t and S - t share
+// their cosine and have opposite sines: A_f = x_0 cos 0 + sum_t u_t cos(2 pi
+// f t / S) [+ x_{S/2} cos(pi f)], B_f = sum_t v_t sin(2 pi f t / S) [+
+// x_{S/2} sin(pi f)], t = 1..Th in order, half the products of the plain
+// sum over t = 0..S-1.  xs is the folded series from centre_kernel, or NULL
+// to fold here (bit-identical: the same operations).
 __global__ void power_kernel(const float* __restrict__ cube, const double* __restrict__ xs,
                              int S, int nt, int F, const double* __restrict__ mu,
                              const double* __restrict__ ct, const double* __restrict__ st,
@@ -94,20 +111,36 @@ __global__ void power_kernel(const float* __restrict__ cube, const double* __res
   const int f1 = (int)(id / nt) + 1, f2 = f1 + H;
   const bool two = f2 <= F;
   const double m = mu[k];
-  double A1 = 0.0, B1 = 0.0, A2 = 0.0, B2 = 0.0;
+  const int Th = (S - 1) / 2;
+  auto x = [&](int slot) {
+    return xs ? xs[(size_t)slot * nt + k] : folded(cube, S, nt, k, m, slot);
+  };
+  const double x0 = x(0);
+  double A1 = __dmul_rn(x0, ct[0]), B1 = 0.0;
+  double A2 = two ? __dmul_rn(x0, ct[0]) : 0.0, B2 = 0.0;
   int i1 = 0, i2 = 0;   // (f * t) mod S, advanced incrementally
-  for (int t = 0; t < S; ++t) {
-    const double x = xs ? xs[(size_t)t * nt + k] : __dsub_rn((double)cube[(size_t)t * nt + k], m);
-    A1 = __dadd_rn(A1, __dmul_rn(x, ct[i1]));
-    B1 = __dadd_rn(B1, __dmul_rn(x, st[i1]));
-    if (two) {
-      A2 = __dadd_rn(A2, __dmul_rn(x, ct[i2]));
-      B2 = __dadd_rn(B2, __dmul_rn(x, st[i2]));
-    }
+  for (int t = 1; t <= Th; ++t) {
     i1 += f1;
     if (i1 >= S) i1 -= S;
     i2 += two ? f2 : 0;
     if (i2 >= S) i2 -= S;
+    const double u = x(t), v = x(Th + t);
+    A1 = __dadd_rn(A1, __dmul_rn(u, ct[i1]));
+    B1 = __dadd_rn(B1, __dmul_rn(v, st[i1]));
+    if (two) {
+      A2 = __dadd_rn(A2, __dmul_rn(u, ct[i2]));
+      B2 = __dadd_rn(B2, __dmul_rn(v, st[i2]));
+    }
+  }
+  if ((S & 1) == 0) {
+    const double xm = x(S - 1);
+    const int m1 = (f1 & 1) ? S / 2 : 0, m2 = (f2 & 1) ? S / 2 : 0;   // (f S/2) mod S
+    A1 = __dadd_rn(A1, __dmul_rn(xm, ct[m1]));
+    B1 = __dadd_rn(B1, __dmul_rn(xm, st[m1]));
+    if (two) {
+      A2 = __dadd_rn(A2, __dmul_rn(xm, ct[m2]));
+      B2 = __dadd_rn(B2, __dmul_rn(xm, st[m2]));
+    }
   }
   P[(size_t)f1 * nt + k] = __dadd_rn(__dmul_rn(A1, A1), __dmul_rn(B1, B1));
   if (two) P[(size_t)f2 * nt + k] = __dadd_rn(__dmul_rn(A2, A2), __dmul_rn(B2, B2));
@@ -269,8 +302,8 @@ size_t candidates_scratch_bytes(int S, int nt) {
   return b + 256;
 }
 
-// Bytes of the optional centred-series buffer (periodic mode): with it the
-// series is centred once instead of once per frequency.
+// Bytes of the optional folded-series buffer (periodic mode): with it the
+// series is centred and folded once instead of once per frequency.
 size_t candidates_centre_bytes(int S, int nt) { return sizeof(double) * (size_t)S * nt; }
 
 cudaError_t candidates_run(const float* cube, int S, int nty, int ntx, int T, int mode,

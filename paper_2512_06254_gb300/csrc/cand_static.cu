@@ -75,8 +75,8 @@ extern "C" toi_status tlisi_candidates_noalloc(const float* cube, int32_t S, int
   int* boxes_dev = reinterpret_cast<int*>(reinterpret_cast<char*>(base) + work);
   double* thr_dev = nullptr;
   int* nbox_dev = nullptr;
-  // no room for a centred copy of the series here: the search centres it per
-  // frequency instead (the same bits)
+  // no room for a folded copy of the series here: the search centres and
+  // folds it per frequency instead (the same bits)
   e = toi::candidates_run(cube, S, nty, ntx, tile, mode, st, base, scores, max_boxes, boxes_dev,
                           &thr_dev, &nbox_dev, nullptr);
   int nb = 0;
