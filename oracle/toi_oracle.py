@@ -969,7 +969,8 @@ def periodic_scores(cube: np.ndarray) -> np.ndarray:
     opposite sines (2 pi f (S - t) / S = 2 pi f - 2 pi f t / S); the sums run
     over u_t = x_t + x_{S-t} and v_t = x_t - x_{S-t} for t = 1..floor((S-1)/2)
     with the twiddle of t, after A = x_0 cos(0) and before the middle time
-    S/2 of an even S (reading c10's order)."""
+    S/2 of an even S (reading c10's order); for an even S the frequencies f
+    and S/2 - f are summed together from the even and odd times."""
     S = cube.shape[0]
     x = cube.reshape(S, -1).astype(np.float64)
     nt = x.shape[1]
@@ -986,7 +987,38 @@ def periodic_scores(cube: np.ndarray) -> np.ndarray:
     u = [None] + [xc[t] + xc[S - t] for t in range(1, Th + 1)]
     v = [None] + [xc[t] - xc[S - t] for t in range(1, Th + 1)]
     P = np.zeros((F + 1, nt))
-    for f in range(1, F + 1):
+    half = S // 2
+    singles = list(range(1, F + 1))
+    if S % 2 == 0:
+        # For an even S the frequencies f and g = S/2 - f share their
+        # twiddles: 2 pi g t / S = pi t - 2 pi f t / S, so cos(2 pi g t / S) =
+        # (-1)^t cos(2 pi f t / S) and sin(2 pi g t / S) = -(-1)^t sin(...).
+        # Summing the even and odd times apart gives both transforms (g's
+        # middle time S/2 keeps its own twiddle).
+        NP = (half - 1) // 2
+        for f in range(1, NP + 1):
+            g = half - f
+            Ae, Ao, Be, Bo = np.zeros(nt), np.zeros(nt), np.zeros(nt), np.zeros(nt)
+            for t in range(1, Th + 1):
+                m = (f * t) % S
+                if t % 2 == 0:
+                    Ae = Ae + u[t] * cos_t[m]
+                    Be = Be + v[t] * sin_t[m]
+                else:
+                    Ao = Ao + u[t] * cos_t[m]
+                    Bo = Bo + v[t] * sin_t[m]
+            base = xc[0] * cos_t[0] + Ae
+            Af, Ag = base + Ao, base - Ao
+            Bf, Bg = Be + Bo, Bo - Be
+            mf, mg = (f * half) % S, (g * half) % S
+            Af = Af + xc[half] * cos_t[mf]
+            Bf = Bf + xc[half] * sin_t[mf]
+            Ag = Ag + xc[half] * cos_t[mg]
+            Bg = Bg + xc[half] * sin_t[mg]
+            P[f] = Af * Af + Bf * Bf
+            P[g] = Ag * Ag + Bg * Bg
+        singles = ([half // 2] if half % 2 == 0 else []) + [half]
+    for f in singles:
         A = xc[0] * cos_t[0]
         B = np.zeros(nt)
         for t in range(1, Th + 1):
@@ -994,9 +1026,9 @@ def periodic_scores(cube: np.ndarray) -> np.ndarray:
             A = A + u[t] * cos_t[m]
             B = B + v[t] * sin_t[m]
         if S % 2 == 0:
-            m = (f * (S // 2)) % S
-            A = A + xc[S // 2] * cos_t[m]
-            B = B + xc[S // 2] * sin_t[m]
+            m = (f * half) % S
+            A = A + xc[half] * cos_t[m]
+            B = B + xc[half] * sin_t[m]
         P[f] = A * A + B * B
     best = np.zeros(nt)
     roots = {h: math.sqrt(float(h)) for h in HARMONICS}

@@ -146,6 +146,77 @@ __global__ void power_kernel(const float* __restrict__ cube, const double* __res
   if (two) P[(size_t)f2 * nt + k] = __dadd_rn(__dmul_rn(A2, A2), __dmul_rn(B2, B2));
 }
 
+// Even S: frequencies f and g = S/2 - f share their twiddles (2 pi g t / S
+// = pi t - 2 pi f t / S: cos(...g...) = (-1)^t cos(...f...), sin(...g...) =
+// -(-1)^t sin(...f...)), so one thread sums the even and odd times of the
+// folded series apart and forms both transforms from them:
+//   A_f = (x_0 cos 0 + Ae) + Ao,  A_g = (x_0 cos 0 + Ae) - Ao,
+//   B_f = Be + Bo,               B_g = Bo - Be,
+// then each adds its own middle time S/2.  Thread groups 0..NP-1 are the
+// pairs f = 1..NP (NP = floor((S/2 - 1) / 2)); the rest are the frequencies
+// without a partner, S/4 (when S/2 is even) and S/2, summed as in
+// power_kernel.  Half the products of power_kernel again.
+__global__ void power_pairs_kernel(const float* __restrict__ cube,
+                                   const double* __restrict__ xs, int S, int nt,
+                                   const double* __restrict__ mu,
+                                   const double* __restrict__ ct,
+                                   const double* __restrict__ st, double* __restrict__ P) {
+  const int half = S / 2, Th = half - 1;
+  const int NP = (half - 1) / 2;
+  const int NS = (half % 2 == 0) ? 2 : 1;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)(NP + NS) * nt) return;
+  const int k = (int)(id % nt);
+  const int grp = (int)(id / nt);
+  const double m = mu[k];
+  auto x = [&](int slot) {
+    return xs ? xs[(size_t)slot * nt + k] : folded(cube, S, nt, k, m, slot);
+  };
+  const double x0c = __dmul_rn(x(0), ct[0]);
+  const double xm = x(S - 1);
+  if (grp < NP) {
+    const int f = grp + 1, g = half - f;
+    double Ae = 0.0, Ao = 0.0, Be = 0.0, Bo = 0.0;
+    int i = 0;   // (f * t) mod S
+    for (int t = 1; t <= Th; ++t) {
+      i += f;
+      if (i >= S) i -= S;
+      const double u = x(t), v = x(Th + t);
+      if (t & 1) {
+        Ao = __dadd_rn(Ao, __dmul_rn(u, ct[i]));
+        Bo = __dadd_rn(Bo, __dmul_rn(v, st[i]));
+      } else {
+        Ae = __dadd_rn(Ae, __dmul_rn(u, ct[i]));
+        Be = __dadd_rn(Be, __dmul_rn(v, st[i]));
+      }
+    }
+    const double base = __dadd_rn(x0c, Ae);
+    double Af = __dadd_rn(base, Ao), Ag = __dsub_rn(base, Ao);
+    double Bf = __dadd_rn(Be, Bo), Bg = __dsub_rn(Bo, Be);
+    const int mf = (f & 1) ? half : 0, mg = (g & 1) ? half : 0;   // (f S/2) mod S
+    Af = __dadd_rn(Af, __dmul_rn(xm, ct[mf]));
+    Bf = __dadd_rn(Bf, __dmul_rn(xm, st[mf]));
+    Ag = __dadd_rn(Ag, __dmul_rn(xm, ct[mg]));
+    Bg = __dadd_rn(Bg, __dmul_rn(xm, st[mg]));
+    P[(size_t)f * nt + k] = __dadd_rn(__dmul_rn(Af, Af), __dmul_rn(Bf, Bf));
+    P[(size_t)g * nt + k] = __dadd_rn(__dmul_rn(Ag, Ag), __dmul_rn(Bg, Bg));
+  } else {
+    const int f = (grp == NP && NS == 2) ? half / 2 : half;
+    double A = x0c, B = 0.0;
+    int i = 0;
+    for (int t = 1; t <= Th; ++t) {
+      i += f;
+      if (i >= S) i -= S;
+      A = __dadd_rn(A, __dmul_rn(x(t), ct[i]));
+      B = __dadd_rn(B, __dmul_rn(x(Th + t), st[i]));
+    }
+    const int mf = (f & 1) ? half : 0;
+    A = __dadd_rn(A, __dmul_rn(xm, ct[mf]));
+    B = __dadd_rn(B, __dmul_rn(xm, st[mf]));
+    P[(size_t)f * nt + k] = __dadd_rn(__dmul_rn(A, A), __dmul_rn(B, B));
+  }
+}
+
 __global__ void harmonic_kernel(const double* __restrict__ P, int nt, int F,
                                 double* __restrict__ score) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -335,9 +406,16 @@ cudaError_t candidates_run(const float* cube, int S, int nty, int ntx, int T, in
         const long long nx = (long long)S * nt;
         centre_kernel<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(cube, S, nt, mean, xbuf);
       }
-      const long long n = (long long)((F + 1) / 2) * nt;
-      power_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cube, xbuf, S, nt, F, mean, ct,
-                                                                stw, P);
+      if (S % 2 == 0) {
+        const int half = S / 2;
+        const long long n = (long long)((half - 1) / 2 + (half % 2 == 0 ? 2 : 1)) * nt;
+        power_pairs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cube, xbuf, S, nt, mean,
+                                                                        ct, stw, P);
+      } else {
+        const long long n = (long long)((F + 1) / 2) * nt;
+        power_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cube, xbuf, S, nt, F, mean, ct,
+                                                                  stw, P);
+      }
       harmonic_kernel<<<(nt + 255) / 256, 256, 0, st>>>(P, nt, F, score);
     } else {
       cudaMemsetAsync(score, 0, sizeof(double) * nt, st);

@@ -102,10 +102,13 @@ def test_twiddles_match_libm():
         assert np.abs(s - np.sin(2 * np.pi * m / S)).max() < 2e-15
 
 
-def test_periodogram_matches_fft():
-    """P_f of the fixed-order DFT equals |rfft|^2 of the mean-removed series."""
+@pytest.mark.parametrize("S", [37, 38, 40])
+def test_periodogram_matches_fft(S):
+    """P_f of the fixed-order DFT equals |rfft|^2 of the mean-removed series
+    (odd S: every frequency on its own; even S: f and S/2 - f together, S/2
+    odd or even)."""
     rng = np.random.default_rng(10)
-    cube = rng.uniform(0.5, 1.0, size=(37, 3, 2)).astype(np.float32)
+    cube = rng.uniform(0.5, 1.0, size=(S, 3, 2)).astype(np.float32)
     S = cube.shape[0]
     x = cube.reshape(S, -1).astype(np.float64)
     x = x - x.mean(0)
