@@ -1226,7 +1226,9 @@ def main():
     ap.add_argument("--engine", default="batch", choices=["single", "batch"],
                     help="single: toi_grid + toi_image + tlisi_update per snapshot; batch: "
                          "toi_batch over --batch snapshots per launch")
-    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--batch", type=int, default=None,
+                    help="snapshots per batched launch (default 32; 16 for --workload uneven, "
+                         "the batched-stream configuration's B)")
     ap.add_argument("--grid-rows", type=int, default=0, choices=[0, 4, 8],
                     help="gridder window rows per lane (0: the library's default)")
     ap.add_argument("--mode", type=int, default=2, choices=[2, 3],
@@ -1261,6 +1263,8 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0,
                     help="run N imaging passes of one snapshot (for ncu) and exit")
     args = ap.parse_args()
+    if args.batch is None:
+        args.batch = 16 if args.workload == "uneven" else 32
     if args.profile_case:
         profile_case(args)
         return
