@@ -383,6 +383,16 @@ __device__ __forceinline__ int row_limit(const double* snap, int G) {
   return r < G / 2 ? r : G / 2 - 1;
 }
 
+// The row pass's output T, [G/2 rows][N columns] complex, is stored in
+// column groups of four: element (r, j) at ((j / 4) (G/2) + r) 4 + j mod 4.
+// A column-pass block reads the columns of one group (two transforms) down
+// every row, now one contiguous run per warp instead of one 32-byte piece
+// per row 8 N bytes apart; the row pass still writes whole 32-byte pieces.
+template <int G>
+__device__ __forceinline__ size_t tcol(int r, int j) {
+  return ((size_t)(j >> 2) * (G / 2) + r) * 4 + (j & 3);
+}
+
 template <int G>
 struct RowCfg {
   // one thread per radix-16 butterfly of a row (64 to 512 threads)
@@ -414,12 +424,11 @@ __device__ __forceinline__ void fft_rows_body(float2* __restrict__ H, int N,
   auto load = [&](int, int n) -> float2 {
     return (n >= n_lo && n <= n_hi) ? src[n] : make_float2(0.f, 0.f);
   };
-  float2* dst = T + (size_t)row * N;
   auto store = [&](int, int m, float2 v) {
     const int jp = m < G / 2 ? m : m - G;
     if (jp >= -N / 2 && jp < N / 2) {
       if (jp & 1) { v.x = -v.x; v.y = -v.y; }
-      dst[jp + N / 2] = v;
+      T[tcol<G>(row, jp + N / 2)] = v;
     }
   };
   fft_io<G, 1, G + G / 16, RowCfg<G>::NT>(x, tw, load, store);
@@ -478,7 +487,7 @@ __device__ __forceinline__ void fft_cols_body(const float2* __restrict__ T, int 
   auto load = [&](int sq, int n) -> float2 {
     const int r = n < half ? n : G - n;
     if (n == half || r > rmax) return make_float2(0.f, 0.f);
-    const float4 t = __ldg(reinterpret_cast<const float4*>(T + (size_t)r * N + col0 + 2 * sq));
+    const float4 t = __ldg(reinterpret_cast<const float4*>(T + tcol<G>(r, col0 + 2 * sq)));
     return n < half ? make_float2(t.x - t.w, t.y + t.z) : make_float2(t.x + t.w, t.z - t.y);
   };
   const double omega = snap[SNAP_OMEGA], sumw = snap[SNAP_SUMW];

@@ -165,7 +165,7 @@ struct toi_plan_s {
   double* bpart = nullptr;               // [ceil(max_bl / 8)][11] plane-fit partial sums
   float2* twiddle = nullptr;             // [G] exp(+2 pi i k / G)
   float* corr = nullptr;                 // [N] 1 / psi_hat((j - N/2) / G)
-  float2* fft_tmp = nullptr;             // [G/2][N] rows after pass 1
+  float2* fft_tmp = nullptr;             // (G/2) x N after pass 1, in column groups of four
   float* tilted = nullptr;               // [N][N]
   std::vector<float*> ring;              // [R][N][N] image ring, R = max(3, batch_max + 2)
   unsigned int* ring_max = nullptr;      // [R] float bits of max |I|
@@ -198,7 +198,7 @@ struct toi_plan_s {
   float2* b_kf = nullptr;
   double* b_kpart = nullptr;                // [batch_max][2 ceil(max_ch / 256) + 2]
   double* b_bpart = nullptr;                // [batch_max][11 ceil(max_bl / 8)]
-  float2* b_fft_tmp = nullptr;              // [batch_max][G/2][N]
+  float2* b_fft_tmp = nullptr;              // [batch_max] x (G/2) x N, as fft_tmp
   float* b_tilted = nullptr;                // [batch_max][N][N]
   double* b_tile_mom = nullptr;             // [batch_max][ntl][5]
   int grid_blocks = 0;                      // persistent gridder: resident blocks
