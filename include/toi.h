@@ -179,7 +179,11 @@ toi_status tlisi_reset(toi_plan_t plan);
  * order (no fused multiply-add) so that any implementation of the same order
  * gives identical bits:
  *   periodic:     per tile x_t = tLISI_t - mean; P_f = A_f^2 + B_f^2 with
- *                 A_f, B_f the cosine/sine sums at f = 1..floor(S/2);
+ *                 A_f, B_f the cosine/sine sums at f = 1..floor(S/2), taken
+ *                 over the folded series x_t +- x_{S-t} (t = 1..(S-1)/2,
+ *                 after x_0 and before the middle time of an even S) and,
+ *                 for an even S, for f and S/2 - f together from the sums
+ *                 over even and odd t;
  *                 score = max over f and h in {1,2,4,8} of
  *                 sum_{i<=h, i f <= F} P_{i f} / sqrt(h); k = 5;
  *   nonperiodic:  score = sum_t (1 - tLISI_t); k = 4;
