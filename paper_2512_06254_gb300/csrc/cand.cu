@@ -232,7 +232,10 @@ __global__ void harmonic_kernel(const double* __restrict__ P, int nt, int F,
         if (i * f > F) break;
         H = __dadd_rn(H, P[(size_t)(i * f) * nt + k]);
       }
-      best = fmax(best, __ddiv_rn(H, roots[hi]));
+      // H / sqrt(h): exact for h = 1 (H itself) and h = 4 (H times 0.5, the
+      // same correctly rounded value as the division), divided otherwise
+      const double q = hi == 0 ? H : (hi == 2 ? __dmul_rn(H, 0.5) : __ddiv_rn(H, roots[hi]));
+      best = fmax(best, q);
     }
   }
   score[k] = best;
