@@ -92,9 +92,10 @@ __global__ void centre_kernel(const float* __restrict__ cube, int S, int nt,
   x[id] = folded(cube, S, nt, k, mu[k], (int)(id / nt));
 }
 
-// One thread per (frequency pair, tile): the powers P_f and P_{f+H} (H =
-// ceil(F/2)) of the mean-removed series, so that each folded value feeds
-// four independent sums.  The series is real, so times t and S - t share
+// Odd S (an even S runs power_pairs_kernel below).  One thread per
+// (frequency pair, tile): the powers P_f and P_{f+H} (H = ceil(F/2)) of the
+// mean-removed series, so that each folded value feeds four independent
+// sums.  The series is real, so times t and S - t share
 // their cosine and have opposite sines: A_f = x_0 cos 0 + sum_t u_t cos(2 pi
 // f t / S) [+ x_{S/2} cos(pi f)], B_f = sum_t v_t sin(2 pi f t / S) [+
 // x_{S/2} sin(pi f)], t = 1..Th in order, half the products of the plain
