@@ -113,10 +113,12 @@ def _cand_case(cube, T, mode):
     assert boxes == thr_o["boxes"]
 
 
-@pytest.mark.parametrize("S", [1, 2, 3, 37, 118])
+@pytest.mark.parametrize("S", [1, 2, 3, 4, 37, 40, 118])
 @pytest.mark.parametrize("mode", [toi.TOI_CAND_PERIODIC, toi.TOI_CAND_NONPERIODIC])
 def test_candidates_bit_exact(S, mode):
-    """S8 on the same cube: thresholds, scores and boxes identical in every bit."""
+    """S8 on the same cube: thresholds, scores and boxes identical in every
+    bit.  Odd S, and even S with S/2 odd (frequencies paired, S/2 alone) or
+    S/2 even (S/4 alone as well)."""
     rng = np.random.default_rng(S * 10 + mode)
     cube = (1.0 - np.abs(rng.normal(scale=0.03, size=(S, 16, 16)))).astype(np.float32)
     if S >= 37:
