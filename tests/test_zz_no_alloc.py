@@ -39,6 +39,9 @@ def _cube(seed, S, n):
 
 @pytest.mark.parametrize("mode", [toi.TOI_CAND_PERIODIC, toi.TOI_CAND_NONPERIODIC])
 def test_noalloc_matches_allocating_search_twice(mode):
+    # start from an idle device: no earlier test's work may still be running
+    # on another stream when this test's tensors are allocated
+    torch.cuda.synchronize()
     L = B.lib()
     for call, (seed, S, n) in enumerate([(101, 118, 64), (202, 300, 32)]):
         cube = _cube(seed + mode, S, n)
