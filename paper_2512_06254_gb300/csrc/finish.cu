@@ -261,9 +261,13 @@ image_walk_batch(const BatchEntry* __restrict__ E, const BatchHeader* __restrict
     float mx = 0.f;
     float m5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
+    // only the batch's last two images are read from the ring again (the
+    // next batch's first windows, the plan's last image); the others live
+    // in registers here and, when asked for, in the caller's images
+    const bool keep = i >= n - 2;
     for (int b = 0; b < kBatchPix; ++b) {
       if (!live[b]) continue;
-      e.ring_cur[pixv[b]] = v[b];
+      if (keep) e.ring_cur[pixv[b]] = v[b];
       if (e.image_out) e.image_out[pixv[b]] = v[b];
       mx = fmaxf(mx, fabsf(v[b]));
       const float a = prev1[b] - prev2[b], bd = v[b] - prev1[b];
