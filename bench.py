@@ -13,8 +13,8 @@ once) by its CUDA-event time.  The end-to-end number streams the same
 observation from pinned host memory through toi_stream_*.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-  other workloads: --workload uneven | adjoint | localise; --mode 3;
-  --image-size N --fov-deg F --channels C
+  other workloads: --workload fp16 | uneven | adjoint | localise; --mode 3;
+  --image-size N --fov-deg F --channels C; --batch B (default 32)
 """
 from __future__ import annotations
 
