@@ -237,7 +237,9 @@ toi_status tlisi_candidates_noalloc(const float* cube, int32_t S, int32_t nty,
 
 /* One snapshot of a batch: the arguments of toi_grid (device pointers with
  * the same layouts and rules) plus where toi_image would write its image
- * (dev float32 [N][N] or NULL: the image then stays in the plan's ring). */
+ * (dev float32 [N][N] or NULL: the image is then not written out; the plan
+ * keeps only a batch's last two images, for the next windows, and
+ * toi_plan_buffer reads the last one). */
 typedef struct {
   const double* uvw;
   const double* freq;
