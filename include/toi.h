@@ -263,7 +263,7 @@ typedef struct {
  *
  * toi_batch_prepare validates the snapshots on the host and fills the
  * plan's pinned batch table; toi_batch_run enqueues the batch on the plan's
- * stream (two table copies, a counter reset, then 10 kernels).  toi_batch_run makes no host
+ * stream (two table copies, a counter reset, then 9 kernels).  toi_batch_run makes no host
  * call that a CUDA graph capture forbids, and its launch shapes do not
  * depend on the batch, so one captured toi_batch_run can be replayed for
  * every later batch: call toi_batch_prepare before each replay, after the
